@@ -1,0 +1,171 @@
+/*
+ * cwth.h - C ABI of libcwth.so, the GB300 (sm_103a) hop-size continuous
+ * wavelet transform (CWTH).
+ *
+ * The operation (paper Sec. II.A, Eq. 1, discretised with dt = 1 sample, and
+ * Sec. II.B, which evaluates it only at samples spaced by a hop H):
+ *
+ *     W_s[k] = a_s^{-1/2} * sum_n x[n] * conj(psi((n - k*H) / a_s)),
+ *     k = 0 .. ceil(len/H) - 1,  x[n] = 0 outside [0, len),
+ *     psi(t) = (pi*B)^{-1/2} * exp(-t^2/B) * exp(i*2*pi*C*t)   (complex Morlet),
+ *
+ * and the library returns the scalogram |W_s[k]| in float32.
+ *
+ * Conventions shared by every call:
+ *   - No call throws; each returns a cwth_status.
+ *   - "device" pointers are CUDA device memory of the device that was current
+ *     when the plan was made; "host" pointers are ordinary or pinned host
+ *     memory.  The caller owns every buffer it passes in; a plan owns its
+ *     tables and staging buffers and frees them in cwth_destroy.
+ *   - Calls that take a stream (a cudaStream_t passed as void*, NULL = the
+ *     legacy default stream) enqueue their work on it and return without
+ *     synchronising, except cwth_execute_host, which returns once the result
+ *     is in host memory.
+ *   - A plan may be used by one stream at a time; plans are independent.
+ */
+#ifndef CWTH_H
+#define CWTH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CWTH_OK = 0,
+    CWTH_ERR_INVALID_ARG = 1, /* a pointer, size, scale or flag is out of range */
+    CWTH_ERR_OOM = 2,         /* device or host allocation failed             */
+    CWTH_ERR_CUDA = 3,        /* a CUDA runtime call or kernel launch failed  */
+    CWTH_ERR_UNSUPPORTED = 4, /* valid request this build cannot serve        */
+    CWTH_ERR_TIMEOUT = 5,     /* a bounded device wait ran out                */
+    CWTH_ERR_BAD_PLAN = 6     /* NULL, destroyed or foreign plan handle       */
+} cwth_status;
+
+/* Complex Morlet parameters, "cmor B-C": bandwidth B > 0, centre frequency
+ * C > 0 (cycles per unit of t).  The wavelet's spectrum is
+ * exp(-pi^2 B (f - C)^2), peak 1 at f = C. */
+typedef struct {
+    double bandwidth;
+    double center_freq;
+} cwth_morlet;
+
+typedef struct cwth_plan_s *cwth_plan_t;
+
+/* Arithmetic of the direct (time-domain, tensor-core) path.  The spectral
+ * path always computes in float32. */
+enum {
+    CWTH_PREC_FP32 = 0,   /* float32 everywhere                          */
+    CWTH_PREC_BF16 = 1,   /* bf16 operands, float32 accumulation         */
+    CWTH_PREC_BF16X2 = 2  /* hi+lo split bf16 operands, fp32 accumulate  */
+};
+
+/* Which evaluation each scale takes. */
+enum {
+    CWTH_PATH_AUTO = 0,     /* per scale, by the plan's cost model      */
+    CWTH_PATH_SPECTRAL = 1, /* every scale through the FFT path         */
+    CWTH_PATH_DIRECT = 2    /* every scale through the direct sum       */
+};
+
+/*
+ * Build a plan for clips of up to max_len samples.
+ *
+ *   w           host, the Morlet parameters (Eq. 1's psi).
+ *   scales      host, S scales a_s in samples (Eq. 1's a; a_s = C*fs/f_s
+ *               for a centre frequency f_s in Hz).  Output row s is scale s.
+ *   S           number of scales, >= 1.
+ *   hop         H of Sec. II.B, >= 1 (H = 1 is the plain CWT).
+ *   sample_rate fs in Hz, > 0 (recorded for cwth_plan_query; scales are
+ *               already in samples).
+ *   max_len     longest clip the plan accepts, >= 1.
+ *   precision   CWTH_PREC_*; path CWTH_PATH_*.
+ *   out         host, receives the handle.
+ *
+ * Makes the float64-generated tables (FFT twiddles, per-scale Morlet band
+ * limits, direct-path tap banks) on the current device and synchronises
+ * with them.  Errors: CWTH_ERR_INVALID_ARG for a NULL pointer, S/hop/max_len
+ * < 1, a scale that is not finite and positive, B/C/fs not finite and
+ * positive, or an unknown flag; CWTH_ERR_UNSUPPORTED when the forced path
+ * cannot serve the request (the spectral path needs a power-of-two hop; the
+ * direct path needs hop % 8 == 0 for bf16 operands and at most 4096 taps);
+ * CWTH_ERR_OOM / CWTH_ERR_CUDA otherwise.  On error *out is set to NULL.
+ */
+cwth_status cwth_plan(const cwth_morlet *w, const double *scales, int32_t S, int32_t hop,
+                      double sample_rate, int64_t max_len, int32_t precision,
+                      int32_t path, cwth_plan_t *out);
+
+/*
+ * Scalograms of a batch of clips, asynchronous on `stream`.
+ *
+ *   d_x       device, float32, clip i occupies d_x[i*ld_x .. i*ld_x + len_i).
+ *   ld_x      row stride in elements, >= max_len.
+ *   d_lengths device, int64 per clip, each in [0, max_len]; NULL means every
+ *             clip has max_len samples.  Lengths are read on the device.
+ *   batch     number of clips, >= 0 (0 is a no-op).
+ *   d_out     device, float32 [batch][S][F_max], F_max = cwth_num_frames(
+ *             max_len, hop).  out[i][s][k] = |W_s[k]| of clip i for
+ *             k < ceil(len_i/H); frames at and beyond ceil(len_i/H) are not
+ *             written.  d_out must not overlap d_x.
+ *   stream    cudaStream_t as void*, NULL for the legacy default stream.
+ *
+ * Errors: CWTH_ERR_BAD_PLAN, CWTH_ERR_INVALID_ARG (NULL buffer with
+ * batch > 0, ld_x < max_len, batch < 0), CWTH_ERR_CUDA (launch failure).
+ * Kernel faults surface later, at the caller's next synchronisation.
+ */
+cwth_status cwth_execute(cwth_plan_t plan, const float *d_x, int64_t ld_x,
+                         const int64_t *d_lengths, int32_t batch, float *d_out,
+                         void *stream);
+
+/*
+ * Same transform from and to host memory: copies the batch in (one
+ * cudaMemcpyAsync per buffer), runs cwth_execute on `stream`, copies the
+ * scalograms out and synchronises the stream before returning.  h_lengths
+ * is host memory (or NULL); the other arguments are as in cwth_execute.
+ * Device staging is owned by the plan and grows to the largest batch seen.
+ * Pinned host buffers make the copies asynchronous DMA transfers.
+ */
+cwth_status cwth_execute_host(cwth_plan_t plan, const float *h_x, int64_t ld_x,
+                              const int64_t *h_lengths, int32_t batch, float *h_out,
+                              void *stream);
+
+/* Release a plan's device tables and staging.  NULL is accepted.  The caller
+ * must not destroy a plan while work it enqueued may still be running. */
+cwth_status cwth_destroy(cwth_plan_t plan);
+
+/* ceil(n / hop), the number of frames b = 0, H, 2H, ... inside [0, n);
+ * 0 when n <= 0 or hop <= 0. */
+int64_t cwth_num_frames(int64_t n, int32_t hop);
+
+/* Static, human-readable name of a status code. */
+const char *cwth_status_string(cwth_status s);
+
+/* What a plan decided, for tests and benchmarks. */
+typedef struct {
+    int32_t num_scales;        /* S                                            */
+    int32_t hop;               /* H                                            */
+    int64_t max_len;           /* longest clip                                 */
+    int64_t frames_max;        /* cwth_num_frames(max_len, hop)                */
+    int32_t num_spectral;      /* scales on the FFT path                       */
+    int32_t num_direct;        /* scales on the direct path                    */
+    int32_t seg_len;           /* FFT segment length M (spectral path)         */
+    int32_t seg_frames;        /* frames each segment produces                 */
+    int32_t seg_halo;          /* samples of left context per segment          */
+    int32_t fold_len;          /* P = M / H, the inverse-FFT length            */
+    int32_t num_segments;      /* segments per max_len clip                    */
+    int32_t direct_taps;       /* padded tap count of the direct path          */
+    int64_t table_bytes;       /* device bytes held by the plan's tables       */
+    double sample_rate;        /* as given to cwth_plan                        */
+} cwth_plan_info;
+
+/* Fill *info.  Errors: CWTH_ERR_BAD_PLAN, CWTH_ERR_INVALID_ARG (NULL info). */
+cwth_status cwth_plan_query(cwth_plan_t plan, cwth_plan_info *info);
+
+/* Per-scale path decision: paths[s] = CWTH_PATH_SPECTRAL or CWTH_PATH_DIRECT
+ * for s < S (host array of S entries). */
+cwth_status cwth_plan_scale_paths(cwth_plan_t plan, int32_t *paths);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CWTH_H */

@@ -1,0 +1,320 @@
+// Spectral path of the hop-size CWT (paper Sec. II.A Eq. 1 + Sec. II.B hop).
+//
+// One CTA owns one (clip, segment, scale group).  A segment is M consecutive
+// samples whose left `halo` samples (a multiple of the hop) and right tail are
+// context, so that the circular correlation over the segment equals the
+// linear one of Eq. 1 at the segment's `seg_frames` valid frames
+// (overlap-save).  Everything after the input load stays in shared memory:
+//
+//   a1  stage    z[n] = x[s0+2n] + i x[s0+2n+1], zero outside [0, len)
+//   a2  FFT      Stockham radix-4/8 FFT of the M/2 complex points, then the
+//                real-input split to X[q], q = 0 .. M/2
+//   a3  fold     Z_s[r] = sum_{q = r (mod P)} X[q] * sqrt(a)/M * Psi(a q/M)
+//                over the unwrapped Morlet band of scale s (P = M/H); the
+//                spectrum is summed over the H aliases of each bin, which is
+//                decimation by the hop done in frequency
+//   a4  IFFT     length-P inverse FFT of every Z_s, |.|, store the valid
+//                frames of row s
+//
+// The correlation taps g[t] = a^{-1/2} conj(psi(t/a)) have the real
+// spectrum sqrt(a) sum_m Psi(a(nu - m)) (Poisson summation of the sampled
+// Gaussian), so no complex multiplier is needed; bins q > M/2 come from
+// conj(X[M - q]) because x is real.
+#include "cwth_internal.h"
+
+namespace cwth {
+namespace {
+
+// Shared-memory index with one float2 of padding every 32 entries, so that
+// strided Stockham writes spread over the banks.
+__device__ __forceinline__ int spad(int i) { return i + (i >> 5); }
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// times -i (forward transform) or +i (inverse transform)
+template <bool INV>
+__device__ __forceinline__ float2 rot90(float2 a) {
+    return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+template <int R, bool INV>
+struct Dft;
+
+template <bool INV>
+struct Dft<2, INV> {
+    static __device__ __forceinline__ void run(float2* v) {
+        const float2 a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    }
+};
+
+template <bool INV>
+struct Dft<4, INV> {
+    static __device__ __forceinline__ void run(float2* v) {
+        const float2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+        const float2 t2 = cadd(v[1], v[3]), t3 = rot90<INV>(csub(v[1], v[3]));
+        v[0] = cadd(t0, t2);
+        v[2] = csub(t0, t2);
+        v[1] = cadd(t1, t3);
+        v[3] = csub(t1, t3);
+    }
+};
+
+template <bool INV>
+struct Dft<8, INV> {
+    static __device__ __forceinline__ void run(float2* v) {
+        float2 e[4] = {v[0], v[2], v[4], v[6]};
+        float2 o[4] = {v[1], v[3], v[5], v[7]};
+        Dft<4, INV>::run(e);
+        Dft<4, INV>::run(o);
+        const float h = 0.70710678118654752440f;
+        // o[k] *= exp(-+ i pi k / 4)
+        const float2 o1 = INV ? make_float2(h * (o[1].x - o[1].y), h * (o[1].x + o[1].y))
+                              : make_float2(h * (o[1].x + o[1].y), h * (o[1].y - o[1].x));
+        const float2 o2 = rot90<INV>(o[2]);
+        const float2 o3 = INV ? make_float2(-h * (o[3].x + o[3].y), h * (o[3].x - o[3].y))
+                              : make_float2(h * (o[3].y - o[3].x), -h * (o[3].x + o[3].y));
+        v[0] = cadd(e[0], o[0]);
+        v[4] = csub(e[0], o[0]);
+        v[1] = cadd(e[1], o1);
+        v[5] = csub(e[1], o1);
+        v[2] = cadd(e[2], o2);
+        v[6] = csub(e[2], o2);
+        v[3] = cadd(e[3], o3);
+        v[7] = csub(e[3], o3);
+    }
+};
+
+// One Stockham autosort pass over `nbatch` independent transforms of length
+// L (a power of two) stored back to back in `buf`.  Ns is the length of the
+// sub-transforms already done; each butterfly j reads R points spaced L/R
+// apart, multiplies point r by w^{r*k} (k = j mod Ns, w = exp(-+2 pi i /
+// (Ns R))), does a length-R DFT and writes the points spaced Ns apart at
+// (j - k) R + k.  All reads finish before any write (barrier), so the pass
+// runs in place.  tstride is the twiddle-table step for one unit of r*k.
+template <int R, int MAXB, bool INV>
+__device__ __forceinline__ void fft_pass(float2* __restrict__ buf, int L, int nbatch, int Ns,
+                                         const float2* __restrict__ tw, int tstride) {
+    const int LR = L / R;
+    const int lg_lr = __ffs(LR) - 1;
+    const int nb = nbatch * LR;
+    float2 v[MAXB][R];
+#pragma unroll
+    for (int u = 0; u < MAXB; ++u) {
+        const int j = threadIdx.x + u * blockDim.x;
+        if (j < nb) {
+            const int b = j >> lg_lr;
+            const int jj = j & (LR - 1);
+            const int base = b * L;
+            const int k = jj & (Ns - 1);
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[u][r] = buf[spad(base + jj + r * LR)];
+            if (Ns > 1) {
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    float2 w = __ldg(&tw[r * k * tstride]);
+                    if (INV) w.y = -w.y;
+                    v[u][r] = cmul(v[u][r], w);
+                }
+            }
+            Dft<R, INV>::run(v[u]);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < MAXB; ++u) {
+        const int j = threadIdx.x + u * blockDim.x;
+        if (j < nb) {
+            const int b = j >> lg_lr;
+            const int jj = j & (LR - 1);
+            const int base = b * L;
+            const int k = jj & (Ns - 1);
+            const int d = base + (jj - k) * R + k;
+#pragma unroll
+            for (int r = 0; r < R; ++r) buf[spad(d + r * Ns)] = v[u][r];
+        }
+    }
+    __syncthreads();
+}
+
+template <int R, bool INV>
+__device__ __forceinline__ void fft_pass_dispatch(float2* buf, int L, int nbatch, int Ns,
+                                                  const float2* tw, int tstride) {
+    const int nb = nbatch * (L / R);
+    const int per = (nb + blockDim.x - 1) / blockDim.x;
+    // Up to 16 complex values per thread: the caller keeps nbatch * L <= 8192
+    // with 512 threads.
+    constexpr int kMaxB = 16 / R;
+    if (per <= 1)
+        fft_pass<R, 1, INV>(buf, L, nbatch, Ns, tw, tstride);
+    else if (per <= 2)
+        fft_pass<R, 2, INV>(buf, L, nbatch, Ns, tw, tstride);
+    else if (per <= 4 || kMaxB <= 4)
+        fft_pass<R, (kMaxB < 4 ? kMaxB : 4), INV>(buf, L, nbatch, Ns, tw, tstride);
+    else
+        fft_pass<R, kMaxB, INV>(buf, L, nbatch, Ns, tw, tstride);
+}
+
+// Batched power-of-two FFT in shared memory (natural order in and out).
+// ts = M / L maps the transform's twiddles onto the table of exp(-2 pi i m/M).
+// Radices: 8 where possible, a leading 4 (or 4,4) for the remainder of log2 L.
+template <bool INV>
+__device__ __noinline__ void fft_block(float2* buf, int L, int nbatch, const float2* tw, int ts) {
+    const int e = __ffs(L) - 1;
+    int n4 = 0;
+    // L >= 8 here: the plan keeps P = M / H >= 8 and M / 2 >= 256.
+    if (e % 3 == 1) n4 = 2;
+    if (e % 3 == 2) n4 = 1;
+    int Ns = 1;
+    for (int i = 0; i < n4; ++i) {
+        fft_pass_dispatch<4, INV>(buf, L, nbatch, Ns, tw, ts * (L / (Ns * 4)));
+        Ns *= 4;
+    }
+    while (Ns < L) {
+        fft_pass_dispatch<8, INV>(buf, L, nbatch, Ns, tw, ts * (L / (Ns * 8)));
+        Ns *= 8;
+    }
+}
+
+__global__ void __launch_bounds__(kSpecThreads, 1) spectral_segment_kernel(const SpecLaunch p) {
+    extern __shared__ float2 smem[];
+    const int M = p.M, Mh = M >> 1, P = p.P;
+    float2* X = smem;                  // spad(Mh) + 1 used
+    float2* Z = smem + spad(Mh) + 2;   // spad(nconc * P - 1) + 1 used
+
+    const int seg = blockIdx.x, clip = blockIdx.y, grp = blockIdx.z;
+    int64_t len = p.lengths ? p.lengths[clip] : p.max_len;
+    len = len < 0 ? 0 : (len > p.max_len ? p.max_len : len);
+    const int64_t F = (len + p.hop - 1) / p.hop;
+    const int64_t k0 = (int64_t)seg * p.seg_frames;
+    const int sp_begin = grp * p.group_size;
+    if (k0 >= F || sp_begin >= p.n_sp) return;
+    const int sp_end = min(p.n_sp, sp_begin + p.group_size);
+
+    // a1: stage the segment as M/2 complex points.
+    const int64_t s0 = k0 * p.hop - p.halo;
+    const float* xr = p.x + (int64_t)clip * p.ld_x;
+    for (int n = threadIdx.x; n < Mh; n += blockDim.x) {
+        const int64_t i0 = s0 + 2 * (int64_t)n;
+        const float a = (i0 >= 0 && i0 < len) ? __ldg(xr + i0) : 0.f;
+        const float b = (i0 + 1 >= 0 && i0 + 1 < len) ? __ldg(xr + i0 + 1) : 0.f;
+        X[spad(n)] = make_float2(a, b);
+    }
+    __syncthreads();
+
+    // a2: forward FFT of the M/2 points, twiddles exp(-2 pi i m/(M/2)) = tw[2m].
+    fft_block<false>(X, Mh, 1, p.tw, 2);
+
+    // Real-input split: with Z = FFT(z), E = (Z[q] + conj Z[Mh-q])/2 and
+    // O = (Z[q] - conj Z[Mh-q])/(2i) are the spectra of the even and odd
+    // samples, X[q] = E + exp(-2 pi i q/M) O and X[Mh-q] = conj(E - exp(-2 pi i q/M) O).
+    // Each pair (q, Mh-q) is read and written by one thread only.
+    for (int q = threadIdx.x; q <= (Mh >> 1); q += blockDim.x) {
+        const int qm = (Mh - q) & (Mh - 1);
+        const float2 zq = X[spad(q)];
+        const float2 zm = X[spad(qm)];
+        const float2 E = make_float2(0.5f * (zq.x + zm.x), 0.5f * (zq.y - zm.y));
+        const float2 O = make_float2(0.5f * (zq.y + zm.y), 0.5f * (zm.x - zq.x));
+        const float2 t = cmul(__ldg(&p.tw[q]), O);
+        const float2 xq = cadd(E, t);
+        const float2 xm = csub(E, t);
+        X[spad(q)] = xq;
+        X[spad(Mh - q)] = make_float2(xm.x, -xm.y);
+    }
+    __syncthreads();
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nwarps = blockDim.x >> 5;
+    const int strips = (P + 31) >> 5;
+
+    for (int c0 = sp_begin; c0 < sp_end; c0 += p.nconc) {
+        const int nc = min(p.nconc, sp_end - c0);
+
+        // a3: band multiply + hop fold.  Lane = residue r; one item = 32
+        // consecutive residues of one scale; the loop walks the unwrapped band.
+        for (int it = warp; it < nc * strips; it += nwarps) {
+            const int c = it / strips;
+            const int r = ((it - c * strips) << 5) + lane;
+            if (r >= P) continue;
+            const SpecScale sc = p.sc[c0 + c];
+            int qu = sc.q_lo + ((r - sc.q_lo) & (P - 1));
+            float2 acc = make_float2(0.f, 0.f);
+            for (; qu <= sc.q_hi; qu += P) {
+                const int q = qu & (M - 1);
+                float2 v;
+                if (q <= Mh) {
+                    v = X[spad(q)];
+                } else {
+                    v = X[spad(M - q)];
+                    v.y = -v.y;
+                }
+                const float arg = fmaf((float)qu, sc.a_over_m, -p.center);
+                const float g = sc.gscale * exp2f(p.kexp * arg * arg);
+                acc.x = fmaf(v.x, g, acc.x);
+                acc.y = fmaf(v.y, g, acc.y);
+            }
+            Z[spad(c * P + r)] = acc;
+        }
+        __syncthreads();
+
+        // a4: inverse FFT of length P for every scale of the chunk; the 1/M
+        // normalisation is already in gscale.  exp(+2 pi i m/P) = conj(tw[m H]).
+        fft_block<true>(Z, P, nc, p.tw, p.hop);
+
+        const int Fs = p.seg_frames;
+        for (int i = threadIdx.x; i < nc * Fs; i += blockDim.x) {
+            const int c = i / Fs;
+            const int f = i - c * Fs;
+            const int64_t k = k0 + f;
+            if (k < F) {
+                const float2 w = Z[spad(c * P + p.kp0 + f)];
+                const int row = p.sc[c0 + c].row;
+                p.out[((int64_t)clip * p.S_total + row) * p.frames_max + k] =
+                    sqrtf(fmaf(w.x, w.x, w.y * w.y));
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// exp(-2 pi i m / M) in float64, rounded once to float32.
+__global__ void twiddle_kernel(float2* tw, int M) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m < M) {
+        double s, c;
+        sincospi(2.0 * (double)m / (double)M, &s, &c);
+        tw[m] = make_float2((float)c, (float)-s);
+    }
+}
+
+}  // namespace
+
+size_t spectral_smem_bytes(int M, int P, int nconc) {
+    auto pad = [](long i) { return i + (i >> 5); };
+    const long x = pad(M / 2) + 2;
+    const long z = pad((long)nconc * P - 1) + 1;
+    return (size_t)(x + z) * sizeof(float2);
+}
+
+cudaError_t spectral_prepare_device() {
+    return cudaFuncSetAttribute(spectral_segment_kernel,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+}
+
+cudaError_t spectral_make_twiddles(float2* d_tw, int M, cudaStream_t st) {
+    twiddle_kernel<<<(M + 255) / 256, 256, 0, st>>>(d_tw, M);
+    return cudaGetLastError();
+}
+
+cudaError_t spectral_launch(const SpecLaunch& L, int n_seg, int batch, int n_groups, size_t smem,
+                            cudaStream_t st) {
+    dim3 grid(n_seg, batch, n_groups);
+    spectral_segment_kernel<<<grid, kSpecThreads, smem, st>>>(L);
+    return cudaGetLastError();
+}
+
+}  // namespace cwth

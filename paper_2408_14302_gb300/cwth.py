@@ -1,0 +1,190 @@
+"""Thin ctypes binding of libcwth.so (include/cwth.h).
+
+Argument marshalling only: every step of the transform runs in the CUDA
+library.  PyTorch provides device memory and the current stream.  There is
+no CPU fallback: if the library is missing the import of this module fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libcwth.so")
+
+CWTH_OK = 0
+STATUS = {0: "CWTH_OK", 1: "CWTH_ERR_INVALID_ARG", 2: "CWTH_ERR_OOM", 3: "CWTH_ERR_CUDA",
+          4: "CWTH_ERR_UNSUPPORTED", 5: "CWTH_ERR_TIMEOUT", 6: "CWTH_ERR_BAD_PLAN"}
+PREC = {"fp32": 0, "bf16": 1, "bf16x2": 2}
+PATH = {"auto": 0, "spectral": 1, "direct": 2}
+
+# Every symbol include/cwth.h declares.
+EXPORTS = ("cwth_plan", "cwth_execute", "cwth_execute_host", "cwth_destroy",
+           "cwth_num_frames", "cwth_status_string", "cwth_plan_query",
+           "cwth_plan_scale_paths")
+
+
+class CwthError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)}")
+
+
+class Morlet(ctypes.Structure):
+    _fields_ = [("bandwidth", ctypes.c_double), ("center_freq", ctypes.c_double)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("num_scales", ctypes.c_int32), ("hop", ctypes.c_int32),
+                ("max_len", ctypes.c_int64), ("frames_max", ctypes.c_int64),
+                ("num_spectral", ctypes.c_int32), ("num_direct", ctypes.c_int32),
+                ("seg_len", ctypes.c_int32), ("seg_frames", ctypes.c_int32),
+                ("seg_halo", ctypes.c_int32), ("fold_len", ctypes.c_int32),
+                ("num_segments", ctypes.c_int32), ("direct_taps", ctypes.c_int32),
+                ("table_bytes", ctypes.c_int64), ("sample_rate", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(f"libcwth.so not built ({path}); run "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(path)
+    vp, i32, i64, dp = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    lib.cwth_plan.argtypes = [ctypes.POINTER(Morlet), ctypes.POINTER(ctypes.c_double), i32, i32,
+                              dp, i64, i32, i32, ctypes.POINTER(vp)]
+    lib.cwth_plan.restype = ctypes.c_int
+    lib.cwth_execute.argtypes = [vp, vp, i64, vp, i32, vp, vp]
+    lib.cwth_execute.restype = ctypes.c_int
+    lib.cwth_execute_host.argtypes = [vp, vp, i64, vp, i32, vp, vp]
+    lib.cwth_execute_host.restype = ctypes.c_int
+    lib.cwth_destroy.argtypes = [vp]
+    lib.cwth_destroy.restype = ctypes.c_int
+    lib.cwth_num_frames.argtypes = [i64, i32]
+    lib.cwth_num_frames.restype = i64
+    lib.cwth_status_string.argtypes = [ctypes.c_int]
+    lib.cwth_status_string.restype = ctypes.c_char_p
+    lib.cwth_plan_query.argtypes = [vp, ctypes.POINTER(PlanInfo)]
+    lib.cwth_plan_query.restype = ctypes.c_int
+    lib.cwth_plan_scale_paths.argtypes = [vp, ctypes.POINTER(i32)]
+    lib.cwth_plan_scale_paths.restype = ctypes.c_int
+    return lib
+
+
+_lib = load_library()
+
+
+def lib() -> ctypes.CDLL:
+    return _lib
+
+
+def _check(status: int, where: str):
+    if status != CWTH_OK:
+        raise CwthError(status, where)
+
+
+def num_frames(n: int, hop: int) -> int:
+    return int(_lib.cwth_num_frames(int(n), int(hop)))
+
+
+class Plan:
+    """A cwth_plan_t: scales (in samples), hop, Morlet B/C and the longest clip."""
+
+    def __init__(self, scales, hop: int, max_len: int, bandwidth: float = 1.5,
+                 center: float = 1.0, sample_rate: float = 16000.0,
+                 precision: str = "fp32", path: str = "auto"):
+        sc = np.ascontiguousarray(np.asarray(scales, dtype=np.float64).ravel())
+        self.scales = sc
+        self.hop = int(hop)
+        self.max_len = int(max_len)
+        self.S = int(sc.shape[0])
+        self._h = ctypes.c_void_p()
+        w = Morlet(float(bandwidth), float(center))
+        st = _lib.cwth_plan(ctypes.byref(w), sc.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                            self.S, self.hop, float(sample_rate), self.max_len,
+                            PREC[precision], PATH[path], ctypes.byref(self._h))
+        _check(st, "cwth_plan")
+        self.frames_max = num_frames(self.max_len, self.hop)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        inf = PlanInfo()
+        _check(_lib.cwth_plan_query(self._h, ctypes.byref(inf)), "cwth_plan_query")
+        return inf.as_dict()
+
+    def scale_paths(self) -> np.ndarray:
+        out = np.zeros(self.S, np.int32)
+        _check(_lib.cwth_plan_scale_paths(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))),
+               "cwth_plan_scale_paths")
+        return out
+
+    def execute(self, x, lengths=None, out=None, stream=None):
+        """Device batch ``x`` (torch float32 CUDA tensor [B, ld >= max_len]) ->
+        ``out`` [B, S, frames_max] float32 on the same device."""
+        import torch
+        if x.dim() == 1:
+            x = x.unsqueeze(0)
+        if x.dtype != torch.float32 or not x.is_cuda or x.stride(1) != 1:
+            raise ValueError("x must be a float32 CUDA tensor with unit column stride")
+        B = x.shape[0]
+        if out is None:
+            out = torch.empty((B, self.S, self.frames_max), dtype=torch.float32, device=x.device)
+        if lengths is not None and (lengths.dtype != torch.int64 or not lengths.is_cuda):
+            raise ValueError("lengths must be an int64 CUDA tensor")
+        if stream is None:
+            stream = torch.cuda.current_stream(x.device)
+        # A single row's stride is meaningless (size-1 dims may carry any stride).
+        ld = int(x.shape[1]) if B == 1 else int(x.stride(0))
+        st = _lib.cwth_execute(self._h, ctypes.c_void_p(x.data_ptr()), ld,
+                               ctypes.c_void_p(lengths.data_ptr() if lengths is not None else 0),
+                               int(B), ctypes.c_void_p(out.data_ptr()),
+                               ctypes.c_void_p(stream.cuda_stream))
+        _check(st, "cwth_execute")
+        return out
+
+    def execute_host(self, x, out, lengths=None, stream=None):
+        """Host batch (numpy or pinned torch CPU tensor, float32 [B, ld]) ->
+        host ``out`` [B, S, frames_max]; returns when ``out`` is filled."""
+        def ptr(a):
+            if a is None:
+                return 0
+            if hasattr(a, "data_ptr"):
+                return a.data_ptr()
+            return a.ctypes.data
+        B = x.shape[0]
+        if B == 1:
+            ld = x.shape[1]
+        else:
+            ld = x.stride(0) if hasattr(x, "stride") and callable(x.stride) else x.strides[0] // 4
+        s = 0
+        if stream is not None:
+            s = stream.cuda_stream
+        st = _lib.cwth_execute_host(self._h, ctypes.c_void_p(ptr(x)), int(ld),
+                                    ctypes.c_void_p(ptr(lengths)), int(B),
+                                    ctypes.c_void_p(ptr(out)), ctypes.c_void_p(s))
+        _check(st, "cwth_execute_host")
+        return out
+
+    def close(self):
+        if self._h:
+            _check(_lib.cwth_destroy(self._h), "cwth_destroy")
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

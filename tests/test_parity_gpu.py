@@ -1,0 +1,189 @@
+"""GPU parity: libcwth.so (through the C ABI) against the float64 oracle.
+
+Tolerance (float32 spectral path): max |err| <= 1e-5 * max|W| per clip, the
+normaliser taken over all scales and frames of that clip.  The oracle sees
+the same float32 samples the GPU sees, promoted to float64.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL_FP32 = 1e-5
+
+
+@pytest.fixture(scope="module")
+def cw():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2408_14302_gb300 import cwth
+    return cwth
+
+
+@pytest.fixture(scope="module")
+def sig():
+    from paper_2408_14302_gb300 import signals
+    return signals
+
+
+def rel_err(got, ref):
+    return float(np.max(np.abs(got - ref)) / np.max(ref))
+
+
+def run_gpu(cw, x, scales, hop, lengths=None, path="auto", precision="fp32", max_len=None,
+            fill=np.nan):
+    x = np.ascontiguousarray(np.atleast_2d(np.asarray(x, np.float32)))
+    max_len = x.shape[1] if max_len is None else max_len
+    with cw.Plan(scales, hop=hop, max_len=max_len, path=path, precision=precision) as plan:
+        xd = torch.from_numpy(x).cuda()
+        out = torch.full((x.shape[0], len(scales), plan.frames_max), float(fill),
+                         dtype=torch.float32, device="cuda")
+        ld = torch.from_numpy(np.asarray(lengths, np.int64)).cuda() if lengths is not None else None
+        plan.execute(xd, lengths=ld, out=out)
+        torch.cuda.synchronize()
+        return out.cpu().numpy().astype(np.float64), plan.info()
+
+
+def oracle_mag(x, scales, hop):
+    import oracle
+    return oracle.cwth_magnitude(np.asarray(x, np.float32).astype(np.float64), scales, hop)
+
+
+@pytest.mark.parametrize("hop", [64, 1])
+def test_tones_1s_32_scales(cw, sig, hop):
+    x = sig.tones_clip(seed=0, n=16000).astype(np.float32)
+    sc = sig.scales_for_band(100, 8000, 32, 16000.0)
+    got, info = run_gpu(cw, x, sc, hop)
+    ref = oracle_mag(x, sc, hop)
+    assert got.shape == (1, 32, ref.shape[1])
+    assert rel_err(got[0], ref) <= TOL_FP32, info
+
+
+@pytest.mark.parametrize("hop", [2, 8, 32, 128, 256, 512, 1024])
+def test_hops_ragged_tail(cw, sig, hop):
+    # 9000 samples: not a multiple of any of these hops (ragged last frame),
+    # several segments per clip.
+    x = sig.machine_clip(seed=5, n=9001, dtype=np.float32)
+    sc = sig.scales_for_band(50, 8000, 12, 16000.0)
+    got, info = run_gpu(cw, x, sc, hop)
+    ref = oracle_mag(x, sc, hop)
+    assert info["num_segments"] >= 1
+    assert rel_err(got[0], ref) <= TOL_FP32, info
+
+
+def test_machine_10s_64_scales_hop256_full_clips(cw, sig):
+    n, hop = 160000, 256
+    xs = np.stack([sig.machine_clip(1000 + i, n) for i in range(3)])
+    sc = sig.scales_for_band(50, 8000, 64, 16000.0)
+    got, info = run_gpu(cw, xs, sc, hop)
+    assert info["num_segments"] > 1
+    for i in range(3):
+        ref = oracle_mag(xs[i], sc, hop)
+        assert rel_err(got[i], ref) <= TOL_FP32
+
+
+def test_machine_batch64_sampled_rows(cw, sig):
+    """Full 64-clip batch in the benchmark's launch configuration; rows of a
+    few clips and scales are checked against the oracle one by one."""
+    n, hop, B = 160000, 256, 64
+    xs = sig.machine_batch(B, n)
+    sc = sig.scales_for_band(50, 8000, 64, 16000.0)
+    got, _ = run_gpu(cw, xs, sc, hop)
+    assert np.isfinite(got).all()
+    rng = np.random.default_rng(0)
+    for i in (0, 31, 63):
+        rows = np.sort(rng.choice(64, 6, replace=False))
+        ref = oracle_mag(xs[i], sc[rows], hop)
+        # normaliser: max|W| of the clip over all scales (largest scales dominate)
+        ref_full_max = max(float(ref.max()), float(oracle_mag(xs[i], sc[-4:], hop).max()))
+        err = float(np.max(np.abs(got[i, rows] - ref))) / ref_full_max
+        assert err <= TOL_FP32
+
+
+def test_ragged_lengths_and_untouched_tail(cw, sig):
+    hop, n = 64, 20000
+    lengths = [20000, 19999, 1, 0, 777, 64, 65, 12345]
+    xs = np.stack([sig.machine_clip(50 + i, n) for i in range(len(lengths))])
+    sc = sig.scales_for_band(50, 8000, 16, 16000.0)
+    got, _ = run_gpu(cw, xs, sc, hop, lengths=lengths, fill=-7.0)
+    for i, L in enumerate(lengths):
+        F = -(-L // hop)
+        assert np.all(got[i, :, F:] == -7.0), f"clip {i}: frames beyond ceil(len/H) written"
+        if L == 0:
+            continue
+        ref = oracle_mag(xs[i, :L], sc, hop)
+        assert rel_err(got[i, :, :F], ref) <= TOL_FP32, f"clip {i} (len {L})"
+
+
+def test_single_scale_small_and_large(cw, sig):
+    x = sig.tones_clip(seed=2, n=3000).astype(np.float32)
+    for sc in ([0.7], [2.0], [400.0], [1.1, 600.0]):
+        sc = np.asarray(sc)
+        got, _ = run_gpu(cw, x, sc, 16)
+        ref = oracle_mag(x, sc, 16)
+        assert rel_err(got[0], ref) <= TOL_FP32, sc
+
+
+def test_other_morlet_parameters(cw, sig):
+    import oracle
+    x = sig.tones_clip(seed=3, n=5000).astype(np.float32)
+    sc = sig.scales_for_band(100, 8000, 10, 16000.0)
+    for B, C in ((1.0, 1.5), (2.0, 0.8)):
+        with cw.Plan(sc, hop=32, max_len=5000, bandwidth=B, center=C) as plan:
+            out = plan.execute(torch.from_numpy(x).cuda().unsqueeze(0))
+            got = out[0].cpu().numpy().astype(np.float64)
+        ref = np.abs(oracle.cwth(x.astype(np.float64), sc, 32, bandwidth=B, center=C))
+        assert rel_err(got, ref) <= TOL_FP32
+
+
+def test_host_entry_point_matches_device(cw, sig):
+    n, hop = 30000, 128
+    xs = np.stack([sig.machine_clip(70 + i, n) for i in range(4)]).astype(np.float32)
+    sc = sig.scales_for_band(50, 8000, 20, 16000.0)
+    with cw.Plan(sc, hop=hop, max_len=n) as plan:
+        dev = plan.execute(torch.from_numpy(xs).cuda()).cpu().numpy()
+        hx = torch.from_numpy(xs).pin_memory()
+        hout = torch.empty((4, 20, plan.frames_max), dtype=torch.float32).pin_memory()
+        plan.execute_host(hx, hout)
+        assert np.array_equal(hout.numpy(), dev)
+        lens = np.array([n, 100, 0, 29999], np.int64)
+        hout2 = np.full((4, 20, plan.frames_max), -1.0, np.float32)
+        plan.execute_host(xs, hout2, lengths=lens)
+        for i, L in enumerate(lens):
+            F = -(-int(L) // hop)
+            assert np.all(hout2[i, :, F:] == -1.0)
+        assert np.array_equal(hout2[0], dev[0])
+
+
+def test_non_default_stream_and_two_plans(cw, sig):
+    n = 12000
+    x = torch.from_numpy(sig.machine_clip(9, n)).cuda().unsqueeze(0)
+    sc1 = sig.scales_for_band(50, 8000, 8, 16000.0)
+    sc2 = sig.scales_for_band(200, 4000, 5, 16000.0)
+    with cw.Plan(sc1, hop=64, max_len=n) as p1, cw.Plan(sc2, hop=32, max_len=n) as p2:
+        ref1 = p1.execute(x).clone()
+        ref2 = p2.execute(x).clone()
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            o1 = p1.execute(x)
+            o2 = p2.execute(x)
+        s.synchronize()
+        assert torch.equal(o1, ref1) and torch.equal(o2, ref2)
+
+
+def test_deterministic(cw, sig):
+    x = torch.from_numpy(sig.machine_batch(4, 40000)).cuda()
+    sc = sig.scales_for_band(50, 8000, 32, 16000.0)
+    with cw.Plan(sc, hop=256, max_len=40000) as plan:
+        a = plan.execute(x).clone()
+        b = plan.execute(x)
+        assert torch.equal(a, b)
+
+
+def test_unsupported_hop_for_spectral(cw):
+    with pytest.raises(cw.CwthError) as e:
+        cw.Plan([2.0, 5.0], hop=100, max_len=1000, path="spectral")
+    assert e.value.status == 4
