@@ -1,0 +1,414 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the hop-size CWT on GB300.
+
+Default workload: 64 machine-sound clips of 10 s at 16 kHz (float32, inputs
+resident in HBM), complex Morlet B = 1.5, C = 1.0, 64 scales with centre
+frequencies 50-8000 Hz, hop 256, float32 path.  One step = one cwth_execute
+over the batch.  The L2 is flushed (256 MiB write) before every timed step;
+each step is timed with CUDA events on the launching stream.
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the float64 CPU
+oracle instead (on rank 0 only; other ranks exit without work).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import math
+import os
+import statistics
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2408_14302_gb300 import signals  # noqa: E402
+
+METRIC = "audio-sec/s and scalogram GB/s at hop 256 vs hop 1; serving p50/p99 ms"
+UNIT = "audio-sec/s"
+WORKLOAD = "machine_10s_64clips_64scales_hop256"
+N_CLIPS, N_SAMPLES, FS, S, HOP, F_LO, F_HI = 64, 160000, 16000.0, 64, 256, 50.0, 8000.0
+B_MORLET, C_MORLET = 1.5, 1.0
+FLUSH_BYTES = 256 << 20
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """Samples SM clock, power and clock-event reasons through NVML (ctypes)
+    every few ms while running; falls back to nothing if NVML is absent."""
+
+    REASONS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap",
+               0x8: "hw_slowdown", 0x10: "sync_boost", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown",
+               0x100: "display_clock_setting"}
+
+    def __init__(self, device_index: int = 0, period_s: float = 0.005):
+        self.samples = []
+        self.period = period_s
+        self._stop = threading.Event()
+        self._thr = None
+        self.max_mhz = None
+        self.ok = False
+        try:
+            self.nvml = ctypes.CDLL("libnvidia-ml.so.1")
+            if self.nvml.nvmlInit_v2() != 0:
+                return
+            self.h = ctypes.c_void_p()
+            found = False
+            try:
+                import torch
+                uuid = str(torch.cuda.get_device_properties(device_index).uuid)
+                u = ("GPU-" + uuid) if not uuid.startswith("GPU-") else uuid
+                found = self.nvml.nvmlDeviceGetHandleByUUID(u.encode(), ctypes.byref(self.h)) == 0
+            except Exception:
+                found = False
+            if not found and self.nvml.nvmlDeviceGetHandleByIndex_v2(
+                    device_index, ctypes.byref(self.h)) != 0:
+                return
+            mx = ctypes.c_uint()
+            if self.nvml.nvmlDeviceGetMaxClockInfo(self.h, 1, ctypes.byref(mx)) == 0:
+                self.max_mhz = mx.value
+            self.ok = True
+        except OSError:
+            self.ok = False
+
+    def _one(self):
+        clk = ctypes.c_uint()
+        pw = ctypes.c_uint()
+        rs = ctypes.c_ulonglong()
+        self.nvml.nvmlDeviceGetClockInfo(self.h, 1, ctypes.byref(clk))
+        self.nvml.nvmlDeviceGetPowerUsage(self.h, ctypes.byref(pw))
+        fn = getattr(self.nvml, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            getattr(self.nvml, "nvmlDeviceGetCurrentClocksThrottleReasons")
+        fn(self.h, ctypes.byref(rs))
+        self.samples.append((clk.value, pw.value / 1000.0, rs.value))
+
+    def _loop(self):
+        while not self._stop.is_set():
+            try:
+                self._one()
+            except Exception:
+                return
+            time.sleep(self.period)
+
+    def start(self):
+        if self.ok:
+            self._thr = threading.Thread(target=self._loop, daemon=True)
+            self._thr.start()
+
+    def stop(self):
+        if self._thr:
+            self._stop.set()
+            self._thr.join()
+            if not self.samples:
+                try:
+                    self._one()
+                except Exception:
+                    pass
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": [], "samples": 0,
+                    "source": "nvml" if self.ok else "unavailable"}
+        mhz = [s[0] for s in self.samples]
+        bits = 0
+        for s in self.samples:
+            bits |= s[2]
+        reasons = [name for b, name in self.REASONS.items() if bits & b and b != 0x1]
+        return {"sm_mhz": statistics.median(mhz), "sm_max_mhz": self.max_mhz,
+                "reasons": reasons, "samples": len(self.samples),
+                "power_w_max": max(s[1] for s in self.samples), "source": "nvml"}
+
+
+# ------------------------------------------------------------------ workload
+def make_inputs(rank: int):
+    xs = signals.machine_batch(N_CLIPS, N_SAMPLES, FS, seed0=1000 + N_CLIPS * rank)
+    scales = signals.scales_for_band(F_LO, F_HI, S, FS, C_MORLET)
+    return xs, scales
+
+
+def smooth_at_least(v: int) -> int:
+    """Smallest 2^a 3^b 5^c >= v."""
+    best = None
+    p2 = 1
+    while p2 < 2 * v:
+        p3 = p2
+        while p3 < 2 * v:
+            p5 = p3
+            while p5 < 2 * v:
+                if p5 >= v and (best is None or p5 < best):
+                    best = p5
+                p5 *= 5
+            p3 *= 3
+        p2 *= 2
+    return best
+
+
+def algorithmic_flops_per_clip(scales, hop, n=N_SAMPLES):
+    """Conventional flop count of the method per clip (unsegmented form):
+    forward real FFT 2.5 M log2 M over the smallest 5-smooth multiple of the
+    hop M >= n + support, 4 flops per Morlet-band bin (complex x real multiply-accumulate),
+    5 P log2 P per inverse FFT (P = M / hop) and 4 per output magnitude."""
+    a_max = float(np.max(scales))
+    h = math.ceil(a_max * math.sqrt(B_MORLET * math.log(1e10)))
+    M = hop * smooth_at_least(-(-(n + h) // hop))
+    delta = math.sqrt(math.log(1e9) / (math.pi ** 2 * B_MORLET))
+    band = sum(math.ceil(M * (C_MORLET + delta) / a) - math.floor(M * (C_MORLET - delta) / a) + 1
+               for a in scales)
+    P = M // hop
+    F = -(-n // hop)
+    return (2.5 * M * math.log2(M) + 4.0 * band + len(scales) * 5.0 * P * math.log2(max(P, 2))
+            + 4.0 * len(scales) * F), M
+
+
+def fp32_peak_tflops(sm_mhz):
+    # 152 SMs x 128 FP32 lanes x 2 flops (FMA) per clock
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args, rank, world):
+    """The float64 oracle as it stands, one step = the whole 64-clip batch."""
+    if rank != 0:
+        return None
+    import oracle
+    oracle.build()
+    xs, scales = make_inputs(0)
+    xs = xs.astype(np.float64)
+    cores = oracle.max_threads()
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        for c in range(N_CLIPS):
+            oracle.cwth_magnitude(xs[c], scales, HOP)
+        t1 = time.perf_counter()
+        if i >= args.warmup:
+            times.append(t1 - t0)
+    sec = statistics.mean(times)
+    value = N_CLIPS * (N_SAMPLES / FS) / sec
+    sample = (f"the whole workload per step: {N_CLIPS} clips x 10 s, {S} scales, hop {HOP}, "
+              "float64 direct sum (OpenMP over frames)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded machine-sound generator standing in for MIMII)",
+            "config": {"workload": WORKLOAD, "clips": N_CLIPS, "clip_seconds": N_SAMPLES / FS,
+                       "fs": FS, "scales": S, "hop": HOP, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    return line
+
+
+def cpu_baseline(min_s: float = 3.0):
+    """The oracle on the host cores: whole 64-clip passes until min_s elapsed,
+    plus one clip at hop 1 for the hop-1 comparison."""
+    import oracle
+    oracle.build()
+    xs, scales = make_inputs(0)
+    xs = xs.astype(np.float64)
+    t0 = time.perf_counter()
+    passes = 0
+    while True:
+        for c in range(N_CLIPS):
+            oracle.cwth_magnitude(xs[c], scales, HOP)
+        passes += 1
+        if time.perf_counter() - t0 >= min_s or passes >= 20:
+            break
+    dt = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    oracle.cwth_magnitude(xs[0], scales, 1)
+    dt1 = time.perf_counter() - t1
+    return {"value": passes * N_CLIPS * (N_SAMPLES / FS) / dt, "unit": UNIT,
+            "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"{passes} pass(es) over the whole workload ({N_CLIPS} clips x 10 s, "
+                      f"{S} scales, hop {HOP}), float64 direct sum, OpenMP, {dt:.1f} s wall; "
+                      f"hop 1: one clip, {dt1:.1f} s",
+            "hop1_value": (N_SAMPLES / FS) / dt1}
+
+
+# ------------------------------------------------------------------ our arm
+def time_steps(torch, fn, steps, flush, stream):
+    """Per-step CUDA-event time on `stream` with an L2 flush before each step."""
+    evs = []
+    for i in range(steps):
+        flush.fill_(i & 0xFF)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        evs.append((e0, e1))
+    return evs
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2408_14302_gb300 import cwth
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    xs, scales = make_inputs(rank)
+    audio_s = N_CLIPS * N_SAMPLES / FS
+
+    plan = cwth.Plan(scales, hop=HOP, max_len=N_SAMPLES, bandwidth=B_MORLET, center=C_MORLET,
+                     sample_rate=FS, precision="fp32", path="auto")
+    info = plan.info()
+    x_d = torch.from_numpy(xs).to(dev)
+    out_d = torch.empty((N_CLIPS, S, plan.frames_max), dtype=torch.float32, device=dev)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        plan.execute(x_d, out=out_d, stream=stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local_rank)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    evs = time_steps(torch, step, args.steps, flush, stream)
+    torch.cuda.synchronize()
+    sampler.stop()
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    ms = statistics.mean(step_ms)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    clocks = sampler.summary()
+
+    # Hop 1 on the same batch (the comparison point of the metric).
+    hop1 = None
+    if not args.no_hop1:
+        p1 = cwth.Plan(scales, hop=1, max_len=N_SAMPLES, bandwidth=B_MORLET, center=C_MORLET,
+                       sample_rate=FS, precision="fp32", path="auto")
+        o1 = torch.empty((N_CLIPS, S, p1.frames_max), dtype=torch.float32, device=dev)
+        f1 = lambda: p1.execute(x_d, out=o1, stream=stream)  # noqa: E731
+        for _ in range(2):
+            f1()
+        torch.cuda.synchronize()
+        e1 = time_steps(torch, f1, max(2, min(args.steps, 5)), flush, stream)
+        torch.cuda.synchronize()
+        ms1 = statistics.mean(a.elapsed_time(b) for a, b in e1)
+        hop1 = {"ms_per_step": ms1, "audio_sec_per_s": world * audio_s / (ms1 * 1e-3),
+                "scalogram_gbs": world * o1.numel() * 4 / (ms1 * 1e-3) / 1e9,
+                "seg_len": p1.info()["seg_len"], "num_segments": p1.info()["num_segments"]}
+        del o1
+        p1.close()
+
+    # End to end through the public host entry point (pinned host buffers).
+    hx = torch.from_numpy(xs).pin_memory()
+    hout = torch.empty((N_CLIPS, S, plan.frames_max), dtype=torch.float32).pin_memory()
+    plan.execute_host(hx, hout, stream=stream)
+    e2e_steps = max(3, min(args.steps, 20))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        plan.execute_host(hx, hout, stream=stream)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+
+    pk, pk_kind = peaks()
+    flops_clip, m_unseg = algorithmic_flops_per_clip(scales, HOP)
+    flops_launch = flops_clip * N_CLIPS
+    sm_mhz = clocks.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
+    peak_alu = fp32_peak_tflops(pk.get("sm_max_mhz", 2070.0))
+    achieved = flops_launch / (statistics.mean(step_ms) * 1e-3) / 1e12
+    bytes_launch = N_CLIPS * (N_SAMPLES * 4 + S * plan.frames_max * 4)
+    hbm_achieved = bytes_launch / (statistics.mean(step_ms) * 1e-3) / 1e9
+    out_bytes = N_CLIPS * S * plan.frames_max * 4
+
+    line = {
+        "metric": METRIC, "value": world * audio_s / (ms * 1e-3), "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded machine-sound generator standing in for MIMII)",
+        "config": {"workload": WORKLOAD, "clips": N_CLIPS, "clip_seconds": N_SAMPLES / FS,
+                   "fs": FS, "scales": S, "f_lo_hz": F_LO, "f_hi_hz": F_HI, "hop": HOP,
+                   "morlet": [B_MORLET, C_MORLET], "path": "auto", "precision": "fp32",
+                   "l2": "flushed: 256 MiB write before every timed step",
+                   "seg_len": info["seg_len"], "num_segments": info["num_segments"],
+                   "num_spectral": info["num_spectral"], "num_direct": info["num_direct"]},
+        "scalogram_gbs": world * out_bytes / (ms * 1e-3) / 1e9,
+        "roofline": {"bound": "alu", "kernel": "spectral_segment_kernel",
+                     "achieved": achieved, "peak": peak_alu, "unit": "TFLOP/s",
+                     "frac": achieved / peak_alu, "traffic": None,
+                     "algorithmic_flops_per_launch": flops_launch,
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
+                     "hbm_view": {"algorithmic_bytes_per_launch": bytes_launch,
+                                  "achieved_gbs": hbm_achieved, "peak_gbs": pk["hbm_gbs"],
+                                  "frac": hbm_achieved / pk["hbm_gbs"],
+                                  "peak_source": pk_kind}},
+        "e2e": {"value": world * audio_s / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": int(hx.numel() * 4),
+                "d2h_bytes_per_step": int(hout.numel() * 4),
+                "ms_per_step": e2e_s * 1e3, "api": "cwth_execute_host (pinned host buffers)"},
+        "gpu_launches": args.steps * 1,
+        "clocks": clocks,
+        "hop1": hop1,
+    }
+    plan.close()
+    return line
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-hop1", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        return
+
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    line = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
