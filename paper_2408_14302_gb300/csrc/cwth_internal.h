@@ -12,8 +12,9 @@ namespace cwth {
 
 constexpr uint32_t kPlanMagic = 0xC0A7B17Eu;
 constexpr int kSpecThreads = 512;
-// Largest batched shared-memory FFT (complex points) one CTA performs.
-constexpr int kMaxFftPoints = 8192;
+// Largest batched shared-memory FFT (complex points) one CTA performs: at
+// most 16 points per thread per pass.
+constexpr int kMaxFftPoints = 16 * kSpecThreads;
 
 // Per-scale parameters of the spectral path (one entry per spectral scale).
 // The multiplier at unwrapped bin q_u is

@@ -20,14 +20,17 @@
 // spectrum sqrt(a) sum_m Psi(a(nu - m)) (Poisson summation of the sampled
 // Gaussian), so no complex multiplier is needed; bins q > M/2 come from
 // conj(X[M - q]) because x is real.
+//
+// Shared-memory layouts: buffers are in natural order between phases.  The
+// FFT passes in between write an XOR-swizzled order (element i lives at
+// i ^ ((i >> 4) & 15)), which spreads every Stockham write stride over all
+// banks; the last pass writes natural order again.
 #include "cwth_internal.h"
 
 namespace cwth {
 namespace {
 
-// Shared-memory index with one float2 of padding every 32 entries, so that
-// strided Stockham writes spread over the banks.
-__device__ __forceinline__ int spad(int i) { return i + (i >> 5); }
+__device__ __forceinline__ int lay(int i, bool swz) { return swz ? (i ^ ((i >> 4) & 15)) : i; }
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
@@ -89,16 +92,40 @@ struct Dft<8, INV> {
     }
 };
 
+// Multiplies v[r] by w^r, w = exp(-+ 2 pi i k / (Ns R)) = tw[k * tstride]
+// (conjugated for the inverse).  The powers come from a product tree of
+// depth <= 3, a few roundings each (~3e-7 relative).
+template <int R, bool INV>
+__device__ __forceinline__ void twiddle(float2* v, const float2* __restrict__ tw, int idx) {
+    float2 w1 = __ldg(&tw[idx]);
+    if (INV) w1.y = -w1.y;
+    v[1] = cmul(v[1], w1);
+    if (R >= 4) {
+        const float2 w2 = cmul(w1, w1);
+        v[2] = cmul(v[2], w2);
+        v[3] = cmul(v[3], cmul(w2, w1));
+        if (R >= 8) {
+            const float2 w4 = cmul(w2, w2);
+            v[4] = cmul(v[4], w4);
+            v[5] = cmul(v[5], cmul(w4, w1));
+            v[6] = cmul(v[6], cmul(w4, w2));
+            v[7] = cmul(v[7], cmul(w4, cmul(w2, w1)));
+        }
+    }
+}
+
 // One Stockham autosort pass over `nbatch` independent transforms of length
 // L (a power of two) stored back to back in `buf`.  Ns is the length of the
 // sub-transforms already done; each butterfly j reads R points spaced L/R
 // apart, multiplies point r by w^{r*k} (k = j mod Ns, w = exp(-+2 pi i /
 // (Ns R))), does a length-R DFT and writes the points spaced Ns apart at
 // (j - k) R + k.  All reads finish before any write (barrier), so the pass
-// runs in place.  tstride is the twiddle-table step for one unit of r*k.
+// runs in place; rs / ws select the layout read and written.  tstride is
+// the twiddle-table step for one unit of r*k.
 template <int R, int MAXB, bool INV>
 __device__ __forceinline__ void fft_pass(float2* __restrict__ buf, int L, int nbatch, int Ns,
-                                         const float2* __restrict__ tw, int tstride) {
+                                         const float2* __restrict__ tw, int tstride, bool rs,
+                                         bool ws) {
     const int LR = L / R;
     const int lg_lr = __ffs(LR) - 1;
     const int nb = nbatch * LR;
@@ -109,18 +136,11 @@ __device__ __forceinline__ void fft_pass(float2* __restrict__ buf, int L, int nb
         if (j < nb) {
             const int b = j >> lg_lr;
             const int jj = j & (LR - 1);
-            const int base = b * L;
+            const int base = b * L + jj;
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[u][r] = buf[lay(base + r * LR, rs)];
             const int k = jj & (Ns - 1);
-#pragma unroll
-            for (int r = 0; r < R; ++r) v[u][r] = buf[spad(base + jj + r * LR)];
-            if (Ns > 1) {
-#pragma unroll
-                for (int r = 1; r < R; ++r) {
-                    float2 w = __ldg(&tw[r * k * tstride]);
-                    if (INV) w.y = -w.y;
-                    v[u][r] = cmul(v[u][r], w);
-                }
-            }
+            if (Ns > 1) twiddle<R, INV>(v[u], tw, k * tstride);
             Dft<R, INV>::run(v[u]);
         }
     }
@@ -131,11 +151,10 @@ __device__ __forceinline__ void fft_pass(float2* __restrict__ buf, int L, int nb
         if (j < nb) {
             const int b = j >> lg_lr;
             const int jj = j & (LR - 1);
-            const int base = b * L;
             const int k = jj & (Ns - 1);
-            const int d = base + (jj - k) * R + k;
+            const int d = b * L + (jj - k) * R + k;
 #pragma unroll
-            for (int r = 0; r < R; ++r) buf[spad(d + r * Ns)] = v[u][r];
+            for (int r = 0; r < R; ++r) buf[lay(d + r * Ns, ws)] = v[u][r];
         }
     }
     __syncthreads();
@@ -143,48 +162,107 @@ __device__ __forceinline__ void fft_pass(float2* __restrict__ buf, int L, int nb
 
 template <int R, bool INV>
 __device__ __forceinline__ void fft_pass_dispatch(float2* buf, int L, int nbatch, int Ns,
-                                                  const float2* tw, int tstride) {
+                                                  const float2* tw, int tstride, bool rs, bool ws) {
     const int nb = nbatch * (L / R);
     const int per = (nb + blockDim.x - 1) / blockDim.x;
-    // Up to 16 complex values per thread: the caller keeps nbatch * L <= 8192
-    // with 512 threads.
+    // Up to 16 complex values per thread: the caller keeps nbatch * L <=
+    // kMaxFftPoints = 16 * kSpecThreads.
     constexpr int kMaxB = 16 / R;
     if (per <= 1)
-        fft_pass<R, 1, INV>(buf, L, nbatch, Ns, tw, tstride);
+        fft_pass<R, 1, INV>(buf, L, nbatch, Ns, tw, tstride, rs, ws);
     else if (per <= 2)
-        fft_pass<R, 2, INV>(buf, L, nbatch, Ns, tw, tstride);
+        fft_pass<R, 2, INV>(buf, L, nbatch, Ns, tw, tstride, rs, ws);
     else if (per <= 4 || kMaxB <= 4)
-        fft_pass<R, (kMaxB < 4 ? kMaxB : 4), INV>(buf, L, nbatch, Ns, tw, tstride);
+        fft_pass<R, (kMaxB < 4 ? kMaxB : 4), INV>(buf, L, nbatch, Ns, tw, tstride, rs, ws);
     else
-        fft_pass<R, kMaxB, INV>(buf, L, nbatch, Ns, tw, tstride);
+        fft_pass<R, kMaxB, INV>(buf, L, nbatch, Ns, tw, tstride, rs, ws);
 }
 
-// Batched power-of-two FFT in shared memory (natural order in and out).
+// Batched power-of-two FFT in shared memory, natural order in and out.
 // ts = M / L maps the transform's twiddles onto the table of exp(-2 pi i m/M).
 // Radices: 8 where possible, a leading 4 (or 4,4) for the remainder of log2 L.
 template <bool INV>
-__device__ __noinline__ void fft_block(float2* buf, int L, int nbatch, const float2* tw, int ts) {
-    const int e = __ffs(L) - 1;
-    int n4 = 0;
-    // L >= 8 here: the plan keeps P = M / H >= 8 and M / 2 >= 256.
-    if (e % 3 == 1) n4 = 2;
-    if (e % 3 == 2) n4 = 1;
+__device__ __forceinline__ void fft_block(float2* buf, int L, int nbatch, const float2* tw, int ts) {
+    const int e = __ffs(L) - 1;  // L >= 8: the plan keeps P = M/H >= 8 and M/2 >= 256
+    const int n4 = (e % 3 == 1) ? 2 : (e % 3 == 2) ? 1 : 0;
+    const int npass = n4 + (e - 2 * n4) / 3;
     int Ns = 1;
-    for (int i = 0; i < n4; ++i) {
-        fft_pass_dispatch<4, INV>(buf, L, nbatch, Ns, tw, ts * (L / (Ns * 4)));
-        Ns *= 4;
+    for (int i = 0; i < npass; ++i) {
+        const bool rs = i > 0, ws = i + 1 < npass;
+        if (i < n4) {
+            fft_pass_dispatch<4, INV>(buf, L, nbatch, Ns, tw, ts * (L / (Ns * 4)), rs, ws);
+            Ns *= 4;
+        } else {
+            fft_pass_dispatch<8, INV>(buf, L, nbatch, Ns, tw, ts * (L / (Ns * 8)), rs, ws);
+            Ns *= 8;
+        }
     }
-    while (Ns < L) {
-        fft_pass_dispatch<8, INV>(buf, L, nbatch, Ns, tw, ts * (L / (Ns * 8)));
-        Ns *= 8;
+}
+
+__device__ __forceinline__ float fast_exp2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Sum of X[q] * exp2(kexp * (qf * a_over_m - C)^2) over n bins of one run:
+// indices q0, q0 + dq, ... (dq = +-P) and unwrapped bin positions qf,
+// qf + P, ... .  ex2.approx has ~2^-22 relative error; the argument is
+// formed from the exact bin position, so errors do not accumulate.
+__device__ __forceinline__ float2 fold_run(const float2* __restrict__ X, int q0, int dq, int n,
+                                           float qf, float pf, float a_over_m, float cneg,
+                                           float kexp) {
+    float2 acc = make_float2(0.f, 0.f);
+    const float2* xp = X + q0;
+#pragma unroll 4
+    for (int j = 0; j < n; ++j) {
+        const float2 v = *xp;
+        xp += dq;
+        const float u = fmaf(qf, a_over_m, cneg);
+        qf += pf;
+        const float g = fast_exp2(kexp * u * u);
+        acc.x = fmaf(v.x, g, acc.x);
+        acc.y = fmaf(v.y, g, acc.y);
     }
+    return acc;
+}
+
+// Z[r] = gscale * sum over the unwrapped band [q_lo, q_hi] of the bins
+// q_u = r (mod P) of X[q_u mod M] * Psi-weight; bins above M/2 are read as
+// conj(X[M - q]).  The walk is split into runs that stay on one side of M/2,
+// so the inner loop is branch-free.
+__device__ __forceinline__ float2 fold_residue(const float2* __restrict__ X, const SpecScale& sc,
+                                               int r, int M, int Mh, int P, int lgP, float cneg,
+                                               float kexp) {
+    int qu = sc.q_lo + ((r - sc.q_lo) & (P - 1));
+    int left = qu <= sc.q_hi ? ((sc.q_hi - qu) >> lgP) + 1 : 0;
+    const float pf = (float)P;
+    float2 ad = make_float2(0.f, 0.f), am = make_float2(0.f, 0.f);
+    while (left > 0) {
+        const int q = qu & (M - 1);
+        int n;
+        if (q <= Mh) {
+            n = min(left, ((Mh - q) >> lgP) + 1);
+            const float2 t = fold_run(X, q, P, n, (float)qu, pf, sc.a_over_m, cneg, kexp);
+            ad.x += t.x;
+            ad.y += t.y;
+        } else {
+            n = min(left, ((M - 1 - q) >> lgP) + 1);
+            const float2 t = fold_run(X, M - q, -P, n, (float)qu, pf, sc.a_over_m, cneg, kexp);
+            am.x += t.x;
+            am.y += t.y;
+        }
+        qu += n * P;
+        left -= n;
+    }
+    return make_float2(sc.gscale * (ad.x + am.x), sc.gscale * (ad.y - am.y));
 }
 
 __global__ void __launch_bounds__(kSpecThreads, 1) spectral_segment_kernel(const SpecLaunch p) {
     extern __shared__ float2 smem[];
     const int M = p.M, Mh = M >> 1, P = p.P;
-    float2* X = smem;                  // spad(Mh) + 1 used
-    float2* Z = smem + spad(Mh) + 2;   // spad(nconc * P - 1) + 1 used
+    float2* X = smem;            // Mh + 1 used
+    float2* Z = smem + Mh + 2;   // nconc * P used
 
     const int seg = blockIdx.x, clip = blockIdx.y, grp = blockIdx.z;
     int64_t len = p.lengths ? p.lengths[clip] : p.max_len;
@@ -202,7 +280,7 @@ __global__ void __launch_bounds__(kSpecThreads, 1) spectral_segment_kernel(const
         const int64_t i0 = s0 + 2 * (int64_t)n;
         const float a = (i0 >= 0 && i0 < len) ? __ldg(xr + i0) : 0.f;
         const float b = (i0 + 1 >= 0 && i0 + 1 < len) ? __ldg(xr + i0 + 1) : 0.f;
-        X[spad(n)] = make_float2(a, b);
+        X[n] = make_float2(a, b);
     }
     __syncthreads();
 
@@ -215,15 +293,15 @@ __global__ void __launch_bounds__(kSpecThreads, 1) spectral_segment_kernel(const
     // Each pair (q, Mh-q) is read and written by one thread only.
     for (int q = threadIdx.x; q <= (Mh >> 1); q += blockDim.x) {
         const int qm = (Mh - q) & (Mh - 1);
-        const float2 zq = X[spad(q)];
-        const float2 zm = X[spad(qm)];
+        const float2 zq = X[q];
+        const float2 zm = X[qm];
         const float2 E = make_float2(0.5f * (zq.x + zm.x), 0.5f * (zq.y - zm.y));
         const float2 O = make_float2(0.5f * (zq.y + zm.y), 0.5f * (zm.x - zq.x));
         const float2 t = cmul(__ldg(&p.tw[q]), O);
         const float2 xq = cadd(E, t);
         const float2 xm = csub(E, t);
-        X[spad(q)] = xq;
-        X[spad(Mh - q)] = make_float2(xm.x, -xm.y);
+        X[q] = xq;
+        X[Mh - q] = make_float2(xm.x, -xm.y);
     }
     __syncthreads();
 
@@ -236,28 +314,20 @@ __global__ void __launch_bounds__(kSpecThreads, 1) spectral_segment_kernel(const
 
         // a3: band multiply + hop fold.  Lane = residue r; one item = 32
         // consecutive residues of one scale; the loop walks the unwrapped band.
-        for (int it = warp; it < nc * strips; it += nwarps) {
-            const int c = it / strips;
-            const int r = ((it - c * strips) << 5) + lane;
+        // Items are ordered by decreasing band width (scales ascend); they
+        // are dealt to warps in a snake order to balance the work.
+        const int nitems = nc * strips;
+        const int lgP = __ffs(P) - 1;
+        const int lgS = __ffs(strips) - 1;
+        const float cneg = -p.center;
+        for (int round = 0;; ++round) {
+            const int it = round * nwarps + ((round & 1) ? nwarps - 1 - warp : warp);
+            if (it >= nitems) break;
+            const int c = it >> lgS;
+            const int r = ((it - (c << lgS)) << 5) + lane;
             if (r >= P) continue;
             const SpecScale sc = p.sc[c0 + c];
-            int qu = sc.q_lo + ((r - sc.q_lo) & (P - 1));
-            float2 acc = make_float2(0.f, 0.f);
-            for (; qu <= sc.q_hi; qu += P) {
-                const int q = qu & (M - 1);
-                float2 v;
-                if (q <= Mh) {
-                    v = X[spad(q)];
-                } else {
-                    v = X[spad(M - q)];
-                    v.y = -v.y;
-                }
-                const float arg = fmaf((float)qu, sc.a_over_m, -p.center);
-                const float g = sc.gscale * exp2f(p.kexp * arg * arg);
-                acc.x = fmaf(v.x, g, acc.x);
-                acc.y = fmaf(v.y, g, acc.y);
-            }
-            Z[spad(c * P + r)] = acc;
+            Z[c * P + r] = fold_residue(X, sc, r, M, Mh, P, lgP, cneg, p.kexp);
         }
         __syncthreads();
 
@@ -271,7 +341,7 @@ __global__ void __launch_bounds__(kSpecThreads, 1) spectral_segment_kernel(const
             const int f = i - c * Fs;
             const int64_t k = k0 + f;
             if (k < F) {
-                const float2 w = Z[spad(c * P + p.kp0 + f)];
+                const float2 w = Z[c * P + p.kp0 + f];
                 const int row = p.sc[c0 + c].row;
                 p.out[((int64_t)clip * p.S_total + row) * p.frames_max + k] =
                     sqrtf(fmaf(w.x, w.x, w.y * w.y));
@@ -294,10 +364,7 @@ __global__ void twiddle_kernel(float2* tw, int M) {
 }  // namespace
 
 size_t spectral_smem_bytes(int M, int P, int nconc) {
-    auto pad = [](long i) { return i + (i >> 5); };
-    const long x = pad(M / 2) + 2;
-    const long z = pad((long)nconc * P - 1) + 1;
-    return (size_t)(x + z) * sizeof(float2);
+    return (size_t)(M / 2 + 2 + (long)nconc * P) * sizeof(float2);
 }
 
 cudaError_t spectral_prepare_device() {
