@@ -139,6 +139,12 @@ int64_t cwth_num_frames(int64_t n, int32_t hop);
 /* Static, human-readable name of a status code. */
 const char *cwth_status_string(cwth_status s);
 
+/* Detail of the most recent CUDA or driver failure seen by this library in
+ * the calling thread (CUDA error name and text, or which request the driver
+ * rejected); "" if none.  The string stays valid until the thread's next
+ * failing call. */
+const char *cwth_last_error(void);
+
 /* What a plan decided, for tests and benchmarks. */
 typedef struct {
     int32_t num_scales;        /* S                                            */
@@ -159,6 +165,12 @@ typedef struct {
 
 /* Fill *info.  Errors: CWTH_ERR_BAD_PLAN, CWTH_ERR_INVALID_ARG (NULL info). */
 cwth_status cwth_plan_query(cwth_plan_t plan, cwth_plan_info *info);
+
+/* Wait for the work enqueued on `stream` and report device-side errors of
+ * this plan: CWTH_ERR_TIMEOUT if one of its kernels gave up a bounded wait
+ * (the flag is then cleared), CWTH_ERR_CUDA if the stream reported a fault.
+ * Errors: CWTH_ERR_BAD_PLAN. */
+cwth_status cwth_sync(cwth_plan_t plan, void *stream);
 
 /* Per-scale path decision: paths[s] = CWTH_PATH_SPECTRAL or CWTH_PATH_DIRECT
  * for s < S (host array of S entries). */

@@ -1,9 +1,11 @@
 // C ABI of libcwth.so: argument checking, planning, launches (include/cwth.h).
 #include <math.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "cwth_internal.h"
@@ -23,6 +25,10 @@ constexpr size_t kSmemCap = 227 * 1024;
 // Preferred ceiling, so that two CTAs fit on one SM.
 constexpr size_t kSmemTwoPerSm = 112 * 1024;
 constexpr int kNumSms = 152;
+// Direct path: taps below this fraction of the wavelet peak are dropped.
+constexpr double kEpsDirect = 1e-9;
+// Largest padded tap count the direct path accepts.
+constexpr int kMaxDirectTaps = 4096;
 
 bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
 int ilog2(int64_t v) {
@@ -33,8 +39,16 @@ int ilog2(int64_t v) {
 
 bool valid_plan(const cwth_plan_s* p) { return p && p->magic == cwth::kPlanMagic; }
 
+thread_local char g_last_error[256] = "";
+
+void note_error(const char* what) {
+    snprintf(g_last_error, sizeof(g_last_error), "%s", what);
+}
+
 cwth_status cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return CWTH_OK;
+    snprintf(g_last_error, sizeof(g_last_error), "%s: %s", cudaGetErrorName(e),
+             cudaGetErrorString(e));
     if (e == cudaErrorMemoryAllocation) return CWTH_ERR_OOM;
     return CWTH_ERR_CUDA;
 }
@@ -104,11 +118,193 @@ void free_plan_memory(cwth_plan_s* p) {
     cudaFree(p->d_stage_x);
     cudaFree(p->d_stage_out);
     cudaFree(p->d_stage_len);
+    for (auto& g : p->groups) {
+        cudaFree(g.d_rows);
+        cudaFree(g.d_h);
+        cudaFree(g.d_scales);
+        g.d_rows = nullptr;
+        g.d_h = nullptr;
+        g.d_scales = nullptr;
+    }
+    cudaFree(p->d_bank_hi);
+    cudaFree(p->d_bank_lo);
+    cudaFree(p->d_bank_f32);
+    cudaFree(p->d_status);
+    cudaFree(p->d_xhi);
+    cudaFree(p->d_xlo);
+    p->d_bank_hi = nullptr;
+    p->d_bank_lo = nullptr;
+    p->d_bank_f32 = nullptr;
+    p->d_status = nullptr;
+    p->d_xhi = nullptr;
+    p->d_xlo = nullptr;
     p->d_tw = nullptr;
     p->d_sp = nullptr;
     p->d_stage_x = nullptr;
     p->d_stage_out = nullptr;
     p->d_stage_len = nullptr;
+}
+
+int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+// Half support of the direct path's truncated taps, a multiple of 8 so that
+// every group's view of the staged signal starts 16-byte aligned.
+int32_t direct_half_support(double a, double B) {
+    return (int32_t)round_up((int64_t)ceil(a * sqrt(B * log(1.0 / kEpsDirect))), 8);
+}
+
+bool direct_eligible(const cwth_plan_s& p, double a) {
+    const int64_t k = round_up(2 * (int64_t)direct_half_support(a, p.B) + 1, 64);
+    if (k > kMaxDirectTaps) return false;
+    if (p.precision != CWTH_PREC_FP32 && p.hop % 8 != 0) return false;
+    return true;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)ptr;
+    }
+    return fn;
+}
+
+// 2-D bf16 tensor map: dims {inner, outer}, row stride in bytes, box {64, box_outer},
+// 128-byte swizzle, zero fill out of bounds.
+bool encode_bf16_2d(CUtensorMap* map, const void* base, uint64_t inner, uint64_t outer,
+                    uint64_t row_stride_bytes, uint32_t box_outer) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {inner, outer};
+    const cuuint64_t strides[1] = {row_stride_bytes};
+    const cuuint32_t box[2] = {64, box_outer};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides,
+              box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
+}
+
+// Groups of consecutive (support-sorted) direct scales minimising the padded
+// GEMM volume sum(ncols * k_pad) plus a per-group cost for re-reading the
+// frame tiles; at most 128 scales (256 columns) per group.
+std::vector<std::pair<int, int>> group_scales(const std::vector<int32_t>& h_sorted) {
+    const int n = (int)h_sorted.size();
+    std::vector<double> best(n + 1, 1e300);
+    std::vector<int> from(n + 1, 0);
+    best[0] = 0;
+    for (int j = 1; j <= n; ++j) {
+        for (int i = std::max(0, j - 128); i < j; ++i) {
+            const double ncols = (double)round_up(2 * (j - i), 16);
+            const double kp = (double)round_up(2 * (int64_t)h_sorted[j - 1] + 1, 64);
+            const double c = best[i] + (ncols + 64.0) * kp;
+            if (c < best[j]) {
+                best[j] = c;
+                from[j] = i;
+            }
+        }
+    }
+    std::vector<std::pair<int, int>> g;
+    for (int j = n; j > 0; j = from[j]) g.push_back({from[j], j});
+    std::reverse(g.begin(), g.end());
+    return g;
+}
+
+cwth_status build_direct(cwth_plan_s* p) {
+    std::vector<int> idx;
+    for (int s = 0; s < p->S; ++s)
+        if (p->scale_path[s] == CWTH_PATH_DIRECT) idx.push_back(s);
+    p->n_dir = (int32_t)idx.size();
+    if (p->n_dir == 0) return CWTH_OK;
+    std::stable_sort(idx.begin(), idx.end(),
+                     [&](int a, int b) { return p->scales[a] < p->scales[b]; });
+    std::vector<int32_t> hs(idx.size());
+    for (size_t i = 0; i < idx.size(); ++i) hs[i] = direct_half_support(p->scales[idx[i]], p->B);
+    const auto ranges = group_scales(hs);
+    const bool split = p->precision == CWTH_PREC_BF16X2;
+    int64_t bank_elems = 0, f32_elems = 0;
+    for (auto& r : ranges) {
+        cwth::DirGroup g;
+        g.n_scales = r.second - r.first;
+        g.ncols = (int32_t)round_up(2 * g.n_scales, 16);
+        g.h = hs[r.second - 1];
+        g.k_pad = (int32_t)round_up(2 * (int64_t)g.h + 1, 64);
+        g.bank_off = bank_elems;
+        g.f32_off = f32_elems;
+        g.stages = cwth::direct_max_stages(g.ncols, split);
+        if (g.stages == 0) return CWTH_ERR_UNSUPPORTED;
+        bank_elems += (int64_t)g.ncols * g.k_pad;
+        f32_elems += (int64_t)g.n_scales * g.k_pad;
+        p->groups.push_back(g);
+        p->dir_taps = std::max(p->dir_taps, g.k_pad);
+        p->dir_front = std::max(p->dir_front, g.h);
+    }
+    cudaError_t e = cudaMalloc(&p->d_bank_hi, sizeof(__nv_bfloat16) * bank_elems);
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_bank_lo, sizeof(__nv_bfloat16) * bank_elems);
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_bank_f32, sizeof(float2) * f32_elems);
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int));
+    if (e != cudaSuccess) return cuda_status(e);
+    p->table_bytes += (int64_t)(bank_elems * 4 + f32_elems * 8);
+    for (size_t gi = 0; gi < ranges.size(); ++gi) {
+        cwth::DirGroup& g = p->groups[gi];
+        std::vector<int32_t> rows, hh;
+        std::vector<double> sc;
+        for (int i = ranges[gi].first; i < ranges[gi].second; ++i) {
+            rows.push_back(idx[i]);
+            hh.push_back(hs[i]);
+            sc.push_back(p->scales[idx[i]]);
+        }
+        e = cudaMalloc(&g.d_rows, sizeof(int32_t) * rows.size());
+        if (e == cudaSuccess) e = cudaMalloc(&g.d_h, sizeof(int32_t) * hh.size());
+        if (e == cudaSuccess) e = cudaMalloc(&g.d_scales, sizeof(double) * sc.size());
+        if (e == cudaSuccess)
+            e = cudaMemcpy(g.d_rows, rows.data(), sizeof(int32_t) * rows.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(g.d_h, hh.data(), sizeof(int32_t) * hh.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(g.d_scales, sc.data(), sizeof(double) * sc.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cwth::direct_make_bank(g.d_scales, g.d_h, g.n_scales, g.ncols, g.k_pad, g.h, p->B,
+                                       p->C, p->d_bank_hi + g.bank_off, p->d_bank_lo + g.bank_off,
+                                       p->d_bank_f32 + g.f32_off, 0);
+        if (e != cudaSuccess) return cuda_status(e);
+        if (p->precision != CWTH_PREC_FP32) {
+            if (!encode_bf16_2d(&g.map_b_hi, p->d_bank_hi + g.bank_off, g.k_pad, g.ncols,
+                                (uint64_t)g.k_pad * 2, g.ncols) ||
+                !encode_bf16_2d(&g.map_b_lo, p->d_bank_lo + g.bank_off, g.k_pad, g.ncols,
+                                (uint64_t)g.k_pad * 2, g.ncols)) {
+                note_error("cuTensorMapEncodeTiled rejected the tap-bank tensor map");
+                return CWTH_ERR_UNSUPPORTED;
+            }
+        }
+    }
+    if (p->precision != CWTH_PREC_FP32) {
+        // The frame matrix is a view with overlapping rows (row stride = hop):
+        // check once that the driver accepts it.
+        CUtensorMap probe;
+        const int64_t rows = 1024;
+        if (!encode_bf16_2d(&probe, p->d_bank_hi, p->dir_taps, rows, (uint64_t)p->hop * 2, 128)) {
+            note_error("cuTensorMapEncodeTiled rejected the overlapping frame view");
+            return CWTH_ERR_UNSUPPORTED;
+        }
+        e = cwth::direct_prepare_device();
+    } else {
+        e = cwth::direct_prepare_f32((size_t)(2 * p->dir_front + 1) * sizeof(float2));
+    }
+    if (e != cudaSuccess) return cuda_status(e);
+    return cuda_status(cudaDeviceSynchronize());
 }
 
 cwth_status build_spectral(cwth_plan_s* p) {
@@ -199,6 +395,96 @@ cwth_status launch_spectral(const cwth_plan_s* p, const float* d_x, int64_t ld_x
     return cuda_status(cwth::spectral_launch(L, p->n_seg, batch, n_groups, smem, st));
 }
 
+cwth_status launch_direct(cwth_plan_s* p, const float* d_x, int64_t ld_x, const int64_t* d_len,
+                          int32_t batch, float* d_out, cudaStream_t st) {
+    if (p->n_dir == 0 || batch == 0) return CWTH_OK;
+    cwth::DirLaunch L;
+    memset(&L, 0, sizeof(L));
+    L.out = d_out;
+    L.frames_max = p->frames_max;
+    L.S_total = p->S;
+    L.hop = p->hop;
+    L.lengths = d_len;
+    L.max_len = p->max_len;
+    L.batch = batch;
+    L.status = p->d_status;
+    if (p->precision == CWTH_PREC_FP32) {
+        for (auto& g : p->groups) {
+            L.ncols = g.ncols;
+            L.k_pad = g.k_pad;
+            L.h_group = g.h;
+            L.n_scales = g.n_scales;
+            L.rows = g.d_rows;
+            cudaError_t e = cwth::direct_launch_f32(d_x, ld_x, p->d_bank_f32 + g.f32_off, g.d_h, L, st);
+            if (e != cudaSuccess) return cuda_status(e);
+        }
+        return CWTH_OK;
+    }
+    const bool split = p->precision == CWTH_PREC_BF16X2;
+    const int64_t hop = p->hop;
+    const int64_t rows_per_clip =
+        (2 * (int64_t)p->dir_front + p->frames_max * hop + p->dir_taps + hop - 1) / hop;
+    const int64_t lpad = rows_per_clip * hop;
+    const int64_t total_rows = (int64_t)batch * rows_per_clip;
+    const int64_t total = (int64_t)batch * lpad + p->dir_front + p->dir_taps + 64;
+    if (total_rows > (int64_t(1) << 31) - 256) return CWTH_ERR_UNSUPPORTED;
+    if ((size_t)total > p->x_elems) {
+        cudaFree(p->d_xhi);
+        cudaFree(p->d_xlo);
+        p->d_xhi = nullptr;
+        p->d_xlo = nullptr;
+        p->x_elems = 0;
+        p->x_maps_ptr = nullptr;
+        cudaError_t e = cudaMalloc(&p->d_xhi, sizeof(__nv_bfloat16) * (size_t)total);
+        if (e == cudaSuccess) e = cudaMalloc(&p->d_xlo, sizeof(__nv_bfloat16) * (size_t)total);
+        if (e != cudaSuccess) return cuda_status(e);
+        p->x_elems = (size_t)total;
+    }
+    if (p->x_maps_ptr != p->d_xhi || p->x_maps_rows != total_rows) {
+        p->maps_a_hi.assign(p->groups.size(), CUtensorMap());
+        p->maps_a_lo.assign(p->groups.size(), CUtensorMap());
+        for (size_t gi = 0; gi < p->groups.size(); ++gi) {
+            const cwth::DirGroup& g = p->groups[gi];
+            const int64_t off = p->dir_front - g.h;
+            if (!encode_bf16_2d(&p->maps_a_hi[gi], p->d_xhi + off, g.k_pad, total_rows, hop * 2, 128) ||
+                !encode_bf16_2d(&p->maps_a_lo[gi], p->d_xlo + off, g.k_pad, total_rows, hop * 2, 128)) {
+                note_error("cuTensorMapEncodeTiled rejected the frame-matrix tensor map");
+                return CWTH_ERR_UNSUPPORTED;
+            }
+        }
+        p->x_maps_ptr = p->d_xhi;
+        p->x_maps_rows = total_rows;
+    }
+    cudaError_t e = cwth::direct_stage(d_x, ld_x, d_len, p->max_len, batch, p->d_xhi,
+                                       split ? p->d_xlo : nullptr, lpad, p->dir_front, total, st);
+    if (e != cudaSuccess) return cuda_status(e);
+    L.rows_per_clip = rows_per_clip;
+    L.total_rows = total_rows;
+    for (size_t gi = 0; gi < p->groups.size(); ++gi) {
+        const cwth::DirGroup& g = p->groups[gi];
+        CUtensorMap maps[4] = {p->maps_a_hi[gi], p->maps_a_lo[gi], g.map_b_hi, g.map_b_lo};
+        L.ncols = g.ncols;
+        L.k_pad = g.k_pad;
+        L.h_group = g.h;
+        L.n_scales = g.n_scales;
+        L.rows = g.d_rows;
+        L.stages = g.stages;
+        uint32_t tc = 32;
+        while (tc < (uint32_t)g.ncols) tc <<= 1;
+        L.tmem_cols = tc;
+        e = cwth::direct_launch_mma(maps, L, split, st);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    return CWTH_OK;
+}
+
+cwth_status launch_all(cwth_plan_s* p, const float* d_x, int64_t ld_x, const int64_t* d_len,
+                       int32_t batch, float* d_out, cudaStream_t st) {
+    cwth_status s = launch_direct(p, d_x, ld_x, d_len, batch, d_out, st);
+    if (s != CWTH_OK) return s;
+    return launch_spectral(p, d_x, ld_x, d_len, batch, d_out, st);
+}
+
 struct DeviceGuard {
     int prev = -1;
     bool ok = true;
@@ -238,6 +524,8 @@ int64_t cwth_num_frames(int64_t n, int32_t hop) {
     if (n <= 0 || hop <= 0) return 0;
     return (n + hop - 1) / hop;
 }
+
+const char* cwth_last_error(void) { return g_last_error; }
 
 const char* cwth_status_string(cwth_status s) {
     switch (s) {
@@ -286,7 +574,24 @@ cwth_status cwth_plan(const cwth_morlet* w, const double* scales, int32_t S, int
         p->frames_max = cwth_num_frames(max_len, hop);
         p->scales.assign(scales, scales + S);
         p->scale_path.assign(S, CWTH_PATH_SPECTRAL);
-        if (path == CWTH_PATH_DIRECT) st = CWTH_ERR_UNSUPPORTED;
+        const bool spectral_ok = is_pow2(hop);
+        for (int32_t s = 0; s < S && st == CWTH_OK; ++s) {
+            const bool direct_ok = direct_eligible(*p, scales[s]);
+            int32_t choice;
+            if (path == CWTH_PATH_SPECTRAL)
+                choice = spectral_ok ? CWTH_PATH_SPECTRAL : -1;
+            else if (path == CWTH_PATH_DIRECT)
+                choice = direct_ok ? CWTH_PATH_DIRECT : -1;
+            else if (precision == CWTH_PREC_FP32)
+                choice = spectral_ok ? CWTH_PATH_SPECTRAL : (direct_ok ? CWTH_PATH_DIRECT : -1);
+            else
+                choice = direct_ok ? CWTH_PATH_DIRECT : (spectral_ok ? CWTH_PATH_SPECTRAL : -1);
+            if (choice < 0)
+                st = CWTH_ERR_UNSUPPORTED;
+            else
+                p->scale_path[s] = choice;
+        }
+        if (st == CWTH_OK) st = build_direct(p);
         if (st == CWTH_OK) st = build_spectral(p);
     } catch (...) {
         st = CWTH_ERR_OOM;
@@ -310,7 +615,7 @@ cwth_status cwth_execute(cwth_plan_t p, const float* d_x, int64_t ld_x, const in
     DeviceGuard g(p->device);
     if (!g.ok) return CWTH_ERR_CUDA;
     cudaStream_t st = (cudaStream_t)stream;
-    return launch_spectral(p, d_x, ld_x, d_lengths, batch, d_out, st);
+    return launch_all(p, d_x, ld_x, d_lengths, batch, d_out, st);
 }
 
 cwth_status cwth_execute_host(cwth_plan_t p, const float* h_x, int64_t ld_x,
@@ -334,8 +639,8 @@ cwth_status cwth_execute_host(cwth_plan_t p, const float* h_x, int64_t ld_x,
         e = cudaMemcpyAsync(p->d_stage_len, h_lengths, (size_t)batch * sizeof(int64_t),
                             cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_status(e);
-    s = launch_spectral(p, p->d_stage_x, ld_x, h_lengths ? p->d_stage_len : nullptr, batch,
-                        p->d_stage_out, st);
+    s = launch_all(p, p->d_stage_x, ld_x, h_lengths ? p->d_stage_len : nullptr, batch,
+                   p->d_stage_out, st);
     if (s != CWTH_OK) return s;
     if (!h_lengths) {
         e = cudaMemcpyAsync(h_out, p->d_stage_out, no * sizeof(float), cudaMemcpyDeviceToHost, st);
@@ -389,6 +694,24 @@ cwth_status cwth_plan_query(cwth_plan_t p, cwth_plan_info* info) {
     info->direct_taps = p->dir_taps;
     info->table_bytes = p->table_bytes;
     info->sample_rate = p->fs;
+    return CWTH_OK;
+}
+
+cwth_status cwth_sync(cwth_plan_t p, void* stream) {
+    if (!valid_plan(p)) return CWTH_ERR_BAD_PLAN;
+    DeviceGuard g(p->device);
+    if (!g.ok) return CWTH_ERR_CUDA;
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (p->d_status) {
+        int flag = 0;
+        e = cudaMemcpy(&flag, p->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_status(e);
+        if (flag != 0) {
+            cudaMemset(p->d_status, 0, sizeof(int));
+            return (cwth_status)flag;
+        }
+    }
     return CWTH_OK;
 }
 

@@ -1,6 +1,8 @@
 // Internal declarations shared by the translation units of libcwth.so.
 #pragma once
 
+#include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -55,11 +57,63 @@ struct SpecLaunch {
     const SpecScale* sc;
 };
 
+// Direct (GEMM) path launch parameters; one launch per scale group.
+constexpr int kMaxDirStages = 6;
+struct DirLaunch {
+    float* out;
+    int64_t frames_max;
+    int32_t S_total;
+    int32_t hop;
+    const int64_t* lengths;
+    int64_t max_len;
+    int32_t batch;
+    int64_t rows_per_clip;  // GEMM rows (frames) reserved per clip
+    int64_t total_rows;     // batch * rows_per_clip
+    int32_t ncols;          // N: 2 * scales, padded to a multiple of 16
+    int32_t k_pad;          // K: padded taps, a multiple of 64
+    int32_t h_group;        // half support of the group (taps -h_group .. h_group)
+    int32_t n_scales;
+    const int32_t* rows;    // output row of each scale of the group
+    int32_t stages;
+    uint32_t tmem_cols;
+    int* status;            // device status word (CWTH_ERR_TIMEOUT on a bounded-wait expiry)
+};
+
 size_t spectral_smem_bytes(int M, int P, int nconc);
 cudaError_t spectral_prepare_device();
 cudaError_t spectral_make_twiddles(float2* d_tw, int M, cudaStream_t st);
 cudaError_t spectral_launch(const SpecLaunch& L, int n_seg, int batch, int n_groups,
                             size_t smem, cudaStream_t st);
+
+size_t direct_smem_bytes(int ncols, int stages, bool split);
+int direct_max_stages(int ncols, bool split);
+cudaError_t direct_prepare_device();
+cudaError_t direct_prepare_f32(size_t smem);
+cudaError_t direct_make_bank(const double* d_scales, const int32_t* d_h, int n_scales, int ncols,
+                             int k_pad, int h_group, double B, double C, __nv_bfloat16* hi,
+                             __nv_bfloat16* lo, float2* f32bank, cudaStream_t st);
+cudaError_t direct_stage(const float* x, int64_t ld_x, const int64_t* lengths, int64_t max_len,
+                         int batch, __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t lpad,
+                         int64_t h_front, int64_t total, cudaStream_t st);
+cudaError_t direct_launch_mma(const CUtensorMap* maps, const DirLaunch& L, bool split,
+                              cudaStream_t st);
+cudaError_t direct_launch_f32(const float* x, int64_t ld_x, const float2* bank, const int32_t* d_h,
+                              const DirLaunch& L, cudaStream_t st);
+
+// One group of direct-path scales (contiguous in support order).
+struct DirGroup {
+    int32_t n_scales = 0;
+    int32_t ncols = 0;
+    int32_t h = 0;       // group half support, a multiple of 8
+    int32_t k_pad = 0;   // multiple of 64, >= 2h + 1
+    int32_t stages = 0;
+    int64_t bank_off = 0;   // element offset into the bf16 banks ([ncols][k_pad])
+    int64_t f32_off = 0;    // element offset into the float32 bank ([n_scales][k_pad])
+    int32_t* d_rows = nullptr;
+    int32_t* d_h = nullptr;
+    double* d_scales = nullptr;
+    CUtensorMap map_b_hi, map_b_lo;
+};
 
 }  // namespace cwth
 
@@ -80,7 +134,21 @@ struct cwth_plan_s {
 
     // direct path
     int32_t n_dir = 0;
-    int32_t dir_taps = 0;
+    int32_t dir_taps = 0;      // largest padded tap count over the groups
+    int32_t dir_front = 0;     // zero samples before each clip in the staged signal
+    std::vector<cwth::DirGroup> groups;
+    __nv_bfloat16* d_bank_hi = nullptr;
+    __nv_bfloat16* d_bank_lo = nullptr;
+    float2* d_bank_f32 = nullptr;
+    int* d_status = nullptr;
+    // staged bf16 signal (workspace), grown on demand
+    __nv_bfloat16* d_xhi = nullptr;
+    __nv_bfloat16* d_xlo = nullptr;
+    size_t x_elems = 0;
+    // A-operand tensor maps per group, valid for (x_maps_ptr, x_maps_rows)
+    std::vector<CUtensorMap> maps_a_hi, maps_a_lo;
+    const void* x_maps_ptr = nullptr;
+    int64_t x_maps_rows = -1;
 
     int64_t table_bytes = 0;
 

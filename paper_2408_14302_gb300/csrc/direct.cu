@@ -1,0 +1,369 @@
+// Direct path of the hop-size CWT (paper Sec. II.A Eq. 1 + Sec. II.B hop):
+//
+//     W_s[k] = sum_{t=-h}^{h} x[kH + t] * g_s[t],   g_s[t] = a_s^{-1/2} conj(psi(t/a_s)),
+//
+// evaluated as a GEMM C[frames x 2S] = A[frames x taps] * B[taps x 2S] with
+// A[k, tau] = x[kH - h + tau] (the hop-strided frame matrix, never
+// materialised: a TMA view of the padded signal whose row stride is H) and B
+// the real/imaginary columns of the zero-padded tap bank.  Scales are
+// grouped by support; each group is one GEMM with K = its padded tap count.
+//
+// tcgen05 kernel (bf16 operands, f32 accumulation in tensor memory), one CTA
+// per 128-frame tile of one group, 6 warps:
+//   warp 0      TMA producer (A and B tiles, 64 taps per stage, 128B swizzle)
+//   warp 1      TMEM allocation + single-thread MMA issue (M=128, N<=256, K=16)
+//   warps 2..5  epilogue: tcgen05.ld, |re + i im|, coalesced stores along k
+// The split variant ("bf16x2") represents x = x_hi + x_lo and g = g_hi + g_lo
+// (each pair within 2^-18 of its value) and accumulates all four products
+// into the same tensor-memory accumulator, so every tap product is within
+// about 2^-17 relative of x * g even when a frame has a single tap.  Every mbarrier wait is bounded; on a timeout the CTA
+// records CWTH_ERR_TIMEOUT in a device status word, drains its own TMA
+// copies (bounded), releases tensor memory and returns.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "cwth_internal.h"
+#include "sm100.cuh"
+
+namespace cwth {
+namespace {
+
+using namespace sm100;
+
+constexpr int kBM = 128;             // frames per tile
+constexpr int kBK = 64;              // taps per stage (128 bytes of bf16)
+constexpr int kDirThreads = 192;
+constexpr long long kWaitBudget = 4000000000LL;  // ~2 s of SM clock
+
+// ------------------------------------------------------------ staging
+// x_pad[b][j] = x[b][j - h_front] for j - h_front in [0, len_b), else 0;
+// hi = bf16(x), lo = bf16(x - hi).  Also zeroes the tail after the last clip.
+__global__ void stage_bf16_kernel(const float* __restrict__ x, int64_t ld_x,
+                                  const int64_t* __restrict__ lengths, int64_t max_len, int batch,
+                                  __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo,
+                                  int64_t lpad, int64_t h_front, int64_t total) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = i / lpad;
+        const int64_t n = i - b * lpad - h_front;
+        float v = 0.f;
+        if (b < batch) {
+            int64_t len = lengths ? lengths[b] : max_len;
+            len = len < 0 ? 0 : (len > max_len ? max_len : len);
+            if (n >= 0 && n < len) v = __ldg(x + b * ld_x + n);
+        }
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        hi[i] = h;
+        if (lo) lo[i] = __float2bfloat16_rn(v - __bfloat162float(h));
+    }
+}
+
+// ------------------------------------------------------------ tap bank (float64)
+// bank[n][tau] for column n of a group: scale j = n / 2 (real part for even n,
+// imaginary for odd n), tap t = tau - h_group, value a^{-1/2} conj(psi(t/a))
+// for |t| <= h_j, else 0.  Columns past 2 * n_scales are zero.
+__global__ void bank_kernel(const double* __restrict__ scales, const int32_t* __restrict__ h_of,
+                            int n_scales, int ncols, int k_pad, int h_group, double B, double C,
+                            __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo,
+                            float2* __restrict__ f32bank) {
+    const int64_t total = (int64_t)ncols * k_pad;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int n = (int)(i / k_pad);
+        const int tau = (int)(i - (int64_t)n * k_pad);
+        const int j = n >> 1;
+        double v = 0.0;
+        if (j < n_scales) {
+            const int t = tau - h_group;
+            if (t >= -h_of[j] && t <= h_of[j]) {
+                const double a = scales[j];
+                const double u = (double)t / a;
+                const double env = exp(-(u * u) / B) / sqrt(a * M_PI * B);
+                double s, c;
+                sincospi(2.0 * C * u, &s, &c);
+                v = (n & 1) ? -env * s : env * c;
+            }
+        }
+        const __nv_bfloat16 h = __float2bfloat16_rn((float)v);
+        hi[i] = h;
+        lo[i] = __float2bfloat16_rn((float)(v - (double)__bfloat162float(h)));
+        if (f32bank && j < n_scales) {
+            // float32 copy for the SIMT kernel: [scale][tau] as (re, im)
+            float* f = reinterpret_cast<float*>(f32bank + (int64_t)j * k_pad + tau);
+            f[n & 1] = (float)v;
+        }
+    }
+}
+
+// ------------------------------------------------------------ tcgen05 GEMM
+template <bool SPLIT>
+__global__ void __launch_bounds__(kDirThreads, 1)
+    direct_mma_kernel(const __grid_constant__ CUtensorMap mA_hi,
+                      const __grid_constant__ CUtensorMap mA_lo,
+                      const __grid_constant__ CUtensorMap mB_hi,
+                      const __grid_constant__ CUtensorMap mB_lo, const DirLaunch p) {
+    extern __shared__ uint8_t dsmem_raw[];
+    __shared__ __align__(8) uint64_t full_bar[kMaxDirStages];
+    __shared__ __align__(8) uint64_t empty_bar[kMaxDirStages];
+    __shared__ __align__(8) uint64_t accum_bar;
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ int abort_sh;
+
+    uint8_t* smem = (uint8_t*)(((uintptr_t)dsmem_raw + 1023) & ~(uintptr_t)1023);
+    const int N = p.ncols;
+    const int stages = p.stages;
+    const uint32_t a_bytes = kBM * kBK * 2;
+    const uint32_t b_bytes = (uint32_t)N * kBK * 2;
+    const uint32_t stage_bytes = (a_bytes + b_bytes) * (SPLIT ? 2 : 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * kBM;
+    const int nkb = p.k_pad / kBK;
+    const uint32_t tcols = p.tmem_cols;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < stages; ++s) {
+            mbar_init(&full_bar[s], 1);
+            mbar_init(&empty_bar[s], 1);
+        }
+        mbar_init(&accum_bar, 1);
+        // A CTA of a launch that already timed out does no work.
+        abort_sh = *(volatile int*)p.status != 0 ? 1 : 0;
+        fence_mbar_init();
+        prefetch_tensormap(&mA_hi);
+        prefetch_tensormap(&mB_hi);
+        if (SPLIT) {
+            prefetch_tensormap(&mA_lo);
+            prefetch_tensormap(&mB_lo);
+        }
+    }
+    if (warp == 1) {
+        tmem_alloc(&tmem_base_sh, tcols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base_sh;
+
+    auto stage_ptr = [&](int s) { return smem + (size_t)s * stage_bytes; };
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // Producer.
+            int issued = 0;
+            for (int kb = 0; kb < nkb; ++kb) {
+                const int s = kb % stages;
+                const uint32_t use = (uint32_t)(kb / stages);
+                if (*(volatile int*)&abort_sh) break;
+                if (kb >= stages && !mbar_wait(&empty_bar[s], (use & 1) ^ 1, kWaitBudget)) {
+                    atomicExch(&abort_sh, 1);
+                    break;
+                }
+                uint8_t* st = stage_ptr(s);
+                mbar_arrive_expect_tx(&full_bar[s], stage_bytes);
+                tma_load_2d(st, &mA_hi, &full_bar[s], kb * kBK, m0);
+                tma_load_2d(st + a_bytes, &mB_hi, &full_bar[s], kb * kBK, 0);
+                if (SPLIT) {
+                    tma_load_2d(st + a_bytes + b_bytes, &mA_lo, &full_bar[s], kb * kBK, m0);
+                    tma_load_2d(st + 2 * a_bytes + b_bytes, &mB_lo, &full_bar[s], kb * kBK, 0);
+                }
+                ++issued;
+            }
+            // Drain: every stage filled must have landed before the CTA exits.
+            for (int kb = (issued > stages ? issued - stages : 0); kb < issued; ++kb) {
+                const int s = kb % stages;
+                if (!mbar_wait(&full_bar[s], (uint32_t)(kb / stages) & 1, kWaitBudget)) {
+                    atomicExch(&abort_sh, 1);
+                    break;
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // MMA issuer.
+            const uint32_t idesc = idesc_bf16_f32(kBM, N);
+            bool ok = true;
+            for (int kb = 0; kb < nkb; ++kb) {
+                const int s = kb % stages;
+                if (*(volatile int*)&abort_sh) break;
+                if (!mbar_wait(&full_bar[s], (uint32_t)(kb / stages) & 1, kWaitBudget)) {
+                    atomicExch(&abort_sh, 1);
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t st = smem_u32(stage_ptr(s));
+                const uint64_t a_hi = desc_kmajor_sw128(st);
+                const uint64_t b_hi = desc_kmajor_sw128(st + a_bytes);
+#pragma unroll
+                for (int k = 0; k < kBK / 16; ++k) {
+                    // 16 bf16 = 32 bytes along K -> +2 in the >>4 address field
+                    const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
+                    mma_f16(tmem, a_hi + 2 * k, b_hi + 2 * k, idesc, acc);
+                    if (SPLIT) {
+                        const uint64_t a_lo = desc_kmajor_sw128(st + a_bytes + b_bytes);
+                        const uint64_t b_lo = desc_kmajor_sw128(st + 2 * a_bytes + b_bytes);
+                        mma_f16(tmem, a_hi + 2 * k, b_lo + 2 * k, idesc, 1u);
+                        mma_f16(tmem, a_lo + 2 * k, b_hi + 2 * k, idesc, 1u);
+                        mma_f16(tmem, a_lo + 2 * k, b_lo + 2 * k, idesc, 1u);
+                    }
+                }
+                mma_commit(&empty_bar[s]);
+            }
+            (void)ok;
+            mma_commit(&accum_bar);
+        }
+    } else {
+        // Epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (one frame each).
+        const int quarter = warp & 3;
+        const bool ready = mbar_wait(&accum_bar, 0, kWaitBudget);
+        if (!ready) atomicExch(&abort_sh, 1);
+        tc_fence_after();
+        const int64_t row = (int64_t)m0 + quarter * 32 + lane;
+        const int64_t b = row / p.rows_per_clip;
+        const int64_t k = row - b * p.rows_per_clip;
+        bool valid = ready && b < p.batch;
+        if (valid) {
+            int64_t len = p.lengths ? p.lengths[b] : p.max_len;
+            len = len < 0 ? 0 : (len > p.max_len ? p.max_len : len);
+            valid = k < (len + p.hop - 1) / p.hop;
+        }
+        if (ready && !*(volatile int*)&abort_sh) {
+            const uint32_t tlane = tmem + ((uint32_t)(quarter * 32) << 16);
+            for (int c0 = 0; c0 < N; c0 += 16) {
+                float v[16];
+                tmem_ld16(tlane + (uint32_t)c0, v);
+                if (valid) {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const int sl = (c0 >> 1) + j;
+                        if (sl < p.n_scales) {
+                            const float re = v[2 * j], im = v[2 * j + 1];
+                            const int orow = __ldg(p.rows + sl);
+                            p.out[(b * p.S_total + orow) * p.frames_max + k] =
+                                sqrtf(fmaf(re, re, im * im));
+                        }
+                    }
+                }
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, tcols);
+    }
+    if (threadIdx.x == 0 && abort_sh) atomicExch(p.status, (int)CWTH_ERR_TIMEOUT);
+}
+
+// ------------------------------------------------------------ float32 SIMT
+// One CTA per (128-frame tile, clip, scale); taps of the scale staged in
+// shared memory; each thread sums one frame in float32.
+__global__ void __launch_bounds__(128) direct_f32_kernel(const float* __restrict__ x, int64_t ld_x,
+                                                         const float2* __restrict__ bank,
+                                                         const DirLaunch p,
+                                                         const int32_t* __restrict__ h_of) {
+    extern __shared__ float2 taps[];
+    const int sl = blockIdx.z;
+    const int64_t b = blockIdx.y;
+    const int h = h_of[sl];
+    const int hg = p.h_group;
+    for (int t = threadIdx.x; t <= 2 * h; t += blockDim.x)
+        taps[t] = bank[(int64_t)sl * p.k_pad + (hg - h) + t];
+    __syncthreads();
+    int64_t len = p.lengths ? p.lengths[b] : p.max_len;
+    len = len < 0 ? 0 : (len > p.max_len ? p.max_len : len);
+    const int64_t F = (len + p.hop - 1) / p.hop;
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= F) return;
+    const float* xr = x + b * ld_x;
+    const int64_t c = k * p.hop;
+    const int64_t t0 = c - h < 0 ? -c : -h;
+    const int64_t t1 = c + h > len - 1 ? len - 1 - c : h;
+    float re = 0.f, im = 0.f;
+    for (int64_t t = t0; t <= t1; ++t) {
+        const float xv = __ldg(xr + c + t);
+        const float2 g = taps[t + h];
+        re = fmaf(xv, g.x, re);
+        im = fmaf(xv, g.y, im);
+    }
+    const int orow = p.rows[sl];
+    p.out[(b * p.S_total + orow) * p.frames_max + k] = sqrtf(fmaf(re, re, im * im));
+}
+
+}  // namespace
+
+size_t direct_smem_bytes(int ncols, int stages, bool split) {
+    const size_t stage = ((size_t)kBM * kBK * 2 + (size_t)ncols * kBK * 2) * (split ? 2 : 1);
+    return stage * stages + 1024;  // + alignment slack
+}
+
+// Dynamic shared memory a direct CTA may request: the 227 KB opt-in limit
+// less room for the kernel's static barriers.
+constexpr size_t kDirSmemLimit = 227 * 1024 - 1024;
+
+int direct_max_stages(int ncols, bool split) {
+    int s = kMaxDirStages;
+    while (s > 2 && direct_smem_bytes(ncols, s, split) > kDirSmemLimit) --s;
+    return direct_smem_bytes(ncols, s, split) <= kDirSmemLimit ? s : 0;
+}
+
+cudaError_t direct_prepare_device() {
+    cudaError_t e = cudaFuncSetAttribute(direct_mma_kernel<false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kDirSmemLimit);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(direct_mma_kernel<true>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDirSmemLimit);
+}
+
+cudaError_t direct_make_bank(const double* d_scales, const int32_t* d_h, int n_scales, int ncols,
+                             int k_pad, int h_group, double B, double C, __nv_bfloat16* hi,
+                             __nv_bfloat16* lo, float2* f32bank, cudaStream_t st) {
+    const int64_t total = (int64_t)ncols * k_pad;
+    const int blocks = (int)std::min<int64_t>((total + 255) / 256, 4096);
+    bank_kernel<<<blocks, 256, 0, st>>>(d_scales, d_h, n_scales, ncols, k_pad, h_group, B, C, hi,
+                                        lo, f32bank);
+    return cudaGetLastError();
+}
+
+cudaError_t direct_stage(const float* x, int64_t ld_x, const int64_t* lengths, int64_t max_len,
+                         int batch, __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t lpad,
+                         int64_t h_front, int64_t total, cudaStream_t st) {
+    const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+    stage_bf16_kernel<<<blocks, 256, 0, st>>>(x, ld_x, lengths, max_len, batch, hi, lo, lpad,
+                                              h_front, total);
+    return cudaGetLastError();
+}
+
+cudaError_t direct_launch_mma(const CUtensorMap* maps, const DirLaunch& L, bool split,
+                              cudaStream_t st) {
+    const int64_t tiles = (L.total_rows + kBM - 1) / kBM;
+    const size_t smem = direct_smem_bytes(L.ncols, L.stages, split);
+    if (split)
+        direct_mma_kernel<true><<<(unsigned)tiles, kDirThreads, smem, st>>>(maps[0], maps[1],
+                                                                           maps[2], maps[3], L);
+    else
+        direct_mma_kernel<false><<<(unsigned)tiles, kDirThreads, smem, st>>>(maps[0], maps[0],
+                                                                            maps[2], maps[2], L);
+    return cudaGetLastError();
+}
+
+cudaError_t direct_launch_f32(const float* x, int64_t ld_x, const float2* bank, const int32_t* d_h,
+                              const DirLaunch& L, cudaStream_t st) {
+    const int64_t ftiles = (L.frames_max + 127) / 128;
+    dim3 grid((unsigned)ftiles, (unsigned)L.batch, (unsigned)L.n_scales);
+    const size_t smem = (size_t)(2 * L.h_group + 1) * sizeof(float2);
+    direct_f32_kernel<<<grid, 128, smem, st>>>(x, ld_x, bank, L, d_h);
+    return cudaGetLastError();
+}
+
+cudaError_t direct_prepare_f32(size_t smem) {
+    return cudaFuncSetAttribute(direct_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)std::max<size_t>(smem, 48 * 1024));
+}
+
+}  // namespace cwth

@@ -23,13 +23,15 @@ PATH = {"auto": 0, "spectral": 1, "direct": 2}
 # Every symbol include/cwth.h declares.
 EXPORTS = ("cwth_plan", "cwth_execute", "cwth_execute_host", "cwth_destroy",
            "cwth_num_frames", "cwth_status_string", "cwth_plan_query",
-           "cwth_plan_scale_paths")
+           "cwth_plan_scale_paths", "cwth_sync", "cwth_last_error")
 
 
 class CwthError(RuntimeError):
-    def __init__(self, status: int, where: str):
+    def __init__(self, status: int, where: str, detail: str = ""):
         self.status = status
-        super().__init__(f"{where}: {STATUS.get(status, status)}")
+        self.detail = detail
+        msg = f"{where}: {STATUS.get(status, status)}"
+        super().__init__(msg + (f" ({detail})" if detail else ""))
 
 
 class Morlet(ctypes.Structure):
@@ -72,6 +74,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.cwth_plan_query.restype = ctypes.c_int
     lib.cwth_plan_scale_paths.argtypes = [vp, ctypes.POINTER(i32)]
     lib.cwth_plan_scale_paths.restype = ctypes.c_int
+    lib.cwth_last_error.argtypes = []
+    lib.cwth_last_error.restype = ctypes.c_char_p
+    lib.cwth_sync.argtypes = [vp, vp]
+    lib.cwth_sync.restype = ctypes.c_int
     return lib
 
 
@@ -84,7 +90,10 @@ def lib() -> ctypes.CDLL:
 
 def _check(status: int, where: str):
     if status != CWTH_OK:
-        raise CwthError(status, where)
+        detail = ""
+        if status in (2, 3, 4):
+            detail = (_lib.cwth_last_error() or b"").decode(errors="replace")
+        raise CwthError(status, where, detail)
 
 
 def num_frames(n: int, hop: int) -> int:
@@ -171,6 +180,12 @@ class Plan:
                                     ctypes.c_void_p(ptr(out)), ctypes.c_void_p(s))
         _check(st, "cwth_execute_host")
         return out
+
+    def sync(self, stream=None):
+        """Wait for this plan's work on ``stream`` and raise on device-side
+        errors (a kernel that gave up a bounded wait)."""
+        s = 0 if stream is None else stream.cuda_stream
+        _check(_lib.cwth_sync(self._h, ctypes.c_void_p(s)), "cwth_sync")
 
     def close(self):
         if self._h:

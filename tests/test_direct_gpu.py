@@ -1,0 +1,113 @@
+"""GPU parity of the direct (time-domain GEMM) path against the float64 oracle.
+
+Tolerances, max |err| / max|W| per clip: bf16 operands 2e-2, split hi+lo bf16
+1e-5, float32 (SIMT) 1e-5.  Workload: the tones generator, 1 s at 16 kHz,
+128 scales 100-8000 Hz, hops 64/128/256/512 (the precision study), plus
+ragged batches and small hops that exercise overlapping frame views.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"bf16": 2e-2, "bf16x2": 1e-5, "fp32": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def cw():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2408_14302_gb300 import cwth
+    return cwth
+
+
+@pytest.fixture(scope="module")
+def sig():
+    from paper_2408_14302_gb300 import signals
+    return signals
+
+
+def oracle_mag(x, scales, hop):
+    import oracle
+    return oracle.cwth_magnitude(np.asarray(x, np.float32).astype(np.float64), scales, hop)
+
+
+def run(cw, xs, scales, hop, precision, path="direct", lengths=None, fill=np.nan):
+    xs = np.ascontiguousarray(np.atleast_2d(np.asarray(xs, np.float32)))
+    with cw.Plan(scales, hop=hop, max_len=xs.shape[1], precision=precision, path=path) as plan:
+        out = torch.full((xs.shape[0], len(scales), plan.frames_max), float(fill), device="cuda")
+        ld = torch.from_numpy(np.asarray(lengths, np.int64)).cuda() if lengths is not None else None
+        plan.execute(torch.from_numpy(xs).cuda(), lengths=ld, out=out)
+        plan.sync()
+        return out.cpu().numpy().astype(np.float64), plan.info(), plan.scale_paths()
+
+
+@pytest.mark.parametrize("precision", ["bf16", "bf16x2", "fp32"])
+@pytest.mark.parametrize("hop", [64, 128, 256, 512])
+def test_precision_study_128_scales(cw, sig, hop, precision):
+    x = sig.tones_clip(seed=0, n=16000).astype(np.float32)
+    sc = sig.scales_for_band(100, 8000, 128, 16000.0)
+    got, info, paths = run(cw, x, sc, hop, precision)
+    assert info["num_direct"] == 128 and (paths == 2).all()
+    ref = oracle_mag(x, sc, hop)
+    err = np.max(np.abs(got[0] - ref)) / ref.max()
+    assert err <= TOL[precision], (hop, precision, err)
+
+
+@pytest.mark.parametrize("precision", ["bf16", "bf16x2"])
+@pytest.mark.parametrize("hop", [8, 16, 40])
+def test_small_hops_overlapping_frames(cw, sig, hop, precision):
+    x = sig.machine_clip(seed=3, n=6001)
+    sc = sig.scales_for_band(200, 8000, 24, 16000.0)
+    got, _, _ = run(cw, x, sc, hop, precision)
+    ref = oracle_mag(x, sc, hop)
+    assert np.max(np.abs(got[0] - ref)) / ref.max() <= TOL[precision]
+
+
+@pytest.mark.parametrize("precision", ["bf16x2", "fp32"])
+def test_ragged_batch_and_untouched_tail(cw, sig, precision):
+    hop, n = 64, 12000
+    lengths = [12000, 11999, 1, 0, 500, 64, 65, 7000, 3333]
+    xs = np.stack([sig.machine_clip(200 + i, n) for i in range(len(lengths))])
+    sc = sig.scales_for_band(100, 8000, 40, 16000.0)
+    got, _, _ = run(cw, xs, sc, hop, precision, lengths=lengths, fill=-3.0)
+    for i, L in enumerate(lengths):
+        F = -(-L // hop)
+        assert np.all(got[i, :, F:] == -3.0)
+        if L == 0:
+            continue
+        ref = oracle_mag(xs[i, :L], sc, hop)
+        assert np.max(np.abs(got[i, :, :F] - ref)) / ref.max() <= TOL[precision], i
+
+
+def test_auto_bf16_mixes_paths(cw, sig):
+    # Scales with more than 4096 taps go to the spectral path.
+    x = sig.machine_clip(seed=4, n=40000)
+    sc = np.array([2.0, 5.0, 30.0, 200.0, 500.0, 1200.0])
+    got, info, paths = run(cw, x, sc, 64, "bf16x2", path="auto")
+    assert info["num_direct"] >= 3 and info["num_spectral"] >= 1
+    assert paths[0] == 2 and paths[-1] == 1
+    ref = oracle_mag(x, sc, 64)
+    assert np.max(np.abs(got[0] - ref)) / ref.max() <= 1e-5
+
+
+def test_direct_large_batch_sampled(cw, sig):
+    """512 clips (the precision study's throughput batch), rows sampled."""
+    hop = 64
+    xs = np.stack([sig.tones_clip(seed=s, n=16000) for s in range(512)]).astype(np.float32)
+    sc = sig.scales_for_band(100, 8000, 128, 16000.0)
+    got, _, _ = run(cw, xs, sc, hop, "bf16x2")
+    assert np.isfinite(got).all()
+    for i in (0, 255, 511):
+        ref = oracle_mag(xs[i], sc, hop)
+        assert np.max(np.abs(got[i] - ref)) / ref.max() <= 1e-5
+
+
+def test_direct_unsupported_cases(cw):
+    with pytest.raises(cw.CwthError):
+        cw.Plan([2.0], hop=12, max_len=1000, precision="bf16", path="direct")   # hop % 8
+    with pytest.raises(cw.CwthError):
+        cw.Plan([900.0], hop=64, max_len=1000, precision="bf16", path="direct")  # > 4096 taps
