@@ -176,6 +176,44 @@ cwth_status cwth_sync(cwth_plan_t plan, void *stream);
  * for s < S (host array of S entries). */
 cwth_status cwth_plan_scale_paths(cwth_plan_t plan, int32_t *paths);
 
+/*
+ * Allocation-free direct-path scalograms.
+ *
+ * For callers that cannot allocate device memory while they run: code whose
+ * device memory is owned by another allocator (a framework's caching pool),
+ * real-time or capture-sensitive loops where cudaMalloc/cudaFree would
+ * synchronise the device or block, and processes that must not grow their
+ * footprint after start-up.  This call needs no plan and allocates nothing:
+ * the tap bank, the per-scale tables, the staged bf16 signal and a status
+ * word all live in one array of CWTH_NOALLOC_SCRATCH_BYTES compiled into
+ * libcwth.so, which every GPU that loads the library holds until the process
+ * exits.  The paper has no counterpart of this call.
+ *
+ * Computes the same |W| as cwth_plan(..., CWTH_PATH_DIRECT) + cwth_execute:
+ *   w, scales, S (1..1024), hop (a multiple of 8), precision
+ *   (CWTH_PREC_BF16 or CWTH_PREC_BF16X2) as in cwth_plan; d_x, ld_x,
+ *   d_lengths, batch, d_out, stream as in cwth_execute, with max_len the
+ *   longest clip and d_out laid out [batch][S][cwth_num_frames(max_len, hop)].
+ *
+ * The first call on a device sets that device up (looks up the array's
+ * device address, sets the kernels' shared-memory limit, fetches the
+ * tensor-map encoder); make that first call before any stream capture.
+ * Every call on a device reuses the same array and leaves the previous call's
+ * contents in it (each call rewrites what it reads), so calls whose work
+ * overlaps on the GPU - on different streams, or from different threads -
+ * race: serialise them, e.g. on one stream.
+ *
+ * Errors: CWTH_ERR_INVALID_ARG for bad arguments and for a request whose
+ * scratch would exceed CWTH_NOALLOC_SCRATCH_BYTES (cwth_last_error() states
+ * the bytes needed); CWTH_ERR_UNSUPPORTED for a scale needing more than 4096
+ * taps; CWTH_ERR_CUDA for a launch failure.  Asynchronous on `stream`.
+ */
+#define CWTH_NOALLOC_SCRATCH_BYTES (64u << 20)
+cwth_status cwth_execute_direct_noalloc(const cwth_morlet *w, const double *scales, int32_t S,
+                                        int32_t hop, int32_t precision, const float *d_x,
+                                        int64_t ld_x, int64_t max_len, const int64_t *d_lengths,
+                                        int32_t batch, float *d_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

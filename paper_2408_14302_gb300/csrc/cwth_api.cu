@@ -518,6 +518,10 @@ cwth_status grow(T** ptr, size_t* have, size_t need) {
 
 }  // namespace
 
+namespace cwth {
+void set_last_error(const char* msg) { snprintf(g_last_error, sizeof(g_last_error), "%s", msg); }
+}  // namespace cwth
+
 extern "C" {
 
 int64_t cwth_num_frames(int64_t n, int32_t hop) {

@@ -79,6 +79,9 @@ struct DirLaunch {
     int* status;            // device status word (CWTH_ERR_TIMEOUT on a bounded-wait expiry)
 };
 
+// Records the detail string cwth_last_error() returns in the calling thread.
+void set_last_error(const char* msg);
+
 size_t spectral_smem_bytes(int M, int P, int nconc);
 cudaError_t spectral_prepare_device();
 cudaError_t spectral_make_twiddles(float2* d_tw, int M, cudaStream_t st);

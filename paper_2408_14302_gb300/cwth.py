@@ -23,7 +23,8 @@ PATH = {"auto": 0, "spectral": 1, "direct": 2}
 # Every symbol include/cwth.h declares.
 EXPORTS = ("cwth_plan", "cwth_execute", "cwth_execute_host", "cwth_destroy",
            "cwth_num_frames", "cwth_status_string", "cwth_plan_query",
-           "cwth_plan_scale_paths", "cwth_sync", "cwth_last_error")
+           "cwth_plan_scale_paths", "cwth_sync", "cwth_last_error",
+           "cwth_execute_direct_noalloc")
 
 
 class CwthError(RuntimeError):
@@ -78,6 +79,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.cwth_last_error.restype = ctypes.c_char_p
     lib.cwth_sync.argtypes = [vp, vp]
     lib.cwth_sync.restype = ctypes.c_int
+    lib.cwth_execute_direct_noalloc.argtypes = [ctypes.POINTER(Morlet),
+                                                ctypes.POINTER(ctypes.c_double), i32, i32, i32,
+                                                vp, i64, i64, vp, i32, vp, vp]
+    lib.cwth_execute_direct_noalloc.restype = ctypes.c_int
     return lib
 
 
@@ -98,6 +103,32 @@ def _check(status: int, where: str):
 
 def num_frames(n: int, hop: int) -> int:
     return int(_lib.cwth_num_frames(int(n), int(hop)))
+
+
+def execute_direct_noalloc(scales, hop: int, x, out, lengths=None, precision: str = "bf16x2",
+                           bandwidth: float = 1.5, center: float = 1.0, max_len=None,
+                           stream=None):
+    """cwth_execute_direct_noalloc: direct-path scalograms without any device
+    allocation (scratch lives in a fixed array inside libcwth.so).  ``x``:
+    float32 CUDA tensor [B, ld]; ``out``: float32 CUDA tensor
+    [B, S, num_frames(max_len, hop)], written asynchronously."""
+    import torch
+    sc = np.ascontiguousarray(np.asarray(scales, dtype=np.float64).ravel())
+    if x.dim() == 1:
+        x = x.unsqueeze(0)
+    B = x.shape[0]
+    max_len = int(x.shape[1]) if max_len is None else int(max_len)
+    ld = int(x.shape[1]) if B == 1 else int(x.stride(0))
+    if stream is None:
+        stream = torch.cuda.current_stream(x.device)
+    w = Morlet(float(bandwidth), float(center))
+    st = _lib.cwth_execute_direct_noalloc(
+        ctypes.byref(w), sc.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(sc.shape[0]),
+        int(hop), PREC[precision], ctypes.c_void_p(x.data_ptr()), ld, max_len,
+        ctypes.c_void_p(lengths.data_ptr() if lengths is not None else 0), int(B),
+        ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(stream.cuda_stream))
+    _check(st, "cwth_execute_direct_noalloc")
+    return out
 
 
 class Plan:
