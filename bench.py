@@ -246,6 +246,55 @@ def cpu_baseline(min_s: float = 3.0):
             "hop1_value": (N_SAMPLES / FS) / dt1}
 
 
+# ------------------------------------------------------------------ direct path leg
+DIRECT_CLIPS, DIRECT_N, DIRECT_S = 512, 16000, 128
+
+
+def direct_useful_flops_per_clip(scales, hop, n=DIRECT_N, eps=1e-9):
+    """2 flops per tap per (frame, real/imag column): F * sum_s (2 h_s + 1) * 2 * 2."""
+    F = -(-n // hop)
+    taps = sum(2 * math.ceil(a * math.sqrt(B_MORLET * math.log(1.0 / eps))) + 1 for a in scales)
+    return 4.0 * F * taps
+
+
+def run_direct_leg(torch, cwth, dev, flush, stream, steps, peak_bf16):
+    """Precision-study workload (tones generator, 1 s at 16 kHz, 128 scales
+    100-8000 Hz) on a 512-clip batch, per hop and operand precision."""
+    xs = np.stack([signals.tones_clip(seed=s, n=DIRECT_N) for s in range(DIRECT_CLIPS)]).astype(np.float32)
+    scales = signals.scales_for_band(100.0, 8000.0, DIRECT_S, FS, C_MORLET)
+    x_d = torch.from_numpy(xs).to(dev)
+    res = {}
+    for hop in (64, 128, 256, 512):
+        for prec in ("bf16", "bf16x2"):
+            p = cwth.Plan(scales, hop=hop, max_len=DIRECT_N, precision=prec, path="direct",
+                          sample_rate=FS)
+            o = torch.empty((DIRECT_CLIPS, DIRECT_S, p.frames_max), device=dev)
+            f = lambda: p.execute(x_d, out=o, stream=stream)  # noqa: E731
+            for _ in range(3):
+                f()
+            p.sync(stream)
+            ev = time_steps(torch, f, max(3, min(steps, 10)), flush, stream)
+            torch.cuda.synchronize()
+            p.sync(stream)
+            ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+            useful = direct_useful_flops_per_clip(scales, hop) * DIRECT_CLIPS
+            products = 4 if prec == "bf16x2" else 1
+            ach = useful * products / (ms * 1e-3) / 1e12
+            res[f"hop{hop}_{prec}"] = {
+                "ms_per_step": ms,
+                "audio_sec_per_s": DIRECT_CLIPS * DIRECT_N / FS / (ms * 1e-3),
+                "useful_tflops": useful / (ms * 1e-3) / 1e12,
+                "tensor_tflops_products": ach,
+                "tensor_frac_of_bf16_peak": ach / peak_bf16,
+                "direct_taps": p.info()["direct_taps"],
+            }
+            p.close()
+            del o
+    return {"workload": "tones_1s_512clips_128scales", "clips": DIRECT_CLIPS,
+            "scales": DIRECT_S, "l2": "flushed: 256 MiB write before every timed step",
+            "peak_bf16_tflops": peak_bf16, "runs": res}
+
+
 # ------------------------------------------------------------------ our arm
 def time_steps(torch, fn, steps, flush, stream):
     """Per-step CUDA-event time on `stream` with an L2 flush before each step."""
@@ -322,6 +371,11 @@ def run_ours(args, rank, world, local_rank):
         del o1
         p1.close()
 
+    pk, pk_kind = peaks()
+    direct = None
+    if not args.no_direct:
+        direct = run_direct_leg(torch, cwth, dev, flush, stream, args.steps, pk["bf16_tflops"])
+
     # End to end through the public host entry point (pinned host buffers).
     hx = torch.from_numpy(xs).pin_memory()
     hout = torch.empty((N_CLIPS, S, plan.frames_max), dtype=torch.float32).pin_memory()
@@ -332,7 +386,6 @@ def run_ours(args, rank, world, local_rank):
         plan.execute_host(hx, hout, stream=stream)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
 
-    pk, pk_kind = peaks()
     flops_clip, m_unseg = algorithmic_flops_per_clip(scales, HOP)
     flops_launch = flops_clip * N_CLIPS
     sm_mhz = clocks.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
@@ -370,6 +423,7 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": args.steps * 1,
         "clocks": clocks,
         "hop1": hop1,
+        "direct": direct,
     }
     plan.close()
     return line
@@ -383,6 +437,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-hop1", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-direct", action="store_true")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -122,6 +122,8 @@ void free_plan_memory(cwth_plan_s* p) {
         cudaFree(g.d_rows);
         cudaFree(g.d_h);
         cudaFree(g.d_scales);
+        cudaFree(g.d_sched);
+        g.d_sched = nullptr;
         g.d_rows = nullptr;
         g.d_h = nullptr;
         g.d_scales = nullptr;
@@ -196,49 +198,28 @@ bool encode_bf16_2d(CUtensorMap* map, const void* base, uint64_t inner, uint64_t
            CUDA_SUCCESS;
 }
 
-// Groups of consecutive (support-sorted) direct scales minimising the padded
-// GEMM volume sum(ncols * k_pad) plus a per-group cost for re-reading the
-// frame tiles; at most 128 scales (256 columns) per group.
-std::vector<std::pair<int, int>> group_scales(const std::vector<int32_t>& h_sorted) {
-    const int n = (int)h_sorted.size();
-    std::vector<double> best(n + 1, 1e300);
-    std::vector<int> from(n + 1, 0);
-    best[0] = 0;
-    for (int j = 1; j <= n; ++j) {
-        for (int i = std::max(0, j - 128); i < j; ++i) {
-            const double ncols = (double)round_up(2 * (j - i), 16);
-            const double kp = (double)round_up(2 * (int64_t)h_sorted[j - 1] + 1, 64);
-            const double c = best[i] + (ncols + 64.0) * kp;
-            if (c < best[j]) {
-                best[j] = c;
-                from[j] = i;
-            }
-        }
-    }
-    std::vector<std::pair<int, int>> g;
-    for (int j = n; j > 0; j = from[j]) g.push_back({from[j], j});
-    std::reverse(g.begin(), g.end());
-    return g;
-}
-
 cwth_status build_direct(cwth_plan_s* p) {
     std::vector<int> idx;
     for (int s = 0; s < p->S; ++s)
         if (p->scale_path[s] == CWTH_PATH_DIRECT) idx.push_back(s);
     p->n_dir = (int32_t)idx.size();
     if (p->n_dir == 0) return CWTH_OK;
+    // Descending support; groups of at most 128 scales (256 columns), each a
+    // pyramid-scheduled GEMM (see direct.cu).
     std::stable_sort(idx.begin(), idx.end(),
-                     [&](int a, int b) { return p->scales[a] < p->scales[b]; });
+                     [&](int a, int b) { return p->scales[a] > p->scales[b]; });
     std::vector<int32_t> hs(idx.size());
     for (size_t i = 0; i < idx.size(); ++i) hs[i] = direct_half_support(p->scales[idx[i]], p->B);
-    const auto ranges = group_scales(hs);
+    std::vector<std::pair<int, int>> ranges;
+    for (int i = 0; i < (int)idx.size(); i += 128)
+        ranges.push_back({i, std::min<int>((int)idx.size(), i + 128)});
     const bool split = p->precision == CWTH_PREC_BF16X2;
     int64_t bank_elems = 0, f32_elems = 0;
     for (auto& r : ranges) {
         cwth::DirGroup g;
         g.n_scales = r.second - r.first;
         g.ncols = (int32_t)round_up(2 * g.n_scales, 16);
-        g.h = hs[r.second - 1];
+        g.h = hs[r.first];
         g.k_pad = (int32_t)round_up(2 * (int64_t)g.h + 1, 64);
         g.bank_off = bank_elems;
         g.f32_off = f32_elems;
@@ -275,6 +256,11 @@ cwth_status build_direct(cwth_plan_s* p) {
             e = cudaMemcpy(g.d_h, hh.data(), sizeof(int32_t) * hh.size(), cudaMemcpyHostToDevice);
         if (e == cudaSuccess)
             e = cudaMemcpy(g.d_scales, sc.data(), sizeof(double) * sc.size(), cudaMemcpyHostToDevice);
+        std::vector<int2> sched(g.k_pad / 64);
+        g.nsteps = cwth::direct_schedule(hh.data(), g.n_scales, g.h, g.k_pad, sched.data());
+        if (e == cudaSuccess) e = cudaMalloc(&g.d_sched, sizeof(int2) * sched.size());
+        if (e == cudaSuccess)
+            e = cudaMemcpy(g.d_sched, sched.data(), sizeof(int2) * g.nsteps, cudaMemcpyHostToDevice);
         if (e == cudaSuccess)
             e = cwth::direct_make_bank(g.d_scales, g.d_h, g.n_scales, g.ncols, g.k_pad, g.h, p->B,
                                        p->C, p->d_bank_hi + g.bank_off, p->d_bank_lo + g.bank_off,
@@ -282,9 +268,9 @@ cwth_status build_direct(cwth_plan_s* p) {
         if (e != cudaSuccess) return cuda_status(e);
         if (p->precision != CWTH_PREC_FP32) {
             if (!encode_bf16_2d(&g.map_b_hi, p->d_bank_hi + g.bank_off, g.k_pad, g.ncols,
-                                (uint64_t)g.k_pad * 2, g.ncols) ||
+                                (uint64_t)g.k_pad * 2, 64) ||
                 !encode_bf16_2d(&g.map_b_lo, p->d_bank_lo + g.bank_off, g.k_pad, g.ncols,
-                                (uint64_t)g.k_pad * 2, g.ncols)) {
+                                (uint64_t)g.k_pad * 2, 64)) {
                 note_error("cuTensorMapEncodeTiled rejected the tap-bank tensor map");
                 return CWTH_ERR_UNSUPPORTED;
             }
@@ -469,6 +455,8 @@ cwth_status launch_direct(cwth_plan_s* p, const float* d_x, int64_t ld_x, const 
         L.n_scales = g.n_scales;
         L.rows = g.d_rows;
         L.stages = g.stages;
+        L.sched = g.d_sched;
+        L.nsteps = g.nsteps;
         uint32_t tc = 32;
         while (tc < (uint32_t)g.ncols) tc <<= 1;
         L.tmem_cols = tc;

@@ -77,6 +77,8 @@ struct DirLaunch {
     int32_t stages;
     uint32_t tmem_cols;
     int* status;            // device status word (CWTH_ERR_TIMEOUT on a bounded-wait expiry)
+    const int2* sched;      // per K step: {tap block, columns used (multiple of 16)}
+    int32_t nsteps;
 };
 
 // Records the detail string cwth_last_error() returns in the calling thread.
@@ -100,6 +102,9 @@ cudaError_t direct_stage(const float* x, int64_t ld_x, const int64_t* lengths, i
                          int64_t h_front, int64_t total, cudaStream_t st);
 cudaError_t direct_launch_mma(const CUtensorMap* maps, const DirLaunch& L, bool split,
                               cudaStream_t st);
+// Centre-out K-block schedule of one group (supports in descending order):
+// out[i] = {tap block, columns}; returns the number of steps (<= k_pad / 64).
+int direct_schedule(const int32_t* h_desc, int n, int h_group, int k_pad, int2* out);
 cudaError_t direct_launch_f32(const float* x, int64_t ld_x, const float2* bank, const int32_t* d_h,
                               const DirLaunch& L, cudaStream_t st);
 
@@ -115,6 +120,8 @@ struct DirGroup {
     int32_t* d_rows = nullptr;
     int32_t* d_h = nullptr;
     double* d_scales = nullptr;
+    int2* d_sched = nullptr;
+    int32_t nsteps = 0;
     CUtensorMap map_b_hi, map_b_lo;
 };
 

@@ -6,7 +6,11 @@
 // A[k, tau] = x[kH - h + tau] (the hop-strided frame matrix, never
 // materialised: a TMA view of the padded signal whose row stride is H) and B
 // the real/imaginary columns of the zero-padded tap bank.  Scales are
-// grouped by support; each group is one GEMM with K = its padded tap count.
+// grouped by support (at most 128 per group, columns in descending support);
+// each group is one GEMM whose K loop starts at the centre tap block and
+// then walks outwards, each block's MMA covering only the columns of the
+// scales whose support reaches it (a pyramid of MMAs instead of a padded
+// rectangle).
 //
 // tcgen05 kernel (bf16 operands, f32 accumulation in tensor memory), one CTA
 // per 128-frame tile of one group, 6 warps:
@@ -20,6 +24,8 @@
 // records CWTH_ERR_TIMEOUT in a device status word, drains its own TMA
 // copies (bounded), releases tensor memory and returns.
 #include <cuda_bf16.h>
+
+#include <stdlib.h>
 
 #include <algorithm>
 
@@ -114,11 +120,11 @@ __global__ void __launch_bounds__(kDirThreads, 1)
     const int N = p.ncols;
     const int stages = p.stages;
     const uint32_t a_bytes = kBM * kBK * 2;
-    const uint32_t b_bytes = (uint32_t)N * kBK * 2;
+    const uint32_t b_bytes = (uint32_t)((N + 63) / 64 * 64) * kBK * 2;
     const uint32_t stage_bytes = (a_bytes + b_bytes) * (SPLIT ? 2 : 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * kBM;
-    const int nkb = p.k_pad / kBK;
+    const int nsteps = p.nsteps;
     const uint32_t tcols = p.tmem_cols;
 
     if (threadIdx.x == 0) {
@@ -151,29 +157,38 @@ __global__ void __launch_bounds__(kDirThreads, 1)
     if (warp == 0) {
         if (lane == 0) {
             // Producer.
+            // Step i loads tap block sched[i].x for the A tile and the first
+            // sched[i].y columns of the bank, in 64-row pieces.
             int issued = 0;
-            for (int kb = 0; kb < nkb; ++kb) {
-                const int s = kb % stages;
-                const uint32_t use = (uint32_t)(kb / stages);
+            for (int i = 0; i < nsteps; ++i) {
+                const int s = i % stages;
+                const uint32_t use = (uint32_t)(i / stages);
                 if (*(volatile int*)&abort_sh) break;
-                if (kb >= stages && !mbar_wait(&empty_bar[s], (use & 1) ^ 1, kWaitBudget)) {
+                if (i >= stages && !mbar_wait(&empty_bar[s], (use & 1) ^ 1, kWaitBudget)) {
                     atomicExch(&abort_sh, 1);
                     break;
                 }
+                const int2 step = __ldg(p.sched + i);
+                const int kx = step.x * kBK;
+                const int pieces = (step.y + 63) >> 6;
                 uint8_t* st = stage_ptr(s);
-                mbar_arrive_expect_tx(&full_bar[s], stage_bytes);
-                tma_load_2d(st, &mA_hi, &full_bar[s], kb * kBK, m0);
-                tma_load_2d(st + a_bytes, &mB_hi, &full_bar[s], kb * kBK, 0);
+                mbar_arrive_expect_tx(&full_bar[s],
+                                      (a_bytes + (uint32_t)pieces * 64 * kBK * 2) * (SPLIT ? 2 : 1));
+                tma_load_2d(st, &mA_hi, &full_bar[s], kx, m0);
+                for (int j = 0; j < pieces; ++j)
+                    tma_load_2d(st + a_bytes + j * 64 * kBK * 2, &mB_hi, &full_bar[s], kx, j * 64);
                 if (SPLIT) {
-                    tma_load_2d(st + a_bytes + b_bytes, &mA_lo, &full_bar[s], kb * kBK, m0);
-                    tma_load_2d(st + 2 * a_bytes + b_bytes, &mB_lo, &full_bar[s], kb * kBK, 0);
+                    tma_load_2d(st + a_bytes + b_bytes, &mA_lo, &full_bar[s], kx, m0);
+                    for (int j = 0; j < pieces; ++j)
+                        tma_load_2d(st + 2 * a_bytes + b_bytes + j * 64 * kBK * 2, &mB_lo,
+                                    &full_bar[s], kx, j * 64);
                 }
                 ++issued;
             }
             // Drain: every stage filled must have landed before the CTA exits.
-            for (int kb = (issued > stages ? issued - stages : 0); kb < issued; ++kb) {
-                const int s = kb % stages;
-                if (!mbar_wait(&full_bar[s], (uint32_t)(kb / stages) & 1, kWaitBudget)) {
+            for (int i = (issued > stages ? issued - stages : 0); i < issued; ++i) {
+                const int s = i % stages;
+                if (!mbar_wait(&full_bar[s], (uint32_t)(i / stages) & 1, kWaitBudget)) {
                     atomicExch(&abort_sh, 1);
                     break;
                 }
@@ -182,24 +197,26 @@ __global__ void __launch_bounds__(kDirThreads, 1)
     } else if (warp == 1) {
         if (lane == 0) {
             // MMA issuer.
-            const uint32_t idesc = idesc_bf16_f32(kBM, N);
+            // The first step is the centre tap block, which every scale
+            // reaches: its N covers all columns and initialises them.
             bool ok = true;
-            for (int kb = 0; kb < nkb; ++kb) {
-                const int s = kb % stages;
+            for (int i = 0; i < nsteps; ++i) {
+                const int s = i % stages;
                 if (*(volatile int*)&abort_sh) break;
-                if (!mbar_wait(&full_bar[s], (uint32_t)(kb / stages) & 1, kWaitBudget)) {
+                if (!mbar_wait(&full_bar[s], (uint32_t)(i / stages) & 1, kWaitBudget)) {
                     atomicExch(&abort_sh, 1);
                     ok = false;
                     break;
                 }
                 tc_fence_after();
+                const uint32_t idesc = idesc_bf16_f32(kBM, __ldg(&p.sched[i].y));
                 const uint32_t st = smem_u32(stage_ptr(s));
                 const uint64_t a_hi = desc_kmajor_sw128(st);
                 const uint64_t b_hi = desc_kmajor_sw128(st + a_bytes);
 #pragma unroll
                 for (int k = 0; k < kBK / 16; ++k) {
                     // 16 bf16 = 32 bytes along K -> +2 in the >>4 address field
-                    const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
+                    const uint32_t acc = (i > 0 || k > 0) ? 1u : 0u;
                     mma_f16(tmem, a_hi + 2 * k, b_hi + 2 * k, idesc, acc);
                     if (SPLIT) {
                         const uint64_t a_lo = desc_kmajor_sw128(st + a_bytes + b_bytes);
@@ -297,7 +314,8 @@ __global__ void __launch_bounds__(128) direct_f32_kernel(const float* __restrict
 }  // namespace
 
 size_t direct_smem_bytes(int ncols, int stages, bool split) {
-    const size_t stage = ((size_t)kBM * kBK * 2 + (size_t)ncols * kBK * 2) * (split ? 2 : 1);
+    const size_t brows = (size_t)(ncols + 63) / 64 * 64;
+    const size_t stage = ((size_t)kBM * kBK * 2 + brows * kBK * 2) * (split ? 2 : 1);
     return stage * stages + 1024;  // + alignment slack
 }
 
@@ -359,6 +377,24 @@ cudaError_t direct_launch_f32(const float* x, int64_t ld_x, const float2* bank, 
     const size_t smem = (size_t)(2 * L.h_group + 1) * sizeof(float2);
     direct_f32_kernel<<<grid, 128, smem, st>>>(x, ld_x, bank, L, d_h);
     return cudaGetLastError();
+}
+
+int direct_schedule(const int32_t* h_desc, int n, int h_group, int k_pad, int2* out) {
+    const int nkb = k_pad / kBK;
+    const int center = h_group / kBK;
+    int steps = 0;
+    for (int r = 0; r < 2 * nkb; ++r) {
+        // centre, centre-1, centre+1, centre-2, centre+2, ...
+        const int kb = center + ((r & 1) ? -((r + 1) >> 1) : (r >> 1));
+        if (kb < 0 || kb >= nkb) continue;
+        const int t0 = kb * kBK - h_group, t1 = t0 + kBK - 1;
+        const int d = (t0 <= 0 && t1 >= 0) ? 0 : std::min(std::abs(t0), std::abs(t1));
+        int cnt = 0;
+        while (cnt < n && h_desc[cnt] >= d) ++cnt;  // supports are in descending order
+        if (cnt == 0) continue;
+        out[steps++] = make_int2(kb, (2 * cnt + 15) / 16 * 16);
+    }
+    return steps;
 }
 
 cudaError_t direct_prepare_f32(size_t smem) {

@@ -20,7 +20,7 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 
 constexpr int kMaxDevices = 64;
 constexpr int kMaxScales = 1024;
-constexpr int kScalesPerGroup = 64;      // N = 128 columns per GEMM
+constexpr int kScalesPerGroup = 128;     // N = 256 columns per GEMM
 constexpr double kEpsTaps = 1e-9;        // tap truncation, as the planned direct path
 constexpr int kMaxTaps = 4096;
 
@@ -124,10 +124,10 @@ cwth_status cwth_execute_direct_noalloc(const cwth_morlet* w, const double* scal
         if (rup(2 * (int64_t)hs[s] + 1, 64) > kMaxTaps)
             return fail(CWTH_ERR_UNSUPPORTED, "a scale needs more than 4096 taps");
     }
-    for (int32_t i = 1; i < S; ++i) {  // insertion sort by support
+    for (int32_t i = 1; i < S; ++i) {  // insertion sort, descending support
         const int32_t v = order[i];
         int32_t j = i - 1;
-        while (j >= 0 && hs[order[j]] > hs[v]) {
+        while (j >= 0 && hs[order[j]] < hs[v]) {
             order[j + 1] = order[j];
             --j;
         }
@@ -142,9 +142,9 @@ cwth_status cwth_execute_direct_noalloc(const cwth_morlet* w, const double* scal
     const int n_groups = (S + kScalesPerGroup - 1) / kScalesPerGroup;
     int32_t front = 0, max_taps = 0;
     for (int g = 0; g < n_groups; ++g) {
-        const int last = std::min(S, (g + 1) * kScalesPerGroup) - 1;
-        front = std::max(front, h_sorted[last]);
-        max_taps = std::max<int32_t>(max_taps, (int32_t)rup(2 * (int64_t)h_sorted[last] + 1, 64));
+        const int first = g * kScalesPerGroup;
+        front = std::max(front, h_sorted[first]);
+        max_taps = std::max<int32_t>(max_taps, (int32_t)rup(2 * (int64_t)h_sorted[first] + 1, 64));
     }
     const int64_t frames_max = (max_len + hop - 1) / hop;
     const int64_t rows_per_clip = (2 * (int64_t)front + frames_max * hop + max_taps + hop - 1) / hop;
@@ -163,6 +163,7 @@ cwth_status cwth_execute_direct_noalloc(const cwth_morlet* w, const double* scal
     const size_t o_rows = take(sizeof(int32_t) * S);
     const size_t o_h = take(sizeof(int32_t) * S);
     const size_t o_sc = take(sizeof(double) * S);
+    const size_t o_sched = take(sizeof(int2) * (kMaxTaps / 64) * ((kMaxScales + kScalesPerGroup - 1) / kScalesPerGroup));
     size_t o_bank[(kMaxScales + kScalesPerGroup - 1) / kScalesPerGroup];
     int32_t ncols[(kMaxScales + kScalesPerGroup - 1) / kScalesPerGroup];
     int32_t kpad[(kMaxScales + kScalesPerGroup - 1) / kScalesPerGroup];
@@ -170,7 +171,7 @@ cwth_status cwth_execute_direct_noalloc(const cwth_morlet* w, const double* scal
         const int first = g * kScalesPerGroup;
         const int n = std::min(S, first + kScalesPerGroup) - first;
         ncols[g] = (int32_t)rup(2 * n, 16);
-        kpad[g] = (int32_t)rup(2 * (int64_t)h_sorted[first + n - 1] + 1, 64);
+        kpad[g] = (int32_t)rup(2 * (int64_t)h_sorted[first] + 1, 64);
         o_bank[g] = take((size_t)ncols[g] * kpad[g] * 2 * sizeof(__nv_bfloat16));
     }
     if (total_rows > (int64_t(1) << 31) - 256)
@@ -210,6 +211,18 @@ cwth_status cwth_execute_direct_noalloc(const cwth_morlet* w, const double* scal
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_sc, sc, sizeof(double) * S, cudaMemcpyHostToDevice, strm);
     if (e != cudaSuccess) return fail_cuda(e);
 
+    // Centre-out K schedules of all groups, one slot of kMaxTaps/64 steps each.
+    int2 sched[(kMaxScales + kScalesPerGroup - 1) / kScalesPerGroup][kMaxTaps / 64];
+    int32_t nsteps[(kMaxScales + kScalesPerGroup - 1) / kScalesPerGroup];
+    int2* d_sched = (int2*)(base + o_sched);
+    for (int g = 0; g < n_groups; ++g) {
+        const int first = g * kScalesPerGroup;
+        const int n = std::min(S, first + kScalesPerGroup) - first;
+        nsteps[g] = cwth::direct_schedule(h_sorted + first, n, h_sorted[first], kpad[g], sched[g]);
+    }
+    e = cudaMemcpyAsync(d_sched, sched, sizeof(sched[0]) * n_groups, cudaMemcpyHostToDevice, strm);
+    if (e != cudaSuccess) return fail_cuda(e);
+
     const bool split = precision == CWTH_PREC_BF16X2;
     for (int g = 0; g < n_groups; ++g) {
         const int first = g * kScalesPerGroup;
@@ -217,7 +230,7 @@ cwth_status cwth_execute_direct_noalloc(const cwth_morlet* w, const double* scal
         __nv_bfloat16* bhi = (__nv_bfloat16*)(base + o_bank[g]);
         __nv_bfloat16* blo = bhi + (size_t)ncols[g] * kpad[g];
         e = cwth::direct_make_bank(d_sc + first, d_h + first, n, ncols[g], kpad[g],
-                                   h_sorted[first + n - 1], w->bandwidth, w->center_freq, bhi,
+                                   h_sorted[first], w->bandwidth, w->center_freq, bhi,
                                    blo, nullptr, strm);
         if (e != cudaSuccess) return fail_cuda(e);
     }
@@ -240,15 +253,15 @@ cwth_status cwth_execute_direct_noalloc(const cwth_morlet* w, const double* scal
     for (int g = 0; g < n_groups; ++g) {
         const int first = g * kScalesPerGroup;
         const int n = std::min(S, first + kScalesPerGroup) - first;
-        const int32_t hg = h_sorted[first + n - 1];
+        const int32_t hg = h_sorted[first];
         __nv_bfloat16* bhi = (__nv_bfloat16*)(base + o_bank[g]);
         __nv_bfloat16* blo = bhi + (size_t)ncols[g] * kpad[g];
         CUtensorMap maps[4];
         const int64_t aoff = front - hg;
         if (!encode(&maps[0], d_xhi + aoff, kpad[g], total_rows, (uint64_t)hop * 2, 128) ||
             !encode(&maps[1], d_xlo + aoff, kpad[g], total_rows, (uint64_t)hop * 2, 128) ||
-            !encode(&maps[2], bhi, kpad[g], ncols[g], (uint64_t)kpad[g] * 2, ncols[g]) ||
-            !encode(&maps[3], blo, kpad[g], ncols[g], (uint64_t)kpad[g] * 2, ncols[g]))
+            !encode(&maps[2], bhi, kpad[g], ncols[g], (uint64_t)kpad[g] * 2, 64) ||
+            !encode(&maps[3], blo, kpad[g], ncols[g], (uint64_t)kpad[g] * 2, 64))
             return fail(CWTH_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled rejected a tensor map");
         L.ncols = ncols[g];
         L.k_pad = kpad[g];
@@ -256,6 +269,8 @@ cwth_status cwth_execute_direct_noalloc(const cwth_morlet* w, const double* scal
         L.n_scales = n;
         L.rows = d_rows + first;
         L.stages = cwth::direct_max_stages(ncols[g], split);
+        L.sched = d_sched + (size_t)g * (kMaxTaps / 64);
+        L.nsteps = nsteps[g];
         uint32_t tc = 32;
         while (tc < (uint32_t)ncols[g]) tc <<= 1;
         L.tmem_cols = tc;
