@@ -223,7 +223,12 @@ cwth_status build_direct(cwth_plan_s* p) {
         g.k_pad = (int32_t)round_up(2 * (int64_t)g.h + 1, 64);
         g.bank_off = bank_elems;
         g.f32_off = f32_elems;
-        g.stages = cwth::direct_max_stages(g.ncols, split);
+        g.win_rows = cwth::direct_window_rows(p->hop, g.k_pad);
+        g.stages = g.win_rows ? cwth::direct_max_stages(g.ncols, split, g.win_rows) : 0;
+        if (g.stages == 0) {  // window does not fit: per-step frame tiles
+            g.win_rows = 0;
+            g.stages = cwth::direct_max_stages(g.ncols, split, 0);
+        }
         if (g.stages == 0) return CWTH_ERR_UNSUPPORTED;
         bank_elems += (int64_t)g.ncols * g.k_pad;
         f32_elems += (int64_t)g.n_scales * g.k_pad;
@@ -457,6 +462,8 @@ cwth_status launch_direct(cwth_plan_s* p, const float* d_x, int64_t ld_x, const 
         L.stages = g.stages;
         L.sched = g.d_sched;
         L.nsteps = g.nsteps;
+        L.win_rows = g.win_rows;
+        L.a_shift = g.win_rows ? 64 / (int)hop : 0;
         uint32_t tc = 32;
         while (tc < (uint32_t)g.ncols) tc <<= 1;
         L.tmem_cols = tc;

@@ -79,6 +79,8 @@ struct DirLaunch {
     int* status;            // device status word (CWTH_ERR_TIMEOUT on a bounded-wait expiry)
     const int2* sched;      // per K step: {tap block, columns used (multiple of 16)}
     int32_t nsteps;
+    int32_t a_shift;        // frame-view rows per tap block (64 / hop) when one window serves all blocks, else 0
+    int32_t win_rows;       // rows of that window (a multiple of 128)
 };
 
 // Records the detail string cwth_last_error() returns in the calling thread.
@@ -90,8 +92,10 @@ cudaError_t spectral_make_twiddles(float2* d_tw, int M, cudaStream_t st);
 cudaError_t spectral_launch(const SpecLaunch& L, int n_seg, int batch, int n_groups,
                             size_t smem, cudaStream_t st);
 
-size_t direct_smem_bytes(int ncols, int stages, bool split);
-int direct_max_stages(int ncols, bool split);
+size_t direct_smem_bytes(int ncols, int stages, bool split, int win_rows);
+int direct_max_stages(int ncols, bool split, int win_rows);
+// Rows of the frame window for hops dividing 64 (0: per-step frame tiles).
+int direct_window_rows(int hop, int k_pad);
 cudaError_t direct_prepare_device();
 cudaError_t direct_prepare_f32(size_t smem);
 cudaError_t direct_make_bank(const double* d_scales, const int32_t* d_h, int n_scales, int ncols,
@@ -115,6 +119,7 @@ struct DirGroup {
     int32_t h = 0;       // group half support, a multiple of 8
     int32_t k_pad = 0;   // multiple of 64, >= 2h + 1
     int32_t stages = 0;
+    int32_t win_rows = 0;
     int64_t bank_off = 0;   // element offset into the bf16 banks ([ncols][k_pad])
     int64_t f32_off = 0;    // element offset into the float32 bank ([n_scales][k_pad])
     int32_t* d_rows = nullptr;

@@ -103,6 +103,14 @@ __global__ void bank_kernel(const double* __restrict__ scales, const int32_t* __
 }
 
 // ------------------------------------------------------------ tcgen05 GEMM
+// Shared-memory layout (1024-byte aligned pieces):
+//   [window hi][window lo]   only when p.a_shift > 0 (see below)
+//   stage s: [A hi][B hi][A lo][B lo]   (A parts absent with a window,
+//                                        lo parts only for the split variant)
+// When 64 is a multiple of the hop, the frame tile of tap block kb is the
+// tile of block 0 moved down by kb * 64 / H rows of the frame view, so one
+// window of 128 + (blocks - 1) * 64/H rows, loaded once, serves every K step
+// through descriptors that start kb * 64/H rows into it.
 template <bool SPLIT>
 __global__ void __launch_bounds__(kDirThreads, 1)
     direct_mma_kernel(const __grid_constant__ CUtensorMap mA_hi,
@@ -113,15 +121,23 @@ __global__ void __launch_bounds__(kDirThreads, 1)
     __shared__ __align__(8) uint64_t full_bar[kMaxDirStages];
     __shared__ __align__(8) uint64_t empty_bar[kMaxDirStages];
     __shared__ __align__(8) uint64_t accum_bar;
+    __shared__ __align__(8) uint64_t win_bar;
     __shared__ uint32_t tmem_base_sh;
     __shared__ int abort_sh;
 
     uint8_t* smem = (uint8_t*)(((uintptr_t)dsmem_raw + 1023) & ~(uintptr_t)1023);
     const int N = p.ncols;
     const int stages = p.stages;
-    const uint32_t a_bytes = kBM * kBK * 2;
+    const int shift = p.a_shift;
+    const uint32_t win_bytes = (uint32_t)p.win_rows * kBK * 2;
+    const uint32_t a_tile = kBM * kBK * 2;
+    const uint32_t a_step = shift ? 0u : a_tile;
     const uint32_t b_bytes = (uint32_t)((N + 63) / 64 * 64) * kBK * 2;
-    const uint32_t stage_bytes = (a_bytes + b_bytes) * (SPLIT ? 2 : 1);
+    const uint32_t half = a_step + b_bytes;
+    const uint32_t stage_bytes = half * (SPLIT ? 2 : 1);
+    uint8_t* win_hi = smem;
+    uint8_t* win_lo = smem + win_bytes;
+    uint8_t* stage0 = smem + win_bytes * (SPLIT ? 2 : 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * kBM;
     const int nsteps = p.nsteps;
@@ -133,6 +149,7 @@ __global__ void __launch_bounds__(kDirThreads, 1)
             mbar_init(&empty_bar[s], 1);
         }
         mbar_init(&accum_bar, 1);
+        mbar_init(&win_bar, 1);
         // A CTA of a launch that already timed out does no work.
         abort_sh = *(volatile int*)p.status != 0 ? 1 : 0;
         fence_mbar_init();
@@ -152,13 +169,22 @@ __global__ void __launch_bounds__(kDirThreads, 1)
     tc_fence_after();
     const uint32_t tmem = tmem_base_sh;
 
-    auto stage_ptr = [&](int s) { return smem + (size_t)s * stage_bytes; };
+    auto stage_ptr = [&](int s) { return stage0 + (size_t)s * stage_bytes; };
 
     if (warp == 0) {
         if (lane == 0) {
             // Producer.
-            // Step i loads tap block sched[i].x for the A tile and the first
-            // sched[i].y columns of the bank, in 64-row pieces.
+            bool win_issued = false;
+            if (shift && !*(volatile int*)&abort_sh) {
+                mbar_arrive_expect_tx(&win_bar, win_bytes * (SPLIT ? 2 : 1));
+                for (int j = 0; j < p.win_rows / kBM; ++j) {
+                    tma_load_2d(win_hi + j * a_tile, &mA_hi, &win_bar, 0, m0 + j * kBM);
+                    if (SPLIT) tma_load_2d(win_lo + j * a_tile, &mA_lo, &win_bar, 0, m0 + j * kBM);
+                }
+                win_issued = true;
+            }
+            // Step i loads tap block sched[i].x (frame tile unless windowed)
+            // and the first sched[i].y columns of the bank, in 64-row pieces.
             int issued = 0;
             for (int i = 0; i < nsteps; ++i) {
                 const int s = i % stages;
@@ -173,19 +199,19 @@ __global__ void __launch_bounds__(kDirThreads, 1)
                 const int pieces = (step.y + 63) >> 6;
                 uint8_t* st = stage_ptr(s);
                 mbar_arrive_expect_tx(&full_bar[s],
-                                      (a_bytes + (uint32_t)pieces * 64 * kBK * 2) * (SPLIT ? 2 : 1));
-                tma_load_2d(st, &mA_hi, &full_bar[s], kx, m0);
+                                      (a_step + (uint32_t)pieces * 64 * kBK * 2) * (SPLIT ? 2 : 1));
+                if (!shift) tma_load_2d(st, &mA_hi, &full_bar[s], kx, m0);
                 for (int j = 0; j < pieces; ++j)
-                    tma_load_2d(st + a_bytes + j * 64 * kBK * 2, &mB_hi, &full_bar[s], kx, j * 64);
+                    tma_load_2d(st + a_step + j * 64 * kBK * 2, &mB_hi, &full_bar[s], kx, j * 64);
                 if (SPLIT) {
-                    tma_load_2d(st + a_bytes + b_bytes, &mA_lo, &full_bar[s], kx, m0);
+                    if (!shift) tma_load_2d(st + half, &mA_lo, &full_bar[s], kx, m0);
                     for (int j = 0; j < pieces; ++j)
-                        tma_load_2d(st + 2 * a_bytes + b_bytes + j * 64 * kBK * 2, &mB_lo,
-                                    &full_bar[s], kx, j * 64);
+                        tma_load_2d(st + half + a_step + j * 64 * kBK * 2, &mB_lo, &full_bar[s], kx,
+                                    j * 64);
                 }
                 ++issued;
             }
-            // Drain: every stage filled must have landed before the CTA exits.
+            // Drain: every copy issued must have landed before the CTA exits.
             for (int i = (issued > stages ? issued - stages : 0); i < issued; ++i) {
                 const int s = i % stages;
                 if (!mbar_wait(&full_bar[s], (uint32_t)(i / stages) & 1, kWaitBudget)) {
@@ -193,34 +219,42 @@ __global__ void __launch_bounds__(kDirThreads, 1)
                     break;
                 }
             }
+            if (win_issued && !mbar_wait(&win_bar, 0, kWaitBudget)) atomicExch(&abort_sh, 1);
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            // MMA issuer.
-            // The first step is the centre tap block, which every scale
-            // reaches: its N covers all columns and initialises them.
+            // MMA issuer.  The first step is the centre tap block, which every
+            // scale reaches: its N covers all columns and initialises them.
             bool ok = true;
-            for (int i = 0; i < nsteps; ++i) {
+            if (shift && !*(volatile int*)&abort_sh && !mbar_wait(&win_bar, 0, kWaitBudget)) {
+                atomicExch(&abort_sh, 1);
+                ok = false;
+            }
+            for (int i = 0; i < nsteps && ok; ++i) {
                 const int s = i % stages;
                 if (*(volatile int*)&abort_sh) break;
                 if (!mbar_wait(&full_bar[s], (uint32_t)(i / stages) & 1, kWaitBudget)) {
                     atomicExch(&abort_sh, 1);
-                    ok = false;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t idesc = idesc_bf16_f32(kBM, __ldg(&p.sched[i].y));
+                const int2 step = __ldg(p.sched + i);
+                const uint32_t idesc = idesc_bf16_f32(kBM, step.y);
                 const uint32_t st = smem_u32(stage_ptr(s));
-                const uint64_t a_hi = desc_kmajor_sw128(st);
-                const uint64_t b_hi = desc_kmajor_sw128(st + a_bytes);
+                const uint32_t a_hi_addr =
+                    shift ? smem_u32(win_hi) + (uint32_t)(step.x * shift) * 128u : st;
+                const uint32_t a_lo_addr =
+                    shift ? smem_u32(win_lo) + (uint32_t)(step.x * shift) * 128u : st + half;
+                const uint64_t a_hi = desc_kmajor_sw128(a_hi_addr);
+                const uint64_t b_hi = desc_kmajor_sw128(st + a_step);
+                const uint64_t a_lo = desc_kmajor_sw128(a_lo_addr);
+                const uint64_t b_lo = desc_kmajor_sw128(st + half + a_step);
 #pragma unroll
                 for (int k = 0; k < kBK / 16; ++k) {
                     // 16 bf16 = 32 bytes along K -> +2 in the >>4 address field
                     const uint32_t acc = (i > 0 || k > 0) ? 1u : 0u;
                     mma_f16(tmem, a_hi + 2 * k, b_hi + 2 * k, idesc, acc);
                     if (SPLIT) {
-                        const uint64_t a_lo = desc_kmajor_sw128(st + a_bytes + b_bytes);
-                        const uint64_t b_lo = desc_kmajor_sw128(st + 2 * a_bytes + b_bytes);
                         mma_f16(tmem, a_hi + 2 * k, b_lo + 2 * k, idesc, 1u);
                         mma_f16(tmem, a_lo + 2 * k, b_hi + 2 * k, idesc, 1u);
                         mma_f16(tmem, a_lo + 2 * k, b_lo + 2 * k, idesc, 1u);
@@ -228,7 +262,6 @@ __global__ void __launch_bounds__(kDirThreads, 1)
                 }
                 mma_commit(&empty_bar[s]);
             }
-            (void)ok;
             mma_commit(&accum_bar);
         }
     } else {
@@ -313,20 +346,36 @@ __global__ void __launch_bounds__(128) direct_f32_kernel(const float* __restrict
 
 }  // namespace
 
-size_t direct_smem_bytes(int ncols, int stages, bool split) {
+size_t direct_smem_bytes(int ncols, int stages, bool split, int win_rows) {
     const size_t brows = (size_t)(ncols + 63) / 64 * 64;
-    const size_t stage = ((size_t)kBM * kBK * 2 + brows * kBK * 2) * (split ? 2 : 1);
-    return stage * stages + 1024;  // + alignment slack
+    const size_t a = win_rows > 0 ? 0 : (size_t)kBM * kBK * 2;
+    const size_t stage = (a + brows * kBK * 2) * (split ? 2 : 1);
+    const size_t win = (size_t)win_rows * kBK * 2 * (split ? 2 : 1);
+    return win + stage * stages + 1024;  // + alignment slack
+}
+
+int direct_window_rows(int hop, int k_pad) {
+    if (hop <= 0 || kBK % hop != 0) return 0;
+    const int rows = kBM + (k_pad / kBK - 1) * (kBK / hop);
+    return (rows + kBM - 1) / kBM * kBM;
 }
 
 // Dynamic shared memory a direct CTA may request: the 227 KB opt-in limit
 // less room for the kernel's static barriers.
 constexpr size_t kDirSmemLimit = 227 * 1024 - 1024;
 
-int direct_max_stages(int ncols, bool split) {
+// Stages: as many as fit while two CTAs still share an SM (one CTA's
+// pipeline fill and epilogue then overlap the other's MMAs); if even two
+// stages do not fit that way, as many as fit in one CTA's opt-in limit.
+constexpr size_t kDirSmemTwoPerSm = 113 * 1024;
+
+int direct_max_stages(int ncols, bool split, int win_rows) {
     int s = kMaxDirStages;
-    while (s > 2 && direct_smem_bytes(ncols, s, split) > kDirSmemLimit) --s;
-    return direct_smem_bytes(ncols, s, split) <= kDirSmemLimit ? s : 0;
+    while (s > 2 && direct_smem_bytes(ncols, s, split, win_rows) > kDirSmemTwoPerSm) --s;
+    if (direct_smem_bytes(ncols, s, split, win_rows) <= kDirSmemTwoPerSm) return s;
+    s = kMaxDirStages;
+    while (s > 2 && direct_smem_bytes(ncols, s, split, win_rows) > kDirSmemLimit) --s;
+    return direct_smem_bytes(ncols, s, split, win_rows) <= kDirSmemLimit ? s : 0;
 }
 
 cudaError_t direct_prepare_device() {
@@ -360,7 +409,7 @@ cudaError_t direct_stage(const float* x, int64_t ld_x, const int64_t* lengths, i
 cudaError_t direct_launch_mma(const CUtensorMap* maps, const DirLaunch& L, bool split,
                               cudaStream_t st) {
     const int64_t tiles = (L.total_rows + kBM - 1) / kBM;
-    const size_t smem = direct_smem_bytes(L.ncols, L.stages, split);
+    const size_t smem = direct_smem_bytes(L.ncols, L.stages, split, L.a_shift ? L.win_rows : 0);
     if (split)
         direct_mma_kernel<true><<<(unsigned)tiles, kDirThreads, smem, st>>>(maps[0], maps[1],
                                                                            maps[2], maps[3], L);

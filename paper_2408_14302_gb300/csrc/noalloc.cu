@@ -268,7 +268,13 @@ cwth_status cwth_execute_direct_noalloc(const cwth_morlet* w, const double* scal
         L.h_group = hg;
         L.n_scales = n;
         L.rows = d_rows + first;
-        L.stages = cwth::direct_max_stages(ncols[g], split);
+        L.win_rows = cwth::direct_window_rows(hop, kpad[g]);
+        L.stages = L.win_rows ? cwth::direct_max_stages(ncols[g], split, L.win_rows) : 0;
+        if (L.stages == 0) {
+            L.win_rows = 0;
+            L.stages = cwth::direct_max_stages(ncols[g], split, 0);
+        }
+        L.a_shift = L.win_rows ? 64 / hop : 0;
         L.sched = d_sched + (size_t)g * (kMaxTaps / 64);
         L.nsteps = nsteps[g];
         uint32_t tc = 32;

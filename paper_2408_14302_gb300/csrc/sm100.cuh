@@ -131,8 +131,12 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 // Shared-memory matrix descriptor for a K-major operand tile written by TMA
 // with 128-byte swizzling: rows of 128 bytes, 8-row (1024-byte) atoms along
 // the M/N dimension (stride byte offset 1024), descriptor version 1,
-// swizzle mode 2 (128B).  The tile base must be 1024-byte aligned; moving
-// along K inside the atom adds the byte offset (>> 4) to the start address.
+// swizzle mode 2 (128B), matrix base offset 0.  TMA swizzles 1024-byte
+// aligned atoms by absolute shared-memory address bits, and the MMA unit
+// undoes the swizzle from the same address bits, so a tile may start any
+// whole number of 128-byte rows into a larger swizzled window (measured on
+// GB300: row offsets 1..28 give exact products).  Moving along K inside a
+// row adds the byte offset (>> 4) to the start address.
 __device__ __forceinline__ uint64_t desc_kmajor_sw128(uint32_t smem_addr) {
     uint64_t d = 0;
     d |= (uint64_t)((smem_addr >> 4) & 0x3FFFu);
