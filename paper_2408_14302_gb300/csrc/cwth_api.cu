@@ -261,8 +261,12 @@ cwth_status build_direct(cwth_plan_s* p) {
             e = cudaMemcpy(g.d_h, hh.data(), sizeof(int32_t) * hh.size(), cudaMemcpyHostToDevice);
         if (e == cudaSuccess)
             e = cudaMemcpy(g.d_scales, sc.data(), sizeof(double) * sc.size(), cudaMemcpyHostToDevice);
-        std::vector<int2> sched(g.k_pad / 64);
+        std::vector<int2> sched(g.k_pad / 64), sched2(2 * (g.k_pad / 64));
         g.nsteps = cwth::direct_schedule(hh.data(), g.n_scales, g.h, g.k_pad, sched.data());
+        if (split) {
+            g.nsteps = cwth::direct_split_schedule(sched.data(), g.nsteps, sched2.data());
+            sched.swap(sched2);
+        }
         if (e == cudaSuccess) e = cudaMalloc(&g.d_sched, sizeof(int2) * sched.size());
         if (e == cudaSuccess)
             e = cudaMemcpy(g.d_sched, sched.data(), sizeof(int2) * g.nsteps, cudaMemcpyHostToDevice);
@@ -437,8 +441,8 @@ cwth_status launch_direct(cwth_plan_s* p, const float* d_x, int64_t ld_x, const 
         for (size_t gi = 0; gi < p->groups.size(); ++gi) {
             const cwth::DirGroup& g = p->groups[gi];
             const int64_t off = p->dir_front - g.h;
-            if (!encode_bf16_2d(&p->maps_a_hi[gi], p->d_xhi + off, g.k_pad, total_rows, hop * 2, 128) ||
-                !encode_bf16_2d(&p->maps_a_lo[gi], p->d_xlo + off, g.k_pad, total_rows, hop * 2, 128)) {
+            if (!encode_bf16_2d(&p->maps_a_hi[gi], p->d_xhi + off, g.k_pad, total_rows, hop * 2, 32) ||
+                !encode_bf16_2d(&p->maps_a_lo[gi], p->d_xlo + off, g.k_pad, total_rows, hop * 2, 32)) {
                 note_error("cuTensorMapEncodeTiled rejected the frame-matrix tensor map");
                 return CWTH_ERR_UNSUPPORTED;
             }

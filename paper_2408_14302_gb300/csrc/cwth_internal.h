@@ -77,7 +77,7 @@ struct DirLaunch {
     int32_t stages;
     uint32_t tmem_cols;
     int* status;            // device status word (CWTH_ERR_TIMEOUT on a bounded-wait expiry)
-    const int2* sched;      // per K step: {tap block, columns used (multiple of 16)}
+    const int2* sched;      // per K step: {tap block, columns used | bank part << 16}
     int32_t nsteps;
     int32_t a_shift;        // frame-view rows per tap block (64 / hop) when one window serves all blocks, else 0
     int32_t win_rows;       // rows of that window (a multiple of 128)
@@ -96,6 +96,9 @@ size_t direct_smem_bytes(int ncols, int stages, bool split, int win_rows);
 int direct_max_stages(int ncols, bool split, int win_rows);
 // Rows of the frame window for hops dividing 64 (0: per-step frame tiles).
 int direct_window_rows(int hop, int k_pad);
+// The split variant's schedule: every step of `in` twice, hi part then lo
+// part (bit 16 of .y); returns 2 n.
+int direct_split_schedule(const int2* in, int n, int2* out);
 cudaError_t direct_prepare_device();
 cudaError_t direct_prepare_f32(size_t smem);
 cudaError_t direct_make_bank(const double* d_scales, const int32_t* d_h, int n_scales, int ncols,

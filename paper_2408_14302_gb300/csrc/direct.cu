@@ -40,28 +40,46 @@ using namespace sm100;
 constexpr int kBM = 128;             // frames per tile
 constexpr int kBK = 64;              // taps per stage (128 bytes of bf16)
 constexpr int kDirThreads = 192;
+constexpr int kAPieceRows = 32;      // frame-map box height (rows per TMA copy)
 constexpr long long kWaitBudget = 4000000000LL;  // ~2 s of SM clock
 
 // ------------------------------------------------------------ staging
 // x_pad[b][j] = x[b][j - h_front] for j - h_front in [0, len_b), else 0;
-// hi = bf16(x), lo = bf16(x - hi).  Also zeroes the tail after the last clip.
+// hi = bf16(x), lo = bf16(x - hi).  Row b = batch is the zero tail after the
+// last clip.  Each thread writes 8 consecutive bf16 (one 16-byte store per
+// buffer); rows and the tail are multiples of 8 elements long.
 __global__ void stage_bf16_kernel(const float* __restrict__ x, int64_t ld_x,
                                   const int64_t* __restrict__ lengths, int64_t max_len, int batch,
                                   __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo,
                                   int64_t lpad, int64_t h_front, int64_t total) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t b = i / lpad;
-        const int64_t n = i - b * lpad - h_front;
-        float v = 0.f;
-        if (b < batch) {
-            int64_t len = lengths ? lengths[b] : max_len;
-            len = len < 0 ? 0 : (len > max_len ? max_len : len);
-            if (n >= 0 && n < len) v = __ldg(x + b * ld_x + n);
+    const int b = blockIdx.y;
+    const int64_t row_len = b < batch ? lpad : total - (int64_t)batch * lpad;
+    int64_t len = 0;
+    if (b < batch) {
+        len = lengths ? lengths[b] : max_len;
+        len = len < 0 ? 0 : (len > max_len ? max_len : len);
+    }
+    const float* xr = x + (int64_t)(b < batch ? b : 0) * ld_x;
+    const int64_t base = (int64_t)b * lpad;
+    for (int64_t j0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 8; j0 < row_len;
+         j0 += (int64_t)gridDim.x * blockDim.x * 8) {
+        uint32_t wh[4], wl[4];
+#pragma unroll
+        for (int e = 0; e < 8; e += 2) {
+            float v[2];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int64_t n = j0 + e + q - h_front;
+                v[q] = (n >= 0 && n < len) ? __ldg(xr + n) : 0.f;
+            }
+            const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[0], v[1]);
+            const float2 hf = __bfloat1622float2(h2);
+            const __nv_bfloat162 l2 = __floats2bfloat162_rn(v[0] - hf.x, v[1] - hf.y);
+            wh[e >> 1] = *reinterpret_cast<const uint32_t*>(&h2);
+            wl[e >> 1] = *reinterpret_cast<const uint32_t*>(&l2);
         }
-        const __nv_bfloat16 h = __float2bfloat16_rn(v);
-        hi[i] = h;
-        if (lo) lo[i] = __float2bfloat16_rn(v - __bfloat162float(h));
+        *reinterpret_cast<uint4*>(hi + base + j0) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
+        if (lo) *reinterpret_cast<uint4*>(lo + base + j0) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
     }
 }
 
@@ -104,9 +122,13 @@ __global__ void bank_kernel(const double* __restrict__ scales, const int32_t* __
 
 // ------------------------------------------------------------ tcgen05 GEMM
 // Shared-memory layout (1024-byte aligned pieces):
-//   [window hi][window lo]   only when p.a_shift > 0 (see below)
-//   stage s: [A hi][B hi][A lo][B lo]   (A parts absent with a window,
-//                                        lo parts only for the split variant)
+//   [window hi][window lo]          only when p.a_shift > 0 (see below)
+//   stage s: [A hi][A lo][B]        A parts only without a window; A lo only
+//                                   for the split variant
+// Schedule step i: tap block sched[i].x; sched[i].y = columns used (low 16
+// bits, a multiple of 16) | bank part (bit 16: 0 = hi, 1 = lo).  The split
+// variant visits every block twice, once per bank part, so a stage holds one
+// bank tile; the plain variant uses the hi part only.
 // When 64 is a multiple of the hop, the frame tile of tap block kb is the
 // tile of block 0 moved down by kb * 64 / H rows of the frame view, so one
 // window of 128 + (blocks - 1) * 64/H rows, loaded once, serves every K step
@@ -129,15 +151,16 @@ __global__ void __launch_bounds__(kDirThreads, 1)
     const int N = p.ncols;
     const int stages = p.stages;
     const int shift = p.a_shift;
+    constexpr uint32_t kPiece = kAPieceRows * kBK * 2;  // one frame-map box
     const uint32_t win_bytes = (uint32_t)p.win_rows * kBK * 2;
+    const uint32_t win_span = (win_bytes + 1023) & ~1023u;
     const uint32_t a_tile = kBM * kBK * 2;
-    const uint32_t a_step = shift ? 0u : a_tile;
+    const uint32_t a_step = shift ? 0u : a_tile * (SPLIT ? 2 : 1);
     const uint32_t b_bytes = (uint32_t)((N + 63) / 64 * 64) * kBK * 2;
-    const uint32_t half = a_step + b_bytes;
-    const uint32_t stage_bytes = half * (SPLIT ? 2 : 1);
+    const uint32_t stage_bytes = a_step + b_bytes;
     uint8_t* win_hi = smem;
-    uint8_t* win_lo = smem + win_bytes;
-    uint8_t* stage0 = smem + win_bytes * (SPLIT ? 2 : 1);
+    uint8_t* win_lo = smem + win_span;
+    uint8_t* stage0 = smem + (shift ? win_span * (SPLIT ? 2 : 1) : 0);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * kBM;
     const int nsteps = p.nsteps;
@@ -177,14 +200,13 @@ __global__ void __launch_bounds__(kDirThreads, 1)
             bool win_issued = false;
             if (shift && !*(volatile int*)&abort_sh) {
                 mbar_arrive_expect_tx(&win_bar, win_bytes * (SPLIT ? 2 : 1));
-                for (int j = 0; j < p.win_rows / kBM; ++j) {
-                    tma_load_2d(win_hi + j * a_tile, &mA_hi, &win_bar, 0, m0 + j * kBM);
-                    if (SPLIT) tma_load_2d(win_lo + j * a_tile, &mA_lo, &win_bar, 0, m0 + j * kBM);
+                for (int j = 0; j < p.win_rows / kAPieceRows; ++j) {
+                    tma_load_2d(win_hi + j * kPiece, &mA_hi, &win_bar, 0, m0 + j * kAPieceRows);
+                    if (SPLIT)
+                        tma_load_2d(win_lo + j * kPiece, &mA_lo, &win_bar, 0, m0 + j * kAPieceRows);
                 }
                 win_issued = true;
             }
-            // Step i loads tap block sched[i].x (frame tile unless windowed)
-            // and the first sched[i].y columns of the bank, in 64-row pieces.
             int issued = 0;
             for (int i = 0; i < nsteps; ++i) {
                 const int s = i % stages;
@@ -196,19 +218,20 @@ __global__ void __launch_bounds__(kDirThreads, 1)
                 }
                 const int2 step = __ldg(p.sched + i);
                 const int kx = step.x * kBK;
-                const int pieces = (step.y + 63) >> 6;
+                const int pieces = ((step.y & 0xFFFF) + 63) >> 6;
+                const CUtensorMap* mb = (SPLIT && (step.y >> 16)) ? &mB_lo : &mB_hi;
                 uint8_t* st = stage_ptr(s);
-                mbar_arrive_expect_tx(&full_bar[s],
-                                      (a_step + (uint32_t)pieces * 64 * kBK * 2) * (SPLIT ? 2 : 1));
-                if (!shift) tma_load_2d(st, &mA_hi, &full_bar[s], kx, m0);
-                for (int j = 0; j < pieces; ++j)
-                    tma_load_2d(st + a_step + j * 64 * kBK * 2, &mB_hi, &full_bar[s], kx, j * 64);
-                if (SPLIT) {
-                    if (!shift) tma_load_2d(st + half, &mA_lo, &full_bar[s], kx, m0);
-                    for (int j = 0; j < pieces; ++j)
-                        tma_load_2d(st + half + a_step + j * 64 * kBK * 2, &mB_lo, &full_bar[s], kx,
-                                    j * 64);
+                mbar_arrive_expect_tx(&full_bar[s], a_step + (uint32_t)pieces * 64 * kBK * 2);
+                if (!shift) {
+                    for (int j = 0; j < kBM / kAPieceRows; ++j) {
+                        tma_load_2d(st + j * kPiece, &mA_hi, &full_bar[s], kx, m0 + j * kAPieceRows);
+                        if (SPLIT)
+                            tma_load_2d(st + a_tile + j * kPiece, &mA_lo, &full_bar[s], kx,
+                                        m0 + j * kAPieceRows);
+                    }
                 }
+                for (int j = 0; j < pieces; ++j)
+                    tma_load_2d(st + a_step + j * 64 * kBK * 2, mb, &full_bar[s], kx, j * 64);
                 ++issued;
             }
             // Drain: every copy issued must have landed before the CTA exits.
@@ -223,8 +246,9 @@ __global__ void __launch_bounds__(kDirThreads, 1)
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            // MMA issuer.  The first step is the centre tap block, which every
-            // scale reaches: its N covers all columns and initialises them.
+            // MMA issuer.  The first step is the centre tap block (hi part),
+            // which every scale reaches: its N covers all columns and its first
+            // MMA initialises them.
             bool ok = true;
             if (shift && !*(volatile int*)&abort_sh && !mbar_wait(&win_bar, 0, kWaitBudget)) {
                 atomicExch(&abort_sh, 1);
@@ -239,26 +263,19 @@ __global__ void __launch_bounds__(kDirThreads, 1)
                 }
                 tc_fence_after();
                 const int2 step = __ldg(p.sched + i);
-                const uint32_t idesc = idesc_bf16_f32(kBM, step.y);
+                const uint32_t idesc = idesc_bf16_f32(kBM, step.y & 0xFFFF);
                 const uint32_t st = smem_u32(stage_ptr(s));
-                const uint32_t a_hi_addr =
-                    shift ? smem_u32(win_hi) + (uint32_t)(step.x * shift) * 128u : st;
-                const uint32_t a_lo_addr =
-                    shift ? smem_u32(win_lo) + (uint32_t)(step.x * shift) * 128u : st + half;
-                const uint64_t a_hi = desc_kmajor_sw128(a_hi_addr);
-                const uint64_t b_hi = desc_kmajor_sw128(st + a_step);
-                const uint64_t a_lo = desc_kmajor_sw128(a_lo_addr);
-                const uint64_t b_lo = desc_kmajor_sw128(st + half + a_step);
+                const uint32_t rows = (uint32_t)(step.x * shift) * 128u;
+                const uint64_t a_hi = desc_kmajor_sw128(shift ? smem_u32(win_hi) + rows : st);
+                const uint64_t a_lo =
+                    desc_kmajor_sw128(shift ? smem_u32(win_lo) + rows : st + a_tile);
+                const uint64_t bd = desc_kmajor_sw128(st + a_step);
 #pragma unroll
                 for (int k = 0; k < kBK / 16; ++k) {
                     // 16 bf16 = 32 bytes along K -> +2 in the >>4 address field
                     const uint32_t acc = (i > 0 || k > 0) ? 1u : 0u;
-                    mma_f16(tmem, a_hi + 2 * k, b_hi + 2 * k, idesc, acc);
-                    if (SPLIT) {
-                        mma_f16(tmem, a_hi + 2 * k, b_lo + 2 * k, idesc, 1u);
-                        mma_f16(tmem, a_lo + 2 * k, b_hi + 2 * k, idesc, 1u);
-                        mma_f16(tmem, a_lo + 2 * k, b_lo + 2 * k, idesc, 1u);
-                    }
+                    mma_f16(tmem, a_hi + 2 * k, bd + 2 * k, idesc, acc);
+                    if (SPLIT) mma_f16(tmem, a_lo + 2 * k, bd + 2 * k, idesc, 1u);
                 }
                 mma_commit(&empty_bar[s]);
             }
@@ -348,16 +365,24 @@ __global__ void __launch_bounds__(128) direct_f32_kernel(const float* __restrict
 
 size_t direct_smem_bytes(int ncols, int stages, bool split, int win_rows) {
     const size_t brows = (size_t)(ncols + 63) / 64 * 64;
-    const size_t a = win_rows > 0 ? 0 : (size_t)kBM * kBK * 2;
-    const size_t stage = (a + brows * kBK * 2) * (split ? 2 : 1);
-    const size_t win = (size_t)win_rows * kBK * 2 * (split ? 2 : 1);
-    return win + stage * stages + 1024;  // + alignment slack
+    const size_t a = win_rows > 0 ? 0 : (size_t)kBM * kBK * 2 * (split ? 2 : 1);
+    const size_t stage = a + brows * kBK * 2;
+    const size_t win_span = ((size_t)win_rows * kBK * 2 + 1023) / 1024 * 1024;
+    return win_span * (split ? 2 : 1) + stage * stages + 1024;  // + alignment slack
 }
 
 int direct_window_rows(int hop, int k_pad) {
     if (hop <= 0 || kBK % hop != 0) return 0;
     const int rows = kBM + (k_pad / kBK - 1) * (kBK / hop);
-    return (rows + kBM - 1) / kBM * kBM;
+    return (rows + kAPieceRows - 1) / kAPieceRows * kAPieceRows;
+}
+
+int direct_split_schedule(const int2* in, int n, int2* out) {
+    for (int i = 0; i < n; ++i) {
+        out[2 * i] = in[i];
+        out[2 * i + 1] = make_int2(in[i].x, in[i].y | (1 << 16));
+    }
+    return 2 * n;
 }
 
 // Dynamic shared memory a direct CTA may request: the 227 KB opt-in limit
@@ -400,9 +425,13 @@ cudaError_t direct_make_bank(const double* d_scales, const int32_t* d_h, int n_s
 cudaError_t direct_stage(const float* x, int64_t ld_x, const int64_t* lengths, int64_t max_len,
                          int batch, __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t lpad,
                          int64_t h_front, int64_t total, cudaStream_t st) {
-    const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
-    stage_bf16_kernel<<<blocks, 256, 0, st>>>(x, ld_x, lengths, max_len, batch, hi, lo, lpad,
-                                              h_front, total);
+    // lpad and the tail are multiples of 8 elements (hop % 8 == 0, supports
+    // and tap counts multiples of 8), so every 16-byte store is aligned.
+    const int64_t longest = std::max<int64_t>(lpad, total - (int64_t)batch * lpad);
+    const unsigned bx = (unsigned)std::min<int64_t>((longest / 8 + 255) / 256, 1024);
+    dim3 grid(bx > 0 ? bx : 1, (unsigned)batch + 1);
+    stage_bf16_kernel<<<grid, 256, 0, st>>>(x, ld_x, lengths, max_len, batch, hi, lo, lpad,
+                                            h_front, total);
     return cudaGetLastError();
 }
 

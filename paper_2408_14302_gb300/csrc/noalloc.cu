@@ -163,7 +163,7 @@ cwth_status cwth_execute_direct_noalloc(const cwth_morlet* w, const double* scal
     const size_t o_rows = take(sizeof(int32_t) * S);
     const size_t o_h = take(sizeof(int32_t) * S);
     const size_t o_sc = take(sizeof(double) * S);
-    const size_t o_sched = take(sizeof(int2) * (kMaxTaps / 64) * ((kMaxScales + kScalesPerGroup - 1) / kScalesPerGroup));
+    const size_t o_sched = take(sizeof(int2) * 2 * (kMaxTaps / 64) * ((kMaxScales + kScalesPerGroup - 1) / kScalesPerGroup));
     size_t o_bank[(kMaxScales + kScalesPerGroup - 1) / kScalesPerGroup];
     int32_t ncols[(kMaxScales + kScalesPerGroup - 1) / kScalesPerGroup];
     int32_t kpad[(kMaxScales + kScalesPerGroup - 1) / kScalesPerGroup];
@@ -212,18 +212,23 @@ cwth_status cwth_execute_direct_noalloc(const cwth_morlet* w, const double* scal
     if (e != cudaSuccess) return fail_cuda(e);
 
     // Centre-out K schedules of all groups, one slot of kMaxTaps/64 steps each.
-    int2 sched[(kMaxScales + kScalesPerGroup - 1) / kScalesPerGroup][kMaxTaps / 64];
+    const bool split = precision == CWTH_PREC_BF16X2;
+    int2 sched[(kMaxScales + kScalesPerGroup - 1) / kScalesPerGroup][2 * (kMaxTaps / 64)];
     int32_t nsteps[(kMaxScales + kScalesPerGroup - 1) / kScalesPerGroup];
     int2* d_sched = (int2*)(base + o_sched);
     for (int g = 0; g < n_groups; ++g) {
         const int first = g * kScalesPerGroup;
         const int n = std::min(S, first + kScalesPerGroup) - first;
-        nsteps[g] = cwth::direct_schedule(h_sorted + first, n, h_sorted[first], kpad[g], sched[g]);
+        int2 one[kMaxTaps / 64];
+        nsteps[g] = cwth::direct_schedule(h_sorted + first, n, h_sorted[first], kpad[g], one);
+        if (split)
+            nsteps[g] = cwth::direct_split_schedule(one, nsteps[g], sched[g]);
+        else
+            for (int i = 0; i < nsteps[g]; ++i) sched[g][i] = one[i];
     }
     e = cudaMemcpyAsync(d_sched, sched, sizeof(sched[0]) * n_groups, cudaMemcpyHostToDevice, strm);
     if (e != cudaSuccess) return fail_cuda(e);
 
-    const bool split = precision == CWTH_PREC_BF16X2;
     for (int g = 0; g < n_groups; ++g) {
         const int first = g * kScalesPerGroup;
         const int n = std::min(S, first + kScalesPerGroup) - first;
@@ -258,8 +263,8 @@ cwth_status cwth_execute_direct_noalloc(const cwth_morlet* w, const double* scal
         __nv_bfloat16* blo = bhi + (size_t)ncols[g] * kpad[g];
         CUtensorMap maps[4];
         const int64_t aoff = front - hg;
-        if (!encode(&maps[0], d_xhi + aoff, kpad[g], total_rows, (uint64_t)hop * 2, 128) ||
-            !encode(&maps[1], d_xlo + aoff, kpad[g], total_rows, (uint64_t)hop * 2, 128) ||
+        if (!encode(&maps[0], d_xhi + aoff, kpad[g], total_rows, (uint64_t)hop * 2, 32) ||
+            !encode(&maps[1], d_xlo + aoff, kpad[g], total_rows, (uint64_t)hop * 2, 32) ||
             !encode(&maps[2], bhi, kpad[g], ncols[g], (uint64_t)kpad[g] * 2, 64) ||
             !encode(&maps[3], blo, kpad[g], ncols[g], (uint64_t)kpad[g] * 2, 64))
             return fail(CWTH_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled rejected a tensor map");
@@ -275,7 +280,7 @@ cwth_status cwth_execute_direct_noalloc(const cwth_morlet* w, const double* scal
             L.stages = cwth::direct_max_stages(ncols[g], split, 0);
         }
         L.a_shift = L.win_rows ? 64 / hop : 0;
-        L.sched = d_sched + (size_t)g * (kMaxTaps / 64);
+        L.sched = d_sched + (size_t)g * 2 * (kMaxTaps / 64);
         L.nsteps = nsteps[g];
         uint32_t tc = 32;
         while (tc < (uint32_t)ncols[g]) tc <<= 1;
