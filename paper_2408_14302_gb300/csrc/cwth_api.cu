@@ -20,10 +20,10 @@ namespace {
 constexpr double kEpsWrap = 1e-10;
 // Morlet band threshold: spectrum bins where Psi(a nu) < kEpsBand are skipped.
 constexpr double kEpsBand = 1e-9;
-// Shared memory a spectral CTA may use.
-constexpr size_t kSmemCap = 227 * 1024;
-// Preferred ceiling, so that two CTAs fit on one SM.
-constexpr size_t kSmemTwoPerSm = 112 * 1024;
+// Dynamic shared memory a spectral CTA may use: the 227 KB opt-in limit less
+// room for the kernel's static arrays.  One 1024-thread CTA fills an SM, so
+// the whole budget is available.
+constexpr size_t kSmemCap = 227 * 1024 - 1024;
 constexpr int kNumSms = 152;
 // Direct path: taps below this fraction of the wavelet peak are dropped.
 constexpr double kEpsDirect = 1e-9;
@@ -333,12 +333,17 @@ cwth_status build_spectral(cwth_plan_s* p) {
         s.q_lo = (int32_t)lo;
         s.q_hi = (int32_t)hi;
         s.row = rows[i];
+        const double kexp = -M_PI * M_PI * p->B / M_LN2;
+        const double dlt = sp[i] * (double)p->P / (double)p->M;
+        s.dlt = (float)dlt;
+        s.q2 = (float)exp2(2.0 * kexp * (double)s.dlt * (double)s.dlt);
     }
-    cudaError_t e = cudaMalloc(&p->d_tw, sizeof(float2) * (size_t)p->M);
+    const size_t ntw = (size_t)cwth::spectral_twiddle_entries(p->M);
+    cudaError_t e = cudaMalloc(&p->d_tw, sizeof(float2) * ntw);
     if (e != cudaSuccess) return cuda_status(e);
     e = cudaMalloc(&p->d_sp, sizeof(SpecScale) * host.size());
     if (e != cudaSuccess) return cuda_status(e);
-    p->table_bytes += (int64_t)(sizeof(float2) * (size_t)p->M + sizeof(SpecScale) * host.size());
+    p->table_bytes += (int64_t)(sizeof(float2) * ntw + sizeof(SpecScale) * host.size());
     e = cudaMemcpy(p->d_sp, host.data(), sizeof(SpecScale) * host.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_status(e);
     e = cwth::spectral_make_twiddles(p->d_tw, p->M, 0);
@@ -360,8 +365,7 @@ cwth_status launch_spectral(const cwth_plan_s* p, const float* d_x, int64_t ld_x
     const int gs = (p->n_sp + n_groups - 1) / n_groups;
     n_groups = (p->n_sp + gs - 1) / gs;
     int nconc = gs;
-    const size_t cap = std::max(kSmemTwoPerSm, cwth::spectral_smem_bytes(p->M, p->P, 1));
-    while (nconc > 1 && cwth::spectral_smem_bytes(p->M, p->P, nconc) > cap) --nconc;
+    while (nconc > 1 && cwth::spectral_smem_bytes(p->M, p->P, nconc) > kSmemCap) --nconc;
     while (nconc > 1 && (int64_t)nconc * p->P > cwth::kMaxFftPoints) --nconc;
     if (batch > 65535 || p->n_seg > 0x7fffffff) return CWTH_ERR_UNSUPPORTED;
 

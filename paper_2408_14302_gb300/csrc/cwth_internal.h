@@ -13,10 +13,10 @@
 namespace cwth {
 
 constexpr uint32_t kPlanMagic = 0xC0A7B17Eu;
-constexpr int kSpecThreads = 512;
+constexpr int kSpecThreads = 1024;
 // Largest batched shared-memory FFT (complex points) one CTA performs: at
-// most 16 points per thread per pass.
-constexpr int kMaxFftPoints = 16 * kSpecThreads;
+// most 8 points per thread per pass.
+constexpr int kMaxFftPoints = 8 * kSpecThreads;
 
 // Per-scale parameters of the spectral path (one entry per spectral scale).
 // The multiplier at unwrapped bin q_u is
@@ -31,7 +31,9 @@ struct SpecScale {
     int32_t q_lo;
     int32_t q_hi;
     int32_t row;     // output row (index into the caller's scale list)
-    int32_t pad_[3];
+    float dlt;       // a P / M: argument step between the bins a residue visits
+    float q2;        // 2^(2 kexp dlt^2): ratio of successive weight ratios
+    int32_t pad_;
 };
 
 struct SpecLaunch {
@@ -53,7 +55,7 @@ struct SpecLaunch {
     int32_t nconc;     // scales folded and inverted together
     float center;
     float kexp;        // -pi^2 B log2(e)
-    const float2* tw;  // exp(-2 pi i m / M), m < M
+    const float2* tw;  // two-level table: exp(-2 pi i 128 i / M), i < M/128, then exp(-2 pi i j / M), j < 128
     const SpecScale* sc;
 };
 
@@ -87,6 +89,7 @@ struct DirLaunch {
 void set_last_error(const char* msg);
 
 size_t spectral_smem_bytes(int M, int P, int nconc);
+int spectral_twiddle_entries(int M);
 cudaError_t spectral_prepare_device();
 cudaError_t spectral_make_twiddles(float2* d_tw, int M, cudaStream_t st);
 cudaError_t spectral_launch(const SpecLaunch& L, int n_seg, int batch, int n_groups,

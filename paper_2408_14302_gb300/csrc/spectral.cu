@@ -92,12 +92,24 @@ struct Dft<8, INV> {
     }
 };
 
-// Multiplies v[r] by w^r, w = exp(-+ 2 pi i k / (Ns R)) = tw[k * tstride]
+// Twiddle table in shared memory, two levels: exp(-2 pi i m / M) =
+// t1[m >> 7] * t2[m & 127], t1[i] = exp(-2 pi i 128 i / M), t2[j] =
+// exp(-2 pi i j / M), both generated in float64 (one extra rounding).
+struct TwTab {
+    const float2* t1;
+    const float2* t2;
+};
+
+__device__ __forceinline__ float2 tw_at(const TwTab& t, int m) {
+    return cmul(t.t1[m >> 7], t.t2[m & 127]);
+}
+
+// Multiplies v[r] by w^r, w = exp(-+ 2 pi i k / (Ns R)) = table[k * tstride]
 // (conjugated for the inverse).  The powers come from a product tree of
 // depth <= 3, a few roundings each (~3e-7 relative).
 template <int R, bool INV>
-__device__ __forceinline__ void twiddle(float2* v, const float2* __restrict__ tw, int idx) {
-    float2 w1 = __ldg(&tw[idx]);
+__device__ __forceinline__ void twiddle(float2* v, const TwTab& tw, int idx) {
+    float2 w1 = tw_at(tw, idx);
     if (INV) w1.y = -w1.y;
     v[1] = cmul(v[1], w1);
     if (R >= 4) {
@@ -124,8 +136,7 @@ __device__ __forceinline__ void twiddle(float2* v, const float2* __restrict__ tw
 // the twiddle-table step for one unit of r*k.
 template <int R, int MAXB, bool INV>
 __device__ __forceinline__ void fft_pass(float2* __restrict__ buf, int L, int nbatch, int Ns,
-                                         const float2* __restrict__ tw, int tstride, bool rs,
-                                         bool ws) {
+                                         const TwTab& tw, int tstride, bool rs, bool ws) {
     const int LR = L / R;
     const int lg_lr = __ffs(LR) - 1;
     const int nb = nbatch * LR;
@@ -137,8 +148,19 @@ __device__ __forceinline__ void fft_pass(float2* __restrict__ buf, int L, int nb
             const int b = j >> lg_lr;
             const int jj = j & (LR - 1);
             const int base = b * L + jj;
+            // The swizzle only mixes bits 4..7 into bits 0..3, so a stride
+            // that is a multiple of 256 moves a swizzled address linearly.
+            if (!rs) {
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[u][r] = buf[lay(base + r * LR, rs)];
+                for (int r = 0; r < R; ++r) v[u][r] = buf[base + r * LR];
+            } else if ((LR & 255) == 0) {
+                const int a0 = lay(base, true);
+#pragma unroll
+                for (int r = 0; r < R; ++r) v[u][r] = buf[a0 + r * LR];
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) v[u][r] = buf[lay(base + r * LR, true)];
+            }
             const int k = jj & (Ns - 1);
             if (Ns > 1) twiddle<R, INV>(v[u], tw, k * tstride);
             Dft<R, INV>::run(v[u]);
@@ -153,8 +175,17 @@ __device__ __forceinline__ void fft_pass(float2* __restrict__ buf, int L, int nb
             const int jj = j & (LR - 1);
             const int k = jj & (Ns - 1);
             const int d = b * L + (jj - k) * R + k;
+            if (!ws) {
 #pragma unroll
-            for (int r = 0; r < R; ++r) buf[lay(d + r * Ns, ws)] = v[u][r];
+                for (int r = 0; r < R; ++r) buf[d + r * Ns] = v[u][r];
+            } else if ((Ns & 255) == 0) {
+                const int a0 = lay(d, true);
+#pragma unroll
+                for (int r = 0; r < R; ++r) buf[a0 + r * Ns] = v[u][r];
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) buf[lay(d + r * Ns, true)] = v[u][r];
+            }
         }
     }
     __syncthreads();
@@ -162,15 +193,15 @@ __device__ __forceinline__ void fft_pass(float2* __restrict__ buf, int L, int nb
 
 template <int R, bool INV>
 __device__ __forceinline__ void fft_pass_dispatch(float2* buf, int L, int nbatch, int Ns,
-                                                  const float2* tw, int tstride, bool rs, bool ws) {
+                                                  const TwTab& tw, int tstride, bool rs, bool ws) {
     const int nb = nbatch * (L / R);
     const int per = (nb + blockDim.x - 1) / blockDim.x;
-    // Up to 16 complex values per thread: the caller keeps nbatch * L <=
-    // kMaxFftPoints = 16 * kSpecThreads.
-    constexpr int kMaxB = 16 / R;
-    if (per <= 1)
+    // Up to 8 complex values per thread: the caller keeps nbatch * L <=
+    // kMaxFftPoints = 8 * kSpecThreads.
+    constexpr int kMaxB = 8 / R;
+    if (per <= 1 || kMaxB <= 1)
         fft_pass<R, 1, INV>(buf, L, nbatch, Ns, tw, tstride, rs, ws);
-    else if (per <= 2)
+    else if (per <= 2 || kMaxB <= 2)
         fft_pass<R, 2, INV>(buf, L, nbatch, Ns, tw, tstride, rs, ws);
     else if (per <= 4 || kMaxB <= 4)
         fft_pass<R, (kMaxB < 4 ? kMaxB : 4), INV>(buf, L, nbatch, Ns, tw, tstride, rs, ws);
@@ -182,7 +213,7 @@ __device__ __forceinline__ void fft_pass_dispatch(float2* buf, int L, int nbatch
 // ts = M / L maps the transform's twiddles onto the table of exp(-2 pi i m/M).
 // Radices: 8 where possible, a leading 4 (or 4,4) for the remainder of log2 L.
 template <bool INV>
-__device__ __forceinline__ void fft_block(float2* buf, int L, int nbatch, const float2* tw, int ts) {
+__device__ __forceinline__ void fft_block(float2* buf, int L, int nbatch, const TwTab& tw, int ts) {
     const int e = __ffs(L) - 1;  // L >= 8: the plan keeps P = M/H >= 8 and M/2 >= 256
     const int n4 = (e % 3 == 1) ? 2 : (e % 3 == 2) ? 1 : 0;
     const int npass = n4 + (e - 2 * n4) / 3;
@@ -207,18 +238,41 @@ __device__ __forceinline__ float fast_exp2(float x) {
 
 // Sum of X[q] * exp2(kexp * (qf * a_over_m - C)^2) over n bins of one run:
 // indices q0, q0 + dq, ... (dq = +-P) and unwrapped bin positions qf,
-// qf + P, ... .  ex2.approx has ~2^-22 relative error; the argument is
-// formed from the exact bin position, so errors do not accumulate.
+// qf + P, ... .  The weight is a sampled Gaussian: with u_j the argument at
+// bin j and D = a P / M its step, g_{j+1} = g_j r_j, r_j = 2^{kexp (2 u_j D
+// + D^2)} and r_{j+1} = r_j Q, Q = 2^{2 kexp D^2}.  Runs of 8 or more bins
+// take g_j this way, re-anchored from the exact argument every 8 bins (at
+// most ~3.5e-6 relative drift at a chunk's end; D <= 0.35 there, so the
+// ratios stay in range); shorter runs and the remainder use one
+// ex2.approx (~2^-22 relative) per bin.
 __device__ __forceinline__ float2 fold_run(const float2* __restrict__ X, int q0, int dq, int n,
-                                           float qf, float pf, float a_over_m, float cneg,
+                                           float qf, float pf, const SpecScale& sc, float cneg,
                                            float kexp) {
     float2 acc = make_float2(0.f, 0.f);
     const float2* xp = X + q0;
-#pragma unroll 4
-    for (int j = 0; j < n; ++j) {
+    int j = 0;
+    if (n >= 8) {
+        const float dlt = sc.dlt, q2 = sc.q2;
+        for (; j + 8 <= n; j += 8) {
+            const float u = fmaf(qf, sc.a_over_m, cneg);
+            float g = fast_exp2(kexp * u * u);
+            float r = fast_exp2(kexp * fmaf(2.f * u, dlt, dlt * dlt));
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const float2 v = xp[t * dq];
+                acc.x = fmaf(v.x, g, acc.x);
+                acc.y = fmaf(v.y, g, acc.y);
+                g *= r;
+                r *= q2;
+            }
+            xp += 8 * dq;
+            qf += 8.f * pf;
+        }
+    }
+    for (; j < n; ++j) {
         const float2 v = *xp;
         xp += dq;
-        const float u = fmaf(qf, a_over_m, cneg);
+        const float u = fmaf(qf, sc.a_over_m, cneg);
         qf += pf;
         const float g = fast_exp2(kexp * u * u);
         acc.x = fmaf(v.x, g, acc.x);
@@ -243,12 +297,12 @@ __device__ __forceinline__ float2 fold_residue(const float2* __restrict__ X, con
         int n;
         if (q <= Mh) {
             n = min(left, ((Mh - q) >> lgP) + 1);
-            const float2 t = fold_run(X, q, P, n, (float)qu, pf, sc.a_over_m, cneg, kexp);
+            const float2 t = fold_run(X, q, P, n, (float)qu, pf, sc, cneg, kexp);
             ad.x += t.x;
             ad.y += t.y;
         } else {
             n = min(left, ((M - 1 - q) >> lgP) + 1);
-            const float2 t = fold_run(X, M - q, -P, n, (float)qu, pf, sc.a_over_m, cneg, kexp);
+            const float2 t = fold_run(X, M - q, -P, n, (float)qu, pf, sc, cneg, kexp);
             am.x += t.x;
             am.y += t.y;
         }
@@ -261,8 +315,11 @@ __device__ __forceinline__ float2 fold_residue(const float2* __restrict__ X, con
 __global__ void __launch_bounds__(kSpecThreads, 1) spectral_segment_kernel(const SpecLaunch p) {
     extern __shared__ float2 smem[];
     const int M = p.M, Mh = M >> 1, P = p.P;
-    float2* X = smem;            // Mh + 1 used
-    float2* Z = smem + Mh + 2;   // nconc * P used
+    const int ntw = (M >> 7) + 128;
+    float2* T = smem;                 // two-level twiddle table, ntw entries
+    float2* X = smem + ntw;           // Mh + 1 used
+    float2* Z = smem + ntw + Mh + 2;  // nconc * P used
+    const TwTab tab{T, T + (M >> 7)};
 
     const int seg = blockIdx.x, clip = blockIdx.y, grp = blockIdx.z;
     int64_t len = p.lengths ? p.lengths[clip] : p.max_len;
@@ -272,6 +329,8 @@ __global__ void __launch_bounds__(kSpecThreads, 1) spectral_segment_kernel(const
     const int sp_begin = grp * p.group_size;
     if (k0 >= F || sp_begin >= p.n_sp) return;
     const int sp_end = min(p.n_sp, sp_begin + p.group_size);
+
+    for (int i = threadIdx.x; i < ntw; i += blockDim.x) T[i] = __ldg(p.tw + i);
 
     // a1: stage the segment as M/2 complex points.
     const int64_t s0 = k0 * p.hop - p.halo;
@@ -285,7 +344,7 @@ __global__ void __launch_bounds__(kSpecThreads, 1) spectral_segment_kernel(const
     __syncthreads();
 
     // a2: forward FFT of the M/2 points, twiddles exp(-2 pi i m/(M/2)) = tw[2m].
-    fft_block<false>(X, Mh, 1, p.tw, 2);
+    fft_block<false>(X, Mh, 1, tab, 2);
 
     // Real-input split: with Z = FFT(z), E = (Z[q] + conj Z[Mh-q])/2 and
     // O = (Z[q] - conj Z[Mh-q])/(2i) are the spectra of the even and odd
@@ -297,7 +356,7 @@ __global__ void __launch_bounds__(kSpecThreads, 1) spectral_segment_kernel(const
         const float2 zm = X[qm];
         const float2 E = make_float2(0.5f * (zq.x + zm.x), 0.5f * (zq.y - zm.y));
         const float2 O = make_float2(0.5f * (zq.y + zm.y), 0.5f * (zm.x - zq.x));
-        const float2 t = cmul(__ldg(&p.tw[q]), O);
+        const float2 t = cmul(tw_at(tab, q), O);
         const float2 xq = cadd(E, t);
         const float2 xm = csub(E, t);
         X[q] = xq;
@@ -333,7 +392,7 @@ __global__ void __launch_bounds__(kSpecThreads, 1) spectral_segment_kernel(const
 
         // a4: inverse FFT of length P for every scale of the chunk; the 1/M
         // normalisation is already in gscale.  exp(+2 pi i m/P) = conj(tw[m H]).
-        fft_block<true>(Z, P, nc, p.tw, p.hop);
+        fft_block<true>(Z, P, nc, tab, p.hop);
 
         const int Fs = p.seg_frames;
         for (int i = threadIdx.x; i < nc * Fs; i += blockDim.x) {
@@ -351,29 +410,34 @@ __global__ void __launch_bounds__(kSpecThreads, 1) spectral_segment_kernel(const
     }
 }
 
-// exp(-2 pi i m / M) in float64, rounded once to float32.
+// Two-level table: entries i < M/128 hold exp(-2 pi i 128 i / M), the next
+// 128 hold exp(-2 pi i j / M); float64, rounded once to float32.
 __global__ void twiddle_kernel(float2* tw, int M) {
-    const int m = blockIdx.x * blockDim.x + threadIdx.x;
-    if (m < M) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n1 = M >> 7;
+    if (i < n1 + 128) {
+        const double m = i < n1 ? 128.0 * i : (double)(i - n1);
         double s, c;
-        sincospi(2.0 * (double)m / (double)M, &s, &c);
-        tw[m] = make_float2((float)c, (float)-s);
+        sincospi(2.0 * m / (double)M, &s, &c);
+        tw[i] = make_float2((float)c, (float)-s);
     }
 }
 
 }  // namespace
 
 size_t spectral_smem_bytes(int M, int P, int nconc) {
-    return (size_t)(M / 2 + 2 + (long)nconc * P) * sizeof(float2);
+    return (size_t)(spectral_twiddle_entries(M) + M / 2 + 2 + (long)nconc * P) * sizeof(float2);
 }
+
+int spectral_twiddle_entries(int M) { return (M >> 7) + 128; }
 
 cudaError_t spectral_prepare_device() {
     return cudaFuncSetAttribute(spectral_segment_kernel,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024 - 1024);
 }
 
 cudaError_t spectral_make_twiddles(float2* d_tw, int M, cudaStream_t st) {
-    twiddle_kernel<<<(M + 255) / 256, 256, 0, st>>>(d_tw, M);
+    twiddle_kernel<<<(spectral_twiddle_entries(M) + 255) / 256, 256, 0, st>>>(d_tw, M);
     return cudaGetLastError();
 }
 
