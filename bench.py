@@ -179,6 +179,24 @@ def algorithmic_flops_per_clip(scales, hop, n=N_SAMPLES):
             + 4.0 * len(scales) * F), M
 
 
+def kernel_traffic(kernel: str, source: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary
+    (profiles/ncu_traffic.json), or None when the kernel's source changed
+    since those counters were taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    src = os.path.join(ROOT, "paper_2408_14302_gb300", "csrc", source)
+    if not (os.path.exists(path) and os.path.exists(src)):
+        return None
+    with open(path) as f:
+        d = json.load(f).get(kernel)
+    if not d:
+        return None
+    with open(src, "rb") as f:
+        sha = hashlib.sha1(f.read()).hexdigest()
+    return d["dram_bytes_per_launch"] if d.get("source_sha1") == sha else None
+
+
 def fp32_peak_tflops(sm_mhz):
     # 152 SMs x 128 FP32 lanes x 2 flops (FMA) per clock
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
@@ -290,9 +308,17 @@ def run_direct_leg(torch, cwth, dev, flush, stream, steps, peak_bf16):
             }
             p.close()
             del o
+    r64 = res["hop64_bf16"]
+    roof = {"bound": "tensor", "kernel": "direct_mma_kernel (bf16, hop 64; time includes the "
+                                        "bf16 staging launch)",
+            "achieved": r64["useful_tflops"], "peak": peak_bf16, "unit": "TFLOP/s",
+            "frac": r64["useful_tflops"] / peak_bf16,
+            "traffic": kernel_traffic("direct_mma_kernel", "direct.cu"),
+            "algorithmic_flops_per_launch": direct_useful_flops_per_clip(scales, 64) * DIRECT_CLIPS,
+            "peak_source": "measured bf16 dense (burst)"}
     return {"workload": "tones_1s_512clips_128scales", "clips": DIRECT_CLIPS,
             "scales": DIRECT_S, "l2": "flushed: 256 MiB write before every timed step",
-            "peak_bf16_tflops": peak_bf16, "runs": res}
+            "peak_bf16_tflops": peak_bf16, "roofline": roof, "runs": res}
 
 
 # ------------------------------------------------------------------ our arm
@@ -376,6 +402,28 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_direct:
         direct = run_direct_leg(torch, cwth, dev, flush, stream, args.steps, pk["bf16_tflops"])
 
+    # The same batch through the automatic path at split-bf16 precision (the
+    # tensor-core direct path for every scale it can take; same 1e-5 tolerance).
+    auto = None
+    if not args.no_direct:
+        pa = cwth.Plan(scales, hop=HOP, max_len=N_SAMPLES, bandwidth=B_MORLET, center=C_MORLET,
+                       sample_rate=FS, precision="bf16x2", path="auto")
+        oa = torch.empty_like(out_d)
+        fa = lambda: pa.execute(x_d, out=oa, stream=stream)  # noqa: E731
+        for _ in range(3):
+            fa()
+        pa.sync(stream)
+        ea = time_steps(torch, fa, max(3, min(args.steps, 20)), flush, stream)
+        torch.cuda.synchronize()
+        pa.sync(stream)
+        msa = statistics.mean(a.elapsed_time(b) for a, b in ea)
+        ia = pa.info()
+        auto = {"precision": "bf16x2", "path": "auto", "ms_per_step": msa,
+                "audio_sec_per_s": world * audio_s / (msa * 1e-3),
+                "num_direct": ia["num_direct"], "num_spectral": ia["num_spectral"]}
+        pa.close()
+        del oa
+
     # End to end through the public host entry point (pinned host buffers).
     hx = torch.from_numpy(xs).pin_memory()
     hout = torch.empty((N_CLIPS, S, plan.frames_max), dtype=torch.float32).pin_memory()
@@ -409,7 +457,8 @@ def run_ours(args, rank, world, local_rank):
         "scalogram_gbs": world * out_bytes / (ms * 1e-3) / 1e9,
         "roofline": {"bound": "alu", "kernel": "spectral_segment_kernel",
                      "achieved": achieved, "peak": peak_alu, "unit": "TFLOP/s",
-                     "frac": achieved / peak_alu, "traffic": None,
+                     "frac": achieved / peak_alu,
+                     "traffic": kernel_traffic("spectral_segment_kernel", "spectral.cu"),
                      "algorithmic_flops_per_launch": flops_launch,
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
                      "hbm_view": {"algorithmic_bytes_per_launch": bytes_launch,
@@ -423,6 +472,7 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": args.steps * 1,
         "clocks": clocks,
         "hop1": hop1,
+        "auto_bf16x2": auto,
         "direct": direct,
     }
     plan.close()
