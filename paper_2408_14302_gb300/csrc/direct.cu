@@ -41,6 +41,7 @@ constexpr int kBM = 128;             // frames per tile
 constexpr int kBK = 64;              // taps per stage (128 bytes of bf16)
 constexpr int kDirThreads = 192;
 constexpr int kAPieceRows = 32;      // frame-map box height (rows per TMA copy)
+constexpr int kMaxGroupScales = 128; // scales per GEMM group (256 columns)
 constexpr long long kWaitBudget = 4000000000LL;  // ~2 s of SM clock
 
 // ------------------------------------------------------------ staging
@@ -146,9 +147,11 @@ __global__ void __launch_bounds__(kDirThreads, 1)
     __shared__ __align__(8) uint64_t win_bar;
     __shared__ uint32_t tmem_base_sh;
     __shared__ int abort_sh;
+    __shared__ int rows_sh[kMaxGroupScales];
 
     uint8_t* smem = (uint8_t*)(((uintptr_t)dsmem_raw + 1023) & ~(uintptr_t)1023);
     const int N = p.ncols;
+    for (int i = threadIdx.x; i < p.n_scales; i += blockDim.x) rows_sh[i] = __ldg(p.rows + i);
     const int stages = p.stages;
     const int shift = p.a_shift;
     constexpr uint32_t kPiece = kAPieceRows * kBK * 2;  // one frame-map box
@@ -307,7 +310,7 @@ __global__ void __launch_bounds__(kDirThreads, 1)
                         const int sl = (c0 >> 1) + j;
                         if (sl < p.n_scales) {
                             const float re = v[2 * j], im = v[2 * j + 1];
-                            const int orow = __ldg(p.rows + sl);
+                            const int orow = rows_sh[sl];
                             p.out[(b * p.S_total + orow) * p.frames_max + k] =
                                 sqrtf(fmaf(re, re, im * im));
                         }
