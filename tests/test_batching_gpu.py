@@ -1,0 +1,67 @@
+"""Uneven-length batches in one CUDA graph: every clip matches the float64
+oracle, and the same clip transformed alone gives the same result as in the
+mix (within the float32 tolerance)."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def batch(tmp_path_factory):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2408_14302_gb300 import batching
+    clips, fs, ns, hs = batching.uneven_workload(n_clips=18, seed=77, min_s=0.05, max_s=1.2,
+                                                 p48k=0.3, scale_counts=(6, 10),
+                                                 hops=(128, 256))
+    cache = batching.TuneCache(str(tmp_path_factory.mktemp("tune") / "cache.json"))
+    runner = batching.BatchRunner(clips, fs, ns, hs, cache=cache)
+    runner.capture()
+    runner.replay()
+    torch.cuda.synchronize()
+    yield runner, clips, fs, ns, hs, cache
+    runner.close()
+
+
+def test_every_clip_matches_the_oracle(batch):
+    import oracle
+    from paper_2408_14302_gb300 import signals
+    runner, clips, fs, ns, hs, _ = batch
+    assert len(runner.groups) >= 3
+    for i in range(len(clips)):
+        got = runner.result(i).astype(np.float64)
+        sc = signals.scales_for_band(50.0, 8000.0, ns[i], fs[i])
+        ref = oracle.cwth_magnitude(np.asarray(clips[i], np.float32).astype(np.float64), sc, hs[i])
+        assert got.shape == ref.shape
+        assert np.max(np.abs(got - ref)) <= TOL * np.max(ref), i
+
+
+def test_alone_equals_in_the_mix(batch):
+    from paper_2408_14302_gb300 import cwth, signals
+    runner, clips, fs, ns, hs, _ = batch
+    for i in (0, 5, 11):
+        gi, _ = runner.where[i]
+        path, prec = runner.groups[gi]["choice"]
+        sc = signals.scales_for_band(50.0, 8000.0, ns[i], fs[i])
+        with cwth.Plan(sc, hop=hs[i], max_len=len(clips[i]), sample_rate=fs[i], path=path,
+                       precision=prec) as p:
+            alone = p.execute(torch.from_numpy(np.asarray(clips[i], np.float32)).cuda())[0]
+            alone = alone.cpu().numpy()
+        mixed = runner.result(i)
+        assert np.max(np.abs(alone - mixed)) <= TOL * np.max(np.abs(alone))
+
+
+def test_replay_is_repeatable_and_cache_is_written(batch):
+    runner, _, _, _, _, cache = batch
+    before = [runner.result(i).copy() for i in range(3)]
+    runner.replay()
+    torch.cuda.synchronize()
+    for i in range(3):
+        assert np.array_equal(before[i], runner.result(i))
+    assert len(cache.data) == len(runner.groups)
