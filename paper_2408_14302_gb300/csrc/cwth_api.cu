@@ -240,7 +240,7 @@ cwth_status build_direct(cwth_plan_s* p) {
     if (e == cudaSuccess) e = cudaMalloc(&p->d_bank_lo, sizeof(__nv_bfloat16) * bank_elems);
     if (e == cudaSuccess) e = cudaMalloc(&p->d_bank_f32, sizeof(float2) * f32_elems);
     if (e == cudaSuccess) e = cudaMalloc(&p->d_status, sizeof(int));
-    if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_status, 0, sizeof(int), p->setup);
     if (e != cudaSuccess) return cuda_status(e);
     p->table_bytes += (int64_t)(bank_elems * 4 + f32_elems * 8);
     for (size_t gi = 0; gi < ranges.size(); ++gi) {
@@ -256,11 +256,11 @@ cwth_status build_direct(cwth_plan_s* p) {
         if (e == cudaSuccess) e = cudaMalloc(&g.d_h, sizeof(int32_t) * hh.size());
         if (e == cudaSuccess) e = cudaMalloc(&g.d_scales, sizeof(double) * sc.size());
         if (e == cudaSuccess)
-            e = cudaMemcpy(g.d_rows, rows.data(), sizeof(int32_t) * rows.size(), cudaMemcpyHostToDevice);
+            e = cudaMemcpyAsync(g.d_rows, rows.data(), sizeof(int32_t) * rows.size(), cudaMemcpyHostToDevice, p->setup);
         if (e == cudaSuccess)
-            e = cudaMemcpy(g.d_h, hh.data(), sizeof(int32_t) * hh.size(), cudaMemcpyHostToDevice);
+            e = cudaMemcpyAsync(g.d_h, hh.data(), sizeof(int32_t) * hh.size(), cudaMemcpyHostToDevice, p->setup);
         if (e == cudaSuccess)
-            e = cudaMemcpy(g.d_scales, sc.data(), sizeof(double) * sc.size(), cudaMemcpyHostToDevice);
+            e = cudaMemcpyAsync(g.d_scales, sc.data(), sizeof(double) * sc.size(), cudaMemcpyHostToDevice, p->setup);
         std::vector<int2> sched(g.k_pad / 64), sched2(2 * (g.k_pad / 64));
         g.nsteps = cwth::direct_schedule(hh.data(), g.n_scales, g.h, g.k_pad, sched.data());
         if (split) {
@@ -269,11 +269,11 @@ cwth_status build_direct(cwth_plan_s* p) {
         }
         if (e == cudaSuccess) e = cudaMalloc(&g.d_sched, sizeof(int2) * sched.size());
         if (e == cudaSuccess)
-            e = cudaMemcpy(g.d_sched, sched.data(), sizeof(int2) * g.nsteps, cudaMemcpyHostToDevice);
+            e = cudaMemcpyAsync(g.d_sched, sched.data(), sizeof(int2) * g.nsteps, cudaMemcpyHostToDevice, p->setup);
         if (e == cudaSuccess)
             e = cwth::direct_make_bank(g.d_scales, g.d_h, g.n_scales, g.ncols, g.k_pad, g.h, p->B,
                                        p->C, p->d_bank_hi + g.bank_off, p->d_bank_lo + g.bank_off,
-                                       p->d_bank_f32 + g.f32_off, 0);
+                                       p->d_bank_f32 + g.f32_off, p->setup);
         if (e != cudaSuccess) return cuda_status(e);
         if (p->precision != CWTH_PREC_FP32) {
             if (!encode_bf16_2d(&g.map_b_hi, p->d_bank_hi + g.bank_off, g.k_pad, g.ncols,
@@ -299,7 +299,7 @@ cwth_status build_direct(cwth_plan_s* p) {
         e = cwth::direct_prepare_f32((size_t)(2 * p->dir_front + 1) * sizeof(float2));
     }
     if (e != cudaSuccess) return cuda_status(e);
-    return cuda_status(cudaDeviceSynchronize());
+    return cuda_status(cudaStreamSynchronize(p->setup));
 }
 
 cwth_status build_spectral(cwth_plan_s* p) {
@@ -344,13 +344,14 @@ cwth_status build_spectral(cwth_plan_s* p) {
     e = cudaMalloc(&p->d_sp, sizeof(SpecScale) * host.size());
     if (e != cudaSuccess) return cuda_status(e);
     p->table_bytes += (int64_t)(sizeof(float2) * ntw + sizeof(SpecScale) * host.size());
-    e = cudaMemcpy(p->d_sp, host.data(), sizeof(SpecScale) * host.size(), cudaMemcpyHostToDevice);
+    e = cudaMemcpyAsync(p->d_sp, host.data(), sizeof(SpecScale) * host.size(), cudaMemcpyHostToDevice,
+                        p->setup);
     if (e != cudaSuccess) return cuda_status(e);
-    e = cwth::spectral_make_twiddles(p->d_tw, p->M, 0);
+    e = cwth::spectral_make_twiddles(p->d_tw, p->M, p->setup);
     if (e != cudaSuccess) return cuda_status(e);
     e = cwth::spectral_prepare_device();
     if (e != cudaSuccess) return cuda_status(e);
-    e = cudaDeviceSynchronize();
+    e = cudaStreamSynchronize(p->setup);
     return cuda_status(e);
 }
 
@@ -598,8 +599,17 @@ cwth_status cwth_plan(const cwth_morlet* w, const double* scales, int32_t S, int
             else
                 p->scale_path[s] = choice;
         }
+        // Tables are made on a private non-blocking stream and only that
+        // stream is waited for, so planning never stalls other work.
+        if (st == CWTH_OK && cudaStreamCreateWithFlags(&p->setup, cudaStreamNonBlocking) != cudaSuccess)
+            st = CWTH_ERR_CUDA;
         if (st == CWTH_OK) st = build_direct(p);
         if (st == CWTH_OK) st = build_spectral(p);
+        if (p->setup) {
+            cudaStreamSynchronize(p->setup);
+            cudaStreamDestroy(p->setup);
+            p->setup = nullptr;
+        }
     } catch (...) {
         st = CWTH_ERR_OOM;
     }

@@ -141,6 +141,7 @@ struct DirGroup {
 struct cwth_plan_s {
     uint32_t magic = 0;
     int device = 0;
+    cudaStream_t setup = nullptr;   // private stream used while the plan is built
     double B = 0, C = 0, fs = 0;
     int32_t S = 0, hop = 0, precision = 0, path = 0;
     int64_t max_len = 0, frames_max = 0;
