@@ -1,4 +1,5 @@
 // C ABI of libcwth.so: argument checking, planning, launches (include/cwth.h).
+#include <limits.h>
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -159,6 +160,8 @@ bool direct_eligible(const cwth_plan_s& p, double a) {
     const int64_t k = round_up(2 * (int64_t)direct_half_support(a, p.B) + 1, 64);
     if (k > kMaxDirectTaps) return false;
     if (p.precision != CWTH_PREC_FP32 && p.hop % 8 != 0) return false;
+    // The tensor-core epilogue addresses a clip's output with 32-bit offsets.
+    if (p.precision != CWTH_PREC_FP32 && (int64_t)p.S * p.frames_max > INT32_MAX) return false;
     return true;
 }
 
@@ -223,13 +226,8 @@ cwth_status build_direct(cwth_plan_s* p) {
         g.k_pad = (int32_t)round_up(2 * (int64_t)g.h + 1, 64);
         g.bank_off = bank_elems;
         g.f32_off = f32_elems;
-        g.win_rows = cwth::direct_window_rows(p->hop, g.k_pad);
-        g.stages = g.win_rows ? cwth::direct_max_stages(g.ncols, split, g.win_rows) : 0;
-        if (g.stages == 0) {  // window does not fit: per-step frame tiles
-            g.win_rows = 0;
-            g.stages = cwth::direct_max_stages(g.ncols, split, 0);
-        }
-        if (g.stages == 0) return CWTH_ERR_UNSUPPORTED;
+        g.shape = cwth::direct_shape(g.ncols, split, p->hop, g.k_pad);
+        if (g.shape.stages == 0) return CWTH_ERR_UNSUPPORTED;
         bank_elems += (int64_t)g.ncols * g.k_pad;
         f32_elems += (int64_t)g.n_scales * g.k_pad;
         p->groups.push_back(g);
@@ -468,14 +466,15 @@ cwth_status launch_direct(cwth_plan_s* p, const float* d_x, int64_t ld_x, const 
         L.h_group = g.h;
         L.n_scales = g.n_scales;
         L.rows = g.d_rows;
-        L.stages = g.stages;
+        L.stages = g.shape.stages;
         L.sched = g.d_sched;
         L.nsteps = g.nsteps;
-        L.win_rows = g.win_rows;
-        L.a_shift = g.win_rows ? 64 / (int)hop : 0;
-        uint32_t tc = 32;
-        while (tc < (uint32_t)g.ncols) tc <<= 1;
-        L.tmem_cols = tc;
+        L.win_rows = g.shape.win_rows;
+        L.a_shift = g.shape.win_rows ? 64 / (int)hop : 0;
+        L.unit = g.shape.unit;
+        L.win_sets = g.shape.win_sets;
+        L.acc_sets = g.shape.acc_sets;
+        L.tmem_cols = g.shape.tmem_cols;
         e = cwth::direct_launch_mma(maps, L, split, st);
         if (e != cudaSuccess) return cuda_status(e);
     }

@@ -61,6 +61,9 @@ struct SpecLaunch {
 
 // Direct (GEMM) path launch parameters; one launch per scale group.
 constexpr int kMaxDirStages = 6;
+// Schedule steps of one group: at most 4096 taps = 64 tap blocks, each
+// visited once per bank part (two parts in the split variant).
+constexpr int kMaxDirSteps = 128;
 struct DirLaunch {
     float* out;
     int64_t frames_max;
@@ -82,7 +85,16 @@ struct DirLaunch {
     const int2* sched;      // per K step: {tap block, columns used | bank part << 16}
     int32_t nsteps;
     int32_t a_shift;        // frame-view rows per tap block (64 / hop) when one window serves all blocks, else 0
-    int32_t win_rows;       // rows of that window (a multiple of 128)
+    int32_t win_rows;       // rows of that window (a multiple of 32)
+    int32_t unit;           // 128-frame tiles sharing each bank tile (1 or 2)
+    int32_t win_sets;       // frame-window sets (2: the next unit's windows load early)
+    int32_t acc_sets;       // tensor-memory accumulator sets (2: epilogue overlaps MMAs)
+};
+
+// Launch shape of one direct-path group.
+struct DirShape {
+    int32_t unit = 0, acc_sets = 0, win_sets = 0, win_rows = 0, stages = 0;
+    uint32_t tmem_cols = 0;
 };
 
 // Records the detail string cwth_last_error() returns in the calling thread.
@@ -95,8 +107,10 @@ cudaError_t spectral_make_twiddles(float2* d_tw, int M, cudaStream_t st);
 cudaError_t spectral_launch(const SpecLaunch& L, int n_seg, int batch, int n_groups,
                             size_t smem, cudaStream_t st);
 
-size_t direct_smem_bytes(int ncols, int stages, bool split, int win_rows);
-int direct_max_stages(int ncols, bool split, int win_rows);
+size_t direct_smem_bytes(int ncols, int stages, bool split, int win_rows, int unit,
+                         int win_sets);
+int direct_max_stages(int ncols, bool split, int win_rows, int unit, int win_sets);
+DirShape direct_shape(int ncols, bool split, int hop, int k_pad);
 // Rows of the frame window for hops dividing 64 (0: per-step frame tiles).
 int direct_window_rows(int hop, int k_pad);
 // The split variant's schedule: every step of `in` twice, hi part then lo
@@ -124,8 +138,7 @@ struct DirGroup {
     int32_t ncols = 0;
     int32_t h = 0;       // group half support, a multiple of 8
     int32_t k_pad = 0;   // multiple of 64, >= 2h + 1
-    int32_t stages = 0;
-    int32_t win_rows = 0;
+    DirShape shape;
     int64_t bank_off = 0;   // element offset into the bf16 banks ([ncols][k_pad])
     int64_t f32_off = 0;    // element offset into the float32 bank ([n_scales][k_pad])
     int32_t* d_rows = nullptr;

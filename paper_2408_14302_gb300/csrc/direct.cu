@@ -44,6 +44,14 @@ constexpr int kAPieceRows = 32;      // frame-map box height (rows per TMA copy)
 constexpr int kMaxGroupScales = 128; // scales per GEMM group (256 columns)
 constexpr long long kWaitBudget = 4000000000LL;  // ~2 s of SM clock
 
+// Square root by the hardware approximation (relative error about 2^-22),
+// well inside every accuracy class of the direct path.
+__device__ __forceinline__ float sqrt_approx(float v) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+
 // ------------------------------------------------------------ staging
 // x_pad[b][j] = x[b][j - h_front] for j - h_front in [0, len_b), else 0;
 // hi = bf16(x), lo = bf16(x - hi).  Row b = batch is the zero tail after the
@@ -122,18 +130,27 @@ __global__ void bank_kernel(const double* __restrict__ scales, const int32_t* __
 }
 
 // ------------------------------------------------------------ tcgen05 GEMM
+// Persistent kernel: one CTA per SM walks units of p.unit (1 or 2) 128-frame
+// tiles, unit u covering tiles u * unit .. u * unit + unit - 1, units
+// blockIdx.x, blockIdx.x + gridDim.x, ...  Every bank tile a stage brings in
+// feeds the MMAs of all tiles of the unit, so the bank is read once per unit
+// rather than once per tile.  TMA stages stream without a break between
+// units; frame windows come in p.win_sets sets and tensor-memory
+// accumulators in p.acc_sets sets (two sets: the next unit's loads / MMAs
+// overlap this unit's MMAs / epilogue).
+//
 // Shared-memory layout (1024-byte aligned pieces):
-//   [window hi][window lo]          only when p.a_shift > 0 (see below)
-//   stage s: [A hi][A lo][B]        A parts only without a window; A lo only
-//                                   for the split variant
-// Schedule step i: tap block sched[i].x; sched[i].y = columns used (low 16
+//   windows: [set][tile][part]     only when p.a_shift > 0 (see below)
+//   stage s: [A tile 0 hi][A tile 0 lo][A tile 1 hi][A tile 1 lo] ... [B]
+//            (A parts only without a window; lo parts only when split)
+// Schedule step j: tap block sched[j].x; sched[j].y = columns used (low 16
 // bits, a multiple of 16) | bank part (bit 16: 0 = hi, 1 = lo).  The split
 // variant visits every block twice, once per bank part, so a stage holds one
 // bank tile; the plain variant uses the hi part only.
 // When 64 is a multiple of the hop, the frame tile of tap block kb is the
 // tile of block 0 moved down by kb * 64 / H rows of the frame view, so one
-// window of 128 + (blocks - 1) * 64/H rows, loaded once, serves every K step
-// through descriptors that start kb * 64/H rows into it.
+// window of 128 + (blocks - 1) * 64/H rows per tile, loaded once, serves
+// every K step through descriptors that start kb * 64/H rows into it.
 template <bool SPLIT>
 __global__ void __launch_bounds__(kDirThreads, 1)
     direct_mma_kernel(const __grid_constant__ CUtensorMap mA_hi,
@@ -143,41 +160,54 @@ __global__ void __launch_bounds__(kDirThreads, 1)
     extern __shared__ uint8_t dsmem_raw[];
     __shared__ __align__(8) uint64_t full_bar[kMaxDirStages];
     __shared__ __align__(8) uint64_t empty_bar[kMaxDirStages];
-    __shared__ __align__(8) uint64_t accum_bar;
-    __shared__ __align__(8) uint64_t win_bar;
+    __shared__ __align__(8) uint64_t win_full[2], win_empty[2];
+    __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2];
     __shared__ uint32_t tmem_base_sh;
     __shared__ int abort_sh;
-    __shared__ int rows_sh[kMaxGroupScales];
+    __shared__ int32_t rowoff_sh[kMaxGroupScales];
+    __shared__ int2 sched_sh[kMaxDirSteps];
 
     uint8_t* smem = (uint8_t*)(((uintptr_t)dsmem_raw + 1023) & ~(uintptr_t)1023);
+    constexpr int kParts = SPLIT ? 2 : 1;
     const int N = p.ncols;
-    for (int i = threadIdx.x; i < p.n_scales; i += blockDim.x) rows_sh[i] = __ldg(p.rows + i);
+    const int T = p.unit;
     const int stages = p.stages;
     const int shift = p.a_shift;
+    const int wsets = p.win_sets, asets = p.acc_sets;
     constexpr uint32_t kPiece = kAPieceRows * kBK * 2;  // one frame-map box
     const uint32_t win_bytes = (uint32_t)p.win_rows * kBK * 2;
     const uint32_t win_span = (win_bytes + 1023) & ~1023u;
+    const uint32_t win_region = shift ? win_span * kParts * T * wsets : 0u;
     const uint32_t a_tile = kBM * kBK * 2;
-    const uint32_t a_step = shift ? 0u : a_tile * (SPLIT ? 2 : 1);
+    const uint32_t a_step = shift ? 0u : a_tile * kParts * T;
     const uint32_t b_bytes = (uint32_t)((N + 63) / 64 * 64) * kBK * 2;
     const uint32_t stage_bytes = a_step + b_bytes;
-    uint8_t* win_hi = smem;
-    uint8_t* win_lo = smem + win_span;
-    uint8_t* stage0 = smem + (shift ? win_span * (SPLIT ? 2 : 1) : 0);
+    uint8_t* stage0 = smem + win_region;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.x * kBM;
     const int nsteps = p.nsteps;
-    const uint32_t tcols = p.tmem_cols;
+    const int ntiles = (int)((p.total_rows + kBM - 1) / kBM);
+    const int nunits = (ntiles + T - 1) / T;
+    const uint32_t acc_cols = p.tmem_cols / (uint32_t)(asets * T);  // columns per tile accumulator
 
+    // Per-scale output offsets (elements from the clip's first row) and the
+    // schedule, both read at every step or store, live in shared memory.
+    for (int i = threadIdx.x; i < p.n_scales; i += blockDim.x)
+        rowoff_sh[i] = (int32_t)(__ldg(p.rows + i) * p.frames_max);
+    for (int i = threadIdx.x; i < nsteps; i += blockDim.x) sched_sh[i] = __ldg(p.sched + i);
     if (threadIdx.x == 0) {
         for (int s = 0; s < stages; ++s) {
             mbar_init(&full_bar[s], 1);
             mbar_init(&empty_bar[s], 1);
         }
-        mbar_init(&accum_bar, 1);
-        mbar_init(&win_bar, 1);
-        // A CTA of a launch that already timed out does no work.
-        abort_sh = *(volatile int*)p.status != 0 ? 1 : 0;
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&win_full[b], 1);
+            mbar_init(&win_empty[b], 1);
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], 4);  // one arrival per epilogue warp
+        }
+        // A CTA of a launch that already timed out, or handed a schedule
+        // longer than its table, does no work.
+        abort_sh = (*(volatile int*)p.status != 0 || nsteps > kMaxDirSteps) ? 1 : 0;
         fence_mbar_init();
         prefetch_tensormap(&mA_hi);
         prefetch_tensormap(&mB_hi);
@@ -187,7 +217,7 @@ __global__ void __launch_bounds__(kDirThreads, 1)
         }
     }
     if (warp == 1) {
-        tmem_alloc(&tmem_base_sh, tcols);
+        tmem_alloc(&tmem_base_sh, p.tmem_cols);
         tmem_relinquish();
     }
     tc_fence_before();
@@ -195,127 +225,233 @@ __global__ void __launch_bounds__(kDirThreads, 1)
     tc_fence_after();
     const uint32_t tmem = tmem_base_sh;
 
-    auto stage_ptr = [&](int s) { return stage0 + (size_t)s * stage_bytes; };
+    auto win_ptr = [&](int set, int tile, int part) {
+        return smem + ((size_t)(set * T + tile) * kParts + part) * win_span;
+    };
+    auto aborted = [&]() { return *(volatile int*)&abort_sh != 0; };
+    auto fail = [&]() { atomicExch(&abort_sh, 1); };
 
+    // The producer and the MMA issuer run as whole warps (control flow stays
+    // warp-uniform) and one elected lane issues the copies, MMAs and commits.
+    // Ring positions advance by counters, never by division: MMA issue is
+    // serial (each tcgen05.mma waits for the one before it to be accepted),
+    // so any latency between two issues adds to the tensor-core time.
     if (warp == 0) {
-        if (lane == 0) {
-            // Producer.
-            bool win_issued = false;
-            if (shift && !*(volatile int*)&abort_sh) {
-                mbar_arrive_expect_tx(&win_bar, win_bytes * (SPLIT ? 2 : 1));
-                for (int j = 0; j < p.win_rows / kAPieceRows; ++j) {
-                    tma_load_2d(win_hi + j * kPiece, &mA_hi, &win_bar, 0, m0 + j * kAPieceRows);
-                    if (SPLIT)
-                        tma_load_2d(win_lo + j * kPiece, &mA_lo, &win_bar, 0, m0 + j * kAPieceRows);
-                }
-                win_issued = true;
-            }
-            int issued = 0;
-            for (int i = 0; i < nsteps; ++i) {
-                const int s = i % stages;
-                const uint32_t use = (uint32_t)(i / stages);
-                if (*(volatile int*)&abort_sh) break;
-                if (i >= stages && !mbar_wait(&empty_bar[s], (use & 1) ^ 1, kWaitBudget)) {
-                    atomicExch(&abort_sh, 1);
+        // Producer.
+        uint32_t g = 0;            // steps issued over all units
+        int s = 0;                 // stage of step g
+        uint32_t sph = 0;          // parity of stage s's current fill
+        int ws = 0, wins = 0;      // window set of the next unit, window sets issued
+        uint32_t wph = 0;
+        for (int u = blockIdx.x; u < nunits && !aborted(); u += gridDim.x) {
+            if (shift) {
+                if (wins >= wsets && !mbar_wait_warp(&win_empty[ws], wph ^ 1, kWaitBudget)) {
+                    if (lane == 0) fail();
                     break;
                 }
-                const int2 step = __ldg(p.sched + i);
-                const int kx = step.x * kBK;
-                const int pieces = ((step.y & 0xFFFF) + 63) >> 6;
-                const CUtensorMap* mb = (SPLIT && (step.y >> 16)) ? &mB_lo : &mB_hi;
-                uint8_t* st = stage_ptr(s);
-                mbar_arrive_expect_tx(&full_bar[s], a_step + (uint32_t)pieces * 64 * kBK * 2);
-                if (!shift) {
-                    for (int j = 0; j < kBM / kAPieceRows; ++j) {
-                        tma_load_2d(st + j * kPiece, &mA_hi, &full_bar[s], kx, m0 + j * kAPieceRows);
-                        if (SPLIT)
-                            tma_load_2d(st + a_tile + j * kPiece, &mA_lo, &full_bar[s], kx,
+                if (elect_one()) {
+                    mbar_arrive_expect_tx(&win_full[ws], win_bytes * kParts * T);
+                    for (int tt = 0; tt < T; ++tt) {
+                        const int m0 = (u * T + tt) * kBM;
+                        for (int j = 0; j < p.win_rows / kAPieceRows; ++j) {
+                            tma_load_2d(win_ptr(ws, tt, 0) + j * kPiece, &mA_hi, &win_full[ws], 0,
                                         m0 + j * kAPieceRows);
+                            if (SPLIT)
+                                tma_load_2d(win_ptr(ws, tt, 1) + j * kPiece, &mA_lo, &win_full[ws],
+                                            0, m0 + j * kAPieceRows);
+                        }
                     }
                 }
-                for (int j = 0; j < pieces; ++j)
-                    tma_load_2d(st + a_step + j * 64 * kBK * 2, mb, &full_bar[s], kx, j * 64);
-                ++issued;
-            }
-            // Drain: every copy issued must have landed before the CTA exits.
-            for (int i = (issued > stages ? issued - stages : 0); i < issued; ++i) {
-                const int s = i % stages;
-                if (!mbar_wait(&full_bar[s], (uint32_t)(i / stages) & 1, kWaitBudget)) {
-                    atomicExch(&abort_sh, 1);
-                    break;
+                __syncwarp();
+                ++wins;
+                if (++ws == wsets) {
+                    ws = 0;
+                    wph ^= 1;
                 }
             }
-            if (win_issued && !mbar_wait(&win_bar, 0, kWaitBudget)) atomicExch(&abort_sh, 1);
+            bool ok = true;
+            for (int j = 0; j < nsteps; ++j) {
+                if (aborted()) {
+                    ok = false;
+                    break;
+                }
+                if (g >= (uint32_t)stages && !mbar_wait_warp(&empty_bar[s], sph ^ 1, kWaitBudget)) {
+                    if (lane == 0) fail();
+                    ok = false;
+                    break;
+                }
+                const int2 step = sched_sh[j];
+                if (elect_one()) {
+                    const int kx = step.x * kBK;
+                    const int pieces = ((step.y & 0xFFFF) + 63) >> 6;
+                    const CUtensorMap* mb = (SPLIT && (step.y >> 16)) ? &mB_lo : &mB_hi;
+                    uint8_t* st = stage0 + (size_t)s * stage_bytes;
+                    mbar_arrive_expect_tx(&full_bar[s], a_step + (uint32_t)pieces * 64 * kBK * 2);
+                    if (!shift) {
+                        for (int tt = 0; tt < T; ++tt) {
+                            const int m0 = (u * T + tt) * kBM;
+                            for (int q = 0; q < kBM / kAPieceRows; ++q) {
+                                tma_load_2d(st + (tt * kParts) * a_tile + q * kPiece, &mA_hi,
+                                            &full_bar[s], kx, m0 + q * kAPieceRows);
+                                if (SPLIT)
+                                    tma_load_2d(st + (tt * kParts + 1) * a_tile + q * kPiece,
+                                                &mA_lo, &full_bar[s], kx, m0 + q * kAPieceRows);
+                            }
+                        }
+                    }
+                    for (int q = 0; q < pieces; ++q)
+                        tma_load_2d(st + a_step + q * 64 * kBK * 2, mb, &full_bar[s], kx, q * 64);
+                }
+                __syncwarp();
+                ++g;
+                if (++s == stages) {
+                    s = 0;
+                    sph ^= 1;
+                }
+            }
+            if (!ok) break;
+        }
+        // Drain: every copy issued must have landed before the CTA exits.
+        if (lane == 0) {
+            for (uint32_t gg = g > (uint32_t)stages ? g - stages : 0; gg < g; ++gg)
+                if (!mbar_wait(&full_bar[gg % stages], (gg / stages) & 1, kWaitBudget)) {
+                    fail();
+                    break;
+                }
+            for (int w = wins > wsets ? wins - wsets : 0; w < wins; ++w)
+                if (!mbar_wait(&win_full[w % wsets], (w / wsets) & 1, kWaitBudget)) {
+                    fail();
+                    break;
+                }
         }
     } else if (warp == 1) {
-        if (lane == 0) {
-            // MMA issuer.  The first step is the centre tap block (hi part),
-            // which every scale reaches: its N covers all columns and its first
-            // MMA initialises them.
-            bool ok = true;
-            if (shift && !*(volatile int*)&abort_sh && !mbar_wait(&win_bar, 0, kWaitBudget)) {
-                atomicExch(&abort_sh, 1);
-                ok = false;
+        // MMA issuer.  Each unit's first step is the centre tap block (hi
+        // part), which every scale reaches: its N covers all columns and its
+        // first MMA per tile initialises that tile's accumulator.
+        int s = 0;
+        uint32_t sph = 0;
+        int as = 0, ws = 0, i = 0;
+        uint32_t aph = 0, wph = 0;
+        const uint32_t stage_base = smem_u32(stage0);
+        for (int u = blockIdx.x; u < nunits && !aborted(); u += gridDim.x, ++i) {
+            if (i >= asets && !mbar_wait_warp(&acc_empty[as], aph ^ 1, kWaitBudget)) {
+                if (lane == 0) fail();
+                break;
             }
-            for (int i = 0; i < nsteps && ok; ++i) {
-                const int s = i % stages;
-                if (*(volatile int*)&abort_sh) break;
-                if (!mbar_wait(&full_bar[s], (uint32_t)(i / stages) & 1, kWaitBudget)) {
-                    atomicExch(&abort_sh, 1);
+            if (shift && !mbar_wait_warp(&win_full[ws], wph, kWaitBudget)) {
+                if (lane == 0) fail();
+                break;
+            }
+            tc_fence_after();
+            const uint32_t dacc0 = tmem + (uint32_t)(as * T) * acc_cols;
+            const uint32_t win0 = smem_u32(win_ptr(ws, 0, 0));
+            bool ok = true;
+            int2 step = sched_sh[0];
+            for (int j = 0; j < nsteps; ++j) {
+                // Everything but the MMAs is computed before the wait.
+                const int2 next = sched_sh[j + 1 < nsteps ? j + 1 : j];
+                const uint32_t st = stage_base + (uint32_t)s * stage_bytes;
+                const uint32_t idesc = idesc_bf16_f32(kBM, step.y & 0xFFFF);
+                const uint64_t bd = desc_kmajor_sw128(st + a_step);
+                const uint32_t a0 = shift ? win0 + (uint32_t)(step.x * shift) * 128u : st;
+                const uint32_t first = j > 0 ? 1u : 0u;
+                if (!mbar_wait_warp(&full_bar[s], sph, kWaitBudget)) {
+                    if (lane == 0) fail();
+                    ok = false;
                     break;
                 }
                 tc_fence_after();
-                const int2 step = __ldg(p.sched + i);
-                const uint32_t idesc = idesc_bf16_f32(kBM, step.y & 0xFFFF);
-                const uint32_t st = smem_u32(stage_ptr(s));
-                const uint32_t rows = (uint32_t)(step.x * shift) * 128u;
-                const uint64_t a_hi = desc_kmajor_sw128(shift ? smem_u32(win_hi) + rows : st);
-                const uint64_t a_lo =
-                    desc_kmajor_sw128(shift ? smem_u32(win_lo) + rows : st + a_tile);
-                const uint64_t bd = desc_kmajor_sw128(st + a_step);
+                if (elect_one()) {
+                    for (int tt = 0; tt < T; ++tt) {
+                        const uint32_t dacc = dacc0 + (uint32_t)tt * acc_cols;
+                        // tile tt, part q: windows are [tile][part] win_span apart,
+                        // stage A tiles [tile][part] a_tile apart
+                        const uint32_t pitch = shift ? win_span : a_tile;
+                        const uint64_t a_hi = desc_kmajor_sw128(a0 + (uint32_t)(tt * kParts) * pitch);
+                        const uint64_t a_lo =
+                            desc_kmajor_sw128(a0 + (uint32_t)(tt * kParts + kParts - 1) * pitch);
 #pragma unroll
-                for (int k = 0; k < kBK / 16; ++k) {
-                    // 16 bf16 = 32 bytes along K -> +2 in the >>4 address field
-                    const uint32_t acc = (i > 0 || k > 0) ? 1u : 0u;
-                    mma_f16(tmem, a_hi + 2 * k, bd + 2 * k, idesc, acc);
-                    if (SPLIT) mma_f16(tmem, a_lo + 2 * k, bd + 2 * k, idesc, 1u);
+                        for (int k = 0; k < kBK / 16; ++k) {
+                            // 16 bf16 = 32 bytes along K -> +2 in the >>4 address field
+                            mma_f16(dacc, a_hi + 2 * k, bd + 2 * k, idesc, (first | k) ? 1u : 0u);
+                            if (SPLIT) mma_f16(dacc, a_lo + 2 * k, bd + 2 * k, idesc, 1u);
+                        }
+                    }
+                    mma_commit(&empty_bar[s]);
                 }
-                mma_commit(&empty_bar[s]);
+                __syncwarp();
+                step = next;
+                if (++s == stages) {
+                    s = 0;
+                    sph ^= 1;
+                }
             }
-            mma_commit(&accum_bar);
+            if (!ok) break;
+            if (elect_one()) {
+                mma_commit(&acc_full[as]);
+                if (shift) mma_commit(&win_empty[ws]);
+            }
+            __syncwarp();
+            if (++as == asets) {
+                as = 0;
+                aph ^= 1;
+            }
+            if (++ws == wsets) {
+                ws = 0;
+                wph ^= 1;
+            }
         }
     } else {
         // Epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (one frame each).
         const int quarter = warp & 3;
-        const bool ready = mbar_wait(&accum_bar, 0, kWaitBudget);
-        if (!ready) atomicExch(&abort_sh, 1);
-        tc_fence_after();
-        const int64_t row = (int64_t)m0 + quarter * 32 + lane;
-        const int64_t b = row / p.rows_per_clip;
-        const int64_t k = row - b * p.rows_per_clip;
-        bool valid = ready && b < p.batch;
-        if (valid) {
-            int64_t len = p.lengths ? p.lengths[b] : p.max_len;
-            len = len < 0 ? 0 : (len > p.max_len ? p.max_len : len);
-            valid = k < (len + p.hop - 1) / p.hop;
-        }
-        if (ready && !*(volatile int*)&abort_sh) {
-            const uint32_t tlane = tmem + ((uint32_t)(quarter * 32) << 16);
-            for (int c0 = 0; c0 < N; c0 += 16) {
-                float v[16];
-                tmem_ld16(tlane + (uint32_t)c0, v);
+        int as = 0;
+        uint32_t aph = 0;
+        for (int u = blockIdx.x; u < nunits && !aborted(); u += gridDim.x) {
+            if (!mbar_wait(&acc_full[as], aph, kWaitBudget)) {
+                fail();
+                break;
+            }
+            tc_fence_after();
+            for (int tt = 0; tt < T; ++tt) {
+                const int64_t row = (int64_t)(u * T + tt) * kBM + quarter * 32 + lane;
+                const int64_t b = row / p.rows_per_clip;
+                const int64_t k = row - b * p.rows_per_clip;
+                bool valid = b < p.batch;
                 if (valid) {
+                    int64_t len = p.lengths ? p.lengths[b] : p.max_len;
+                    len = len < 0 ? 0 : (len > p.max_len ? p.max_len : len);
+                    valid = k < (len + p.hop - 1) / p.hop;
+                }
+                const uint32_t tlane = tmem + (uint32_t)(as * T + tt) * acc_cols +
+                                       ((uint32_t)(quarter * 32) << 16);
+                float* obase = p.out + (valid ? (b * p.S_total) * p.frames_max + k : 0);
+                // 64 columns (32 scales) per wait: four loads in flight at a time.
+                for (int c0 = 0; c0 < N; c0 += 64) {
+                    uint32_t r[64];
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const int sl = (c0 >> 1) + j;
-                        if (sl < p.n_scales) {
-                            const float re = v[2 * j], im = v[2 * j + 1];
-                            const int orow = rows_sh[sl];
-                            p.out[(b * p.S_total + orow) * p.frames_max + k] =
-                                sqrtf(fmaf(re, re, im * im));
+                    for (int q = 0; q < 4; ++q)
+                        if (c0 + 16 * q < N) tmem_ld16_nowait(tlane + (uint32_t)(c0 + 16 * q), r + 16 * q);
+                    tmem_ld_wait();
+                    if (valid) {
+                        const int nsc = min(32, p.n_scales - (c0 >> 1));
+#pragma unroll
+                        for (int jj = 0; jj < 32; ++jj) {
+                            if (jj < nsc) {
+                                const float re = __uint_as_float(r[2 * jj]);
+                                const float im = __uint_as_float(r[2 * jj + 1]);
+                                __stcs(obase + rowoff_sh[(c0 >> 1) + jj],
+                                       sqrt_approx(fmaf(re, re, im * im)));
+                            }
                         }
                     }
                 }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[as]);
+            if (++as == asets) {
+                as = 0;
+                aph ^= 1;
             }
         }
     }
@@ -324,7 +460,7 @@ __global__ void __launch_bounds__(kDirThreads, 1)
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        tmem_dealloc(tmem, tcols);
+        tmem_dealloc(tmem, p.tmem_cols);
     }
     if (threadIdx.x == 0 && abort_sh) atomicExch(p.status, (int)CWTH_ERR_TIMEOUT);
 }
@@ -366,12 +502,21 @@ __global__ void __launch_bounds__(128) direct_f32_kernel(const float* __restrict
 
 }  // namespace
 
-size_t direct_smem_bytes(int ncols, int stages, bool split, int win_rows) {
+// Dynamic shared memory of a launch: two frame windows, the stages, 1 KB of
+// alignment slack, and at least kDirSmemMin so that one CTA holds an SM (the
+// CTA allocates both tensor-memory accumulators).
+constexpr size_t kDirSmemMin = 120 * 1024;
+
+size_t direct_smem_bytes(int ncols, int stages, bool split, int win_rows, int unit,
+                         int win_sets) {
+    const size_t parts = split ? 2 : 1;
     const size_t brows = (size_t)(ncols + 63) / 64 * 64;
-    const size_t a = win_rows > 0 ? 0 : (size_t)kBM * kBK * 2 * (split ? 2 : 1);
+    const size_t a = win_rows > 0 ? 0 : (size_t)kBM * kBK * 2 * parts * unit;
     const size_t stage = a + brows * kBK * 2;
     const size_t win_span = ((size_t)win_rows * kBK * 2 + 1023) / 1024 * 1024;
-    return win_span * (split ? 2 : 1) + stage * stages + 1024;  // + alignment slack
+    const size_t bytes = (win_rows > 0 ? win_span * parts * unit * win_sets : 0) +
+                         stage * stages + 1024;
+    return bytes < kDirSmemMin ? kDirSmemMin : bytes;
 }
 
 int direct_window_rows(int hop, int k_pad) {
@@ -389,21 +534,47 @@ int direct_split_schedule(const int2* in, int n, int2* out) {
 }
 
 // Dynamic shared memory a direct CTA may request: the 227 KB opt-in limit
-// less room for the kernel's static barriers.
-constexpr size_t kDirSmemLimit = 227 * 1024 - 1024;
+// less room for the kernel's static shared memory (barriers, the per-scale
+// output offsets and the schedule: under 2 KB).
+constexpr size_t kDirSmemLimit = 227 * 1024 - 2048;
 
-// Stages: as many as fit while two CTAs still share an SM (one CTA's
-// pipeline fill and epilogue then overlap the other's MMAs); if even two
-// stages do not fit that way, as many as fit in one CTA's opt-in limit.
-constexpr size_t kDirSmemTwoPerSm = 113 * 1024;
-
-int direct_max_stages(int ncols, bool split, int win_rows) {
+int direct_max_stages(int ncols, bool split, int win_rows, int unit, int win_sets) {
     int s = kMaxDirStages;
-    while (s > 2 && direct_smem_bytes(ncols, s, split, win_rows) > kDirSmemTwoPerSm) --s;
-    if (direct_smem_bytes(ncols, s, split, win_rows) <= kDirSmemTwoPerSm) return s;
-    s = kMaxDirStages;
-    while (s > 2 && direct_smem_bytes(ncols, s, split, win_rows) > kDirSmemLimit) --s;
-    return direct_smem_bytes(ncols, s, split, win_rows) <= kDirSmemLimit ? s : 0;
+    while (s > 2 && direct_smem_bytes(ncols, s, split, win_rows, unit, win_sets) > kDirSmemLimit)
+        --s;
+    return direct_smem_bytes(ncols, s, split, win_rows, unit, win_sets) <= kDirSmemLimit ? s : 0;
+}
+
+// Launch shape of a group: frame tiles per unit, window and accumulator
+// sets, stages.  Two tiles share each bank tile only while two accumulator
+// sets still fit in tensor memory (N <= 128): measured on GB300, exposing
+// the epilogue (two 256-column tiles filling all 512 columns) costs more
+// than the halved bank traffic saves.
+DirShape direct_shape(int ncols, bool split, int hop, int k_pad) {
+    DirShape best{};
+    int cpow = 32;
+    while (cpow < ncols) cpow <<= 1;
+    const int win = direct_window_rows(hop, k_pad);
+    for (int unit = 2; unit >= 1; --unit) {
+        const int asets = std::min(2, 512 / (unit * cpow));
+        if (asets < 1 || (unit == 2 && asets < 2)) continue;
+        for (int wrows : {win, 0}) {
+            if (wrows == 0 && win > 0 && best.stages > 0) continue;
+            for (int wsets = (wrows ? 2 : 1); wsets >= 1; --wsets) {
+                const int st = direct_max_stages(ncols, split, wrows, unit, wsets);
+                if (st >= (wsets == 2 ? 3 : 2)) {
+                    best.unit = unit;
+                    best.acc_sets = asets;
+                    best.win_sets = wsets;
+                    best.win_rows = wrows;
+                    best.stages = st;
+                    best.tmem_cols = asets * unit * cpow;
+                    return best;
+                }
+            }
+        }
+    }
+    return best;
 }
 
 cudaError_t direct_prepare_device() {
@@ -440,8 +611,14 @@ cudaError_t direct_stage(const float* x, int64_t ld_x, const int64_t* lengths, i
 
 cudaError_t direct_launch_mma(const CUtensorMap* maps, const DirLaunch& L, bool split,
                               cudaStream_t st) {
-    const int64_t tiles = (L.total_rows + kBM - 1) / kBM;
-    const size_t smem = direct_smem_bytes(L.ncols, L.stages, split, L.a_shift ? L.win_rows : 0);
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int64_t units = ((L.total_rows + kBM - 1) / kBM + L.unit - 1) / L.unit;
+    const int64_t tiles = std::min<int64_t>(units, sms);
+    const size_t smem = direct_smem_bytes(L.ncols, L.stages, split, L.a_shift ? L.win_rows : 0,
+                                          L.unit, L.win_sets);
     if (split)
         direct_mma_kernel<true><<<(unsigned)tiles, kDirThreads, smem, st>>>(maps[0], maps[1],
                                                                            maps[2], maps[3], L);

@@ -2,6 +2,7 @@
 // scratch memory (tap bank, per-scale tables, staged bf16 signal, status
 // word) carved out of one fixed array compiled into the library, for callers
 // that must not allocate device memory while they run (see include/cwth.h).
+#include <limits.h>
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -114,6 +115,8 @@ cwth_status cwth_execute_direct_noalloc(const cwth_morlet* w, const double* scal
             return fail(CWTH_ERR_INVALID_ARG, "scales must be finite and positive");
     if (batch == 0) return CWTH_OK;
     if (!d_x || !d_out || ld_x < max_len) return fail(CWTH_ERR_INVALID_ARG, "NULL buffer or ld_x < max_len");
+    if ((int64_t)S * ((max_len + hop - 1) / hop) > INT32_MAX)
+        return fail(CWTH_ERR_UNSUPPORTED, "one clip's output exceeds 2^31 elements");
 
     // Per-scale supports, scales sorted by support (stack arrays only).
     int32_t order[kMaxScales], hs[kMaxScales];
@@ -273,18 +276,16 @@ cwth_status cwth_execute_direct_noalloc(const cwth_morlet* w, const double* scal
         L.h_group = hg;
         L.n_scales = n;
         L.rows = d_rows + first;
-        L.win_rows = cwth::direct_window_rows(hop, kpad[g]);
-        L.stages = L.win_rows ? cwth::direct_max_stages(ncols[g], split, L.win_rows) : 0;
-        if (L.stages == 0) {
-            L.win_rows = 0;
-            L.stages = cwth::direct_max_stages(ncols[g], split, 0);
-        }
-        L.a_shift = L.win_rows ? 64 / hop : 0;
+        const cwth::DirShape sh = cwth::direct_shape(ncols[g], split, hop, kpad[g]);
+        L.stages = sh.stages;
+        L.win_rows = sh.win_rows;
+        L.a_shift = sh.win_rows ? 64 / hop : 0;
+        L.unit = sh.unit;
+        L.win_sets = sh.win_sets;
+        L.acc_sets = sh.acc_sets;
         L.sched = d_sched + (size_t)g * 2 * (kMaxTaps / 64);
         L.nsteps = nsteps[g];
-        uint32_t tc = 32;
-        while (tc < (uint32_t)ncols[g]) tc <<= 1;
-        L.tmem_cols = tc;
+        L.tmem_cols = sh.tmem_cols;
         if (L.stages == 0) return fail(CWTH_ERR_UNSUPPORTED, "tile does not fit in shared memory");
         e = cwth::direct_launch_mma(maps, L, split, strm);
         if (e != cudaSuccess) return fail_cuda(e);
