@@ -325,82 +325,89 @@ __global__ void __launch_bounds__(kDirThreads, 1)
                 }
         }
     } else if (warp == 1) {
-        // MMA issuer.  Each unit's first step is the centre tap block (hi
-        // part), which every scale reaches: its N covers all columns and its
-        // first MMA per tile initialises that tile's accumulator.
-        int s = 0;
-        uint32_t sph = 0;
-        int as = 0, ws = 0, i = 0;
-        uint32_t aph = 0, wph = 0;
-        const uint32_t stage_base = smem_u32(stage0);
-        for (int u = blockIdx.x; u < nunits && !aborted(); u += gridDim.x, ++i) {
-            if (i >= asets && !mbar_wait_warp(&acc_empty[as], aph ^ 1, kWaitBudget)) {
-                if (lane == 0) fail();
-                break;
-            }
-            if (shift && !mbar_wait_warp(&win_full[ws], wph, kWaitBudget)) {
-                if (lane == 0) fail();
-                break;
-            }
-            tc_fence_after();
-            const uint32_t dacc0 = tmem + (uint32_t)(as * T) * acc_cols;
-            const uint32_t win0 = smem_u32(win_ptr(ws, 0, 0));
-            bool ok = true;
-            int2 step = sched_sh[0];
-            for (int j = 0; j < nsteps; ++j) {
-                // Everything but the MMAs is computed before the wait.
-                const int2 next = sched_sh[j + 1 < nsteps ? j + 1 : j];
-                const uint32_t st = stage_base + (uint32_t)s * stage_bytes;
-                const uint32_t idesc = idesc_bf16_f32(kBM, step.y & 0xFFFF);
-                const uint64_t bd = desc_kmajor_sw128(st + a_step);
-                const uint32_t a0 = shift ? win0 + (uint32_t)(step.x * shift) * 128u : st;
-                const uint32_t first = j > 0 ? 1u : 0u;
-                if (!mbar_wait_warp(&full_bar[s], sph, kWaitBudget)) {
-                    if (lane == 0) fail();
-                    ok = false;
+        // MMA issuer: one elected lane runs the loop.  Each unit's first step
+        // is the centre tap block (hi part), which every scale reaches: its N
+        // covers all columns and its first MMA per tile initialises that
+        // tile's accumulator.  Descriptors are built from 32-bit low words
+        // (start address >> 4) that advance by additions.
+        if (elect_one()) {
+            int s = 0;
+            uint32_t sph = 0;
+            int as = 0, ws = 0, i = 0;
+            uint32_t aph = 0, wph = 0;
+            const uint32_t stage_base = smem_u32(stage0);
+            const uint32_t b_lo0 = desc_sw128_lo(stage_base + a_step);
+            const uint32_t stage16 = stage_bytes >> 4;
+            const uint32_t a_step16 = a_step >> 4;
+            // distance between the A operands of consecutive (tile, part) pairs
+            const uint32_t pitch16 = (shift ? win_span : a_tile) >> 4;
+            const uint32_t idesc0 = idesc_bf16_f32(kBM, 0);
+            uint32_t b_lo = b_lo0;
+            for (int u = blockIdx.x; u < nunits && !aborted(); u += gridDim.x, ++i) {
+                if (i >= asets && !mbar_wait(&acc_empty[as], aph ^ 1, kWaitBudget)) {
+                    fail();
+                    break;
+                }
+                if (shift && !mbar_wait(&win_full[ws], wph, kWaitBudget)) {
+                    fail();
                     break;
                 }
                 tc_fence_after();
-                if (elect_one()) {
+                const uint32_t dacc0 = tmem + (uint32_t)(as * T) * acc_cols;
+                const uint32_t win_lo = desc_sw128_lo(smem_u32(win_ptr(ws, 0, 0)));
+                bool ok = true;
+                int2 step = sched_sh[0];
+                for (int j = 0; j < nsteps; ++j) {
+                    // Everything but the MMAs is computed before the wait.
+                    const int2 next = sched_sh[j + 1 < nsteps ? j + 1 : j];
+                    const uint32_t idesc = idesc0 | ((uint32_t)(step.y & 0xFFFF) >> 3 << 17);
+                    const uint32_t a_lo =
+                        shift ? win_lo + (uint32_t)(step.x * shift) * 8u : b_lo - a_step16;
+                    const uint32_t acc0 = j > 0 ? 1u : 0u;
+                    if (!mbar_wait(&full_bar[s], sph, kWaitBudget)) {
+                        fail();
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
                     for (int tt = 0; tt < T; ++tt) {
                         const uint32_t dacc = dacc0 + (uint32_t)tt * acc_cols;
-                        // tile tt, part q: windows are [tile][part] win_span apart,
-                        // stage A tiles [tile][part] a_tile apart
-                        const uint32_t pitch = shift ? win_span : a_tile;
-                        const uint64_t a_hi = desc_kmajor_sw128(a0 + (uint32_t)(tt * kParts) * pitch);
-                        const uint64_t a_lo =
-                            desc_kmajor_sw128(a0 + (uint32_t)(tt * kParts + kParts - 1) * pitch);
+                        const uint32_t ah = a_lo + (uint32_t)(tt * kParts) * pitch16;
+                        const uint32_t al = ah + (uint32_t)(kParts - 1) * pitch16;
 #pragma unroll
                         for (int k = 0; k < kBK / 16; ++k) {
-                            // 16 bf16 = 32 bytes along K -> +2 in the >>4 address field
-                            mma_f16(dacc, a_hi + 2 * k, bd + 2 * k, idesc, (first | k) ? 1u : 0u);
-                            if (SPLIT) mma_f16(dacc, a_lo + 2 * k, bd + 2 * k, idesc, 1u);
+                            // 16 bf16 = 32 bytes along K -> +2 in the address field
+                            const uint64_t bd = desc_words(b_lo + 2 * k, kDescSw128Hi);
+                            mma_f16(dacc, desc_words(ah + 2 * k, kDescSw128Hi), bd, idesc,
+                                    (acc0 | k) ? 1u : 0u);
+                            if (SPLIT)
+                                mma_f16(dacc, desc_words(al + 2 * k, kDescSw128Hi), bd, idesc, 1u);
                         }
                     }
                     mma_commit(&empty_bar[s]);
+                    step = next;
+                    if (++s == stages) {
+                        s = 0;
+                        sph ^= 1;
+                        b_lo = b_lo0;
+                    } else {
+                        b_lo += stage16;
+                    }
                 }
-                __syncwarp();
-                step = next;
-                if (++s == stages) {
-                    s = 0;
-                    sph ^= 1;
-                }
-            }
-            if (!ok) break;
-            if (elect_one()) {
+                if (!ok) break;
                 mma_commit(&acc_full[as]);
                 if (shift) mma_commit(&win_empty[ws]);
-            }
-            __syncwarp();
-            if (++as == asets) {
-                as = 0;
-                aph ^= 1;
-            }
-            if (++ws == wsets) {
-                ws = 0;
-                wph ^= 1;
+                if (++as == asets) {
+                    as = 0;
+                    aph ^= 1;
+                }
+                if (++ws == wsets) {
+                    ws = 0;
+                    wph ^= 1;
+                }
             }
         }
+        __syncwarp();
     } else {
         // Epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (one frame each).
         const int quarter = warp & 3;

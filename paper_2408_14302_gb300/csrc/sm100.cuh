@@ -187,6 +187,20 @@ __device__ __forceinline__ uint64_t desc_kmajor_sw128(uint32_t smem_addr) {
     return d;
 }
 
+// desc_kmajor_sw128 as two 32-bit words: the low word carries the start
+// address (>> 4, 14 bits; shared-memory addresses stay below 2^18 so adding
+// a few 16-byte units never carries out of the field) and the leading byte
+// offset; the high word is the same for every operand.
+__device__ __forceinline__ uint32_t desc_sw128_lo(uint32_t smem_addr) {
+    return ((smem_addr >> 4) & 0x3FFFu) | (1u << 16);
+}
+constexpr uint32_t kDescSw128Hi = (1024u >> 4) | (1u << 14) | (2u << 29);
+__device__ __forceinline__ uint64_t desc_words(uint32_t lo, uint32_t hi) {
+    uint64_t d;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "r"(lo), "r"(hi));
+    return d;
+}
+
 // Instruction descriptor, kind::f16: f32 accumulator, bf16 A and B, both
 // K-major, shape M x N.
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
