@@ -117,16 +117,34 @@ cwth_status cwth_execute(cwth_plan_t plan, const float *d_x, int64_t ld_x,
                          void *stream);
 
 /*
- * Same transform from and to host memory: copies the batch in (one
- * cudaMemcpyAsync per buffer), runs cwth_execute on `stream`, copies the
- * scalograms out and synchronises the stream before returning.  h_lengths
- * is host memory (or NULL); the other arguments are as in cwth_execute.
- * Device staging is owned by the plan and grows to the largest batch seen.
- * Pinned host buffers make the copies asynchronous DMA transfers.
+ * Same transform from and to host memory.  The batch runs in chunks of
+ * whole clips: chunk c is uploaded on a copy stream of the plan, transformed
+ * on `stream` and downloaded on a second copy stream, so the upload of chunk
+ * c + 1 and the download of chunk c - 1 overlap the transform of chunk c.
+ * The copies start after the work already enqueued on `stream`; the call
+ * synchronises `stream` (which ends with the last download) before
+ * returning.  h_lengths is host memory (or NULL); with lengths, only the
+ * written prefix ceil(len_b / H) of each output row is copied back and the
+ * rest of h_out is left untouched.  The other arguments are as in
+ * cwth_execute.  Device staging is owned by the plan and grows to the
+ * largest batch seen.  Pinned host buffers make the copies asynchronous DMA
+ * transfers (pageable ones serialise them).
+ * Errors: as cwth_execute; after a failure the call still waits for what it
+ * enqueued.
  */
 cwth_status cwth_execute_host(cwth_plan_t plan, const float *h_x, int64_t ld_x,
                               const int64_t *h_lengths, int32_t batch, float *h_out,
                               void *stream);
+
+/*
+ * Chunk count of cwth_execute_host: 0 (the default) chooses it from the
+ * input size (spectral-only plans: about 7 MiB per chunk, at most 8 chunks;
+ * plans with direct-path scales: 2 chunks from 16 MiB on); n >= 1 asks for
+ * n chunks (never more than the batch has clips).  Results do not depend on
+ * it.
+ * Errors: CWTH_ERR_BAD_PLAN, CWTH_ERR_INVALID_ARG (n < 0).
+ */
+cwth_status cwth_plan_set_host_chunks(cwth_plan_t plan, int32_t n);
 
 /* Release a plan's device tables and staging.  NULL is accepted.  The caller
  * must not destroy a plan while work it enqueued may still be running. */

@@ -146,6 +146,43 @@ void free_plan_memory(cwth_plan_s* p) {
     p->d_stage_x = nullptr;
     p->d_stage_out = nullptr;
     p->d_stage_len = nullptr;
+    for (cudaEvent_t* ev : {&p->ev_start, &p->ev_in, &p->ev_comp, &p->ev_out}) {
+        if (*ev) cudaEventDestroy(*ev);
+        *ev = nullptr;
+    }
+    for (cudaStream_t* st : {&p->h2d, &p->d2h, &p->cs2}) {
+        if (*st) cudaStreamDestroy(*st);
+        *st = nullptr;
+    }
+}
+
+// Clip chunks of one cwth_execute_host call, never more than clips.  Spectral
+// chunks run on two alternating streams and stay efficient down to about
+// 7 MiB of input (at most 8 chunks; measured on GB300 with 64 x 10 s clips:
+// 6 chunks best).  Direct-path launches share one workspace and one stream,
+// and a small launch is bound by the latency of its few tiles, so plans with
+// direct-path scales use two chunks once the input reaches 16 MiB.
+int32_t host_chunk_count(const cwth_plan_s* p, int32_t batch, int64_t ld_x) {
+    const int64_t bytes = (int64_t)batch * ld_x * (int64_t)sizeof(float);
+    int64_t n = p->host_chunks;
+    if (n <= 0) {
+        if (p->n_dir > 0)
+            n = bytes >= (16ll << 20) ? 2 : 1;
+        else
+            n = std::min<int64_t>(8, bytes / (7ll << 20));
+    }
+    n = std::max<int64_t>(1, n);
+    return (int32_t)std::min<int64_t>(n, batch);
+}
+
+cudaError_t host_pipeline_init(cwth_plan_s* p) {
+    if (p->h2d) return cudaSuccess;
+    cudaError_t e = cudaStreamCreateWithFlags(&p->h2d, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->d2h, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->cs2, cudaStreamNonBlocking);
+    for (cudaEvent_t* ev : {&p->ev_start, &p->ev_in, &p->ev_comp, &p->ev_out})
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    return e;
 }
 
 int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
@@ -354,12 +391,16 @@ cwth_status build_spectral(cwth_plan_s* p) {
 }
 
 cwth_status launch_spectral(const cwth_plan_s* p, const float* d_x, int64_t ld_x,
-                            const int64_t* d_len, int32_t batch, float* d_out, cudaStream_t st) {
+                            const int64_t* d_len, int32_t batch, float* d_out, cudaStream_t st,
+                            bool fill_gpu) {
     if (p->n_sp == 0 || batch == 0) return CWTH_OK;
-    // Scale groups: enough CTAs for two waves, each group at least 8 scales.
+    // Scale groups: enough CTAs for two waves, each group at least 8 scales
+    // (every group repeats its segment's forward FFT).  A launch that shares
+    // the GPU with other chunks of the same batch keeps one group.
     const int64_t base = (int64_t)p->n_seg * batch;
-    int n_groups = (int)std::min<int64_t>((2 * kNumSms + base - 1) / base,
-                                          std::max(1, p->n_sp / 8));
+    int n_groups = !fill_gpu ? 1
+                             : (int)std::min<int64_t>((2 * kNumSms + base - 1) / base,
+                                                      std::max(1, p->n_sp / 8));
     n_groups = std::max(1, n_groups);
     const int gs = (p->n_sp + n_groups - 1) / n_groups;
     n_groups = (p->n_sp + gs - 1) / gs;
@@ -482,10 +523,10 @@ cwth_status launch_direct(cwth_plan_s* p, const float* d_x, int64_t ld_x, const 
 }
 
 cwth_status launch_all(cwth_plan_s* p, const float* d_x, int64_t ld_x, const int64_t* d_len,
-                       int32_t batch, float* d_out, cudaStream_t st) {
+                       int32_t batch, float* d_out, cudaStream_t st, bool fill_gpu = true) {
     cwth_status s = launch_direct(p, d_x, ld_x, d_len, batch, d_out, st);
     if (s != CWTH_OK) return s;
-    return launch_spectral(p, d_x, ld_x, d_len, batch, d_out, st);
+    return launch_spectral(p, d_x, ld_x, d_len, batch, d_out, st, fill_gpu);
 }
 
 struct DeviceGuard {
@@ -645,41 +686,92 @@ cwth_status cwth_execute_host(cwth_plan_t p, const float* h_x, int64_t ld_x,
     if (!g.ok) return CWTH_ERR_CUDA;
     cudaStream_t st = (cudaStream_t)stream;
     const size_t nx = (size_t)batch * (size_t)ld_x;
-    const size_t no = (size_t)batch * (size_t)p->S * (size_t)p->frames_max;
+    const size_t per_clip = (size_t)p->S * (size_t)p->frames_max;
+    const size_t no = (size_t)batch * per_clip;
     cwth_status s = grow(&p->d_stage_x, &p->stage_x_elems, nx);
     if (s == CWTH_OK) s = grow(&p->d_stage_out, &p->stage_out_elems, no);
     if (s == CWTH_OK && h_lengths) s = grow(&p->d_stage_len, &p->stage_len_elems, (size_t)batch);
     if (s != CWTH_OK) return s;
-    cudaError_t e = cudaMemcpyAsync(p->d_stage_x, h_x, nx * sizeof(float), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess && h_lengths)
-        e = cudaMemcpyAsync(p->d_stage_len, h_lengths, (size_t)batch * sizeof(int64_t),
-                            cudaMemcpyHostToDevice, st);
+    cudaError_t e = host_pipeline_init(p);
     if (e != cudaSuccess) return cuda_status(e);
-    s = launch_all(p, p->d_stage_x, ld_x, h_lengths ? p->d_stage_len : nullptr, batch,
-                   p->d_stage_out, st);
-    if (s != CWTH_OK) return s;
-    if (!h_lengths) {
-        e = cudaMemcpyAsync(h_out, p->d_stage_out, no * sizeof(float), cudaMemcpyDeviceToHost, st);
-    } else {
-        // Rows of short clips keep their trailing frames untouched in h_out:
-        // copy only the written prefix of each row.
-        std::vector<int64_t> F(batch);
+
+    // Frames written per clip (only the written prefix of a short clip's
+    // rows is copied back; the rest of h_out stays untouched).
+    std::vector<int64_t> F;
+    if (h_lengths) {
+        F.resize(batch);
         for (int32_t i = 0; i < batch; ++i) {
-            int64_t len = std::min<int64_t>(std::max<int64_t>(h_lengths[i], 0), p->max_len);
+            const int64_t len = std::min<int64_t>(std::max<int64_t>(h_lengths[i], 0), p->max_len);
             F[i] = cwth_num_frames(len, p->hop);
         }
-        e = cudaSuccess;
-        for (int32_t i = 0; i < batch && e == cudaSuccess; ++i) {
-            if (F[i] == 0) continue;
-            e = cudaMemcpy2DAsync(h_out + (size_t)i * p->S * p->frames_max,
-                                  (size_t)p->frames_max * sizeof(float),
-                                  p->d_stage_out + (size_t)i * p->S * p->frames_max,
-                                  (size_t)p->frames_max * sizeof(float), (size_t)F[i] * sizeof(float),
-                                  (size_t)p->S, cudaMemcpyDeviceToHost, st);
+    }
+    // Chunk c: upload on h2d, transform on `stream`, download on d2h.  Each
+    // event is waited for right after it is recorded, so one event per edge
+    // serves every chunk.  The plan's streams start after the work already
+    // on `stream`, and `stream` ends with the last download.  A plan without
+    // direct-path scales (whose launches share one staging workspace)
+    // transforms odd chunks on a second stream, so that a chunk's last wave
+    // of CTAs overlaps the next chunk's first.
+    const int32_t nch = host_chunk_count(p, batch, ld_x);
+    const bool two = nch > 1 && p->n_dir == 0;
+    e = cudaEventRecord(p->ev_start, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->h2d, p->ev_start, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->d2h, p->ev_start, 0);
+    if (e == cudaSuccess && two) e = cudaStreamWaitEvent(p->cs2, p->ev_start, 0);
+    if (e == cudaSuccess && h_lengths)
+        e = cudaMemcpyAsync(p->d_stage_len, h_lengths, (size_t)batch * sizeof(int64_t),
+                            cudaMemcpyHostToDevice, p->h2d);
+    for (int32_t c = 0; c < nch && e == cudaSuccess && s == CWTH_OK; ++c) {
+        const int32_t b0 = (int32_t)((int64_t)batch * c / nch);
+        const int32_t b1 = (int32_t)((int64_t)batch * (c + 1) / nch);
+        const int32_t nb = b1 - b0;
+        float* dx = p->d_stage_x + (size_t)b0 * ld_x;
+        float* dout = p->d_stage_out + (size_t)b0 * per_clip;
+        e = cudaMemcpyAsync(dx, h_x + (size_t)b0 * ld_x, (size_t)nb * ld_x * sizeof(float),
+                            cudaMemcpyHostToDevice, p->h2d);
+        cudaStream_t cs = (two && (c & 1)) ? p->cs2 : st;
+        if (e == cudaSuccess) e = cudaEventRecord(p->ev_in, p->h2d);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, p->ev_in, 0);
+        if (e != cudaSuccess) break;
+        s = launch_all(p, dx, ld_x, h_lengths ? p->d_stage_len + b0 : nullptr, nb, dout, cs,
+                       nch == 1);
+        if (s != CWTH_OK) break;
+        e = cudaEventRecord(p->ev_comp, cs);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(p->d2h, p->ev_comp, 0);
+        if (e != cudaSuccess) break;
+        if (!h_lengths) {
+            e = cudaMemcpyAsync(h_out + (size_t)b0 * per_clip, dout, (size_t)nb * per_clip * sizeof(float),
+                                cudaMemcpyDeviceToHost, p->d2h);
+        } else {
+            for (int32_t i = b0; i < b1 && e == cudaSuccess; ++i) {
+                if (F[i] == 0) continue;
+                e = cudaMemcpy2DAsync(h_out + (size_t)i * per_clip, (size_t)p->frames_max * sizeof(float),
+                                      p->d_stage_out + (size_t)i * per_clip,
+                                      (size_t)p->frames_max * sizeof(float), (size_t)F[i] * sizeof(float),
+                                      (size_t)p->S, cudaMemcpyDeviceToHost, p->d2h);
+            }
         }
     }
+    // Join whatever was enqueued, also after a failure part-way.
+    cudaError_t ej = cudaEventRecord(p->ev_out, p->d2h);
+    if (ej == cudaSuccess) ej = cudaStreamWaitEvent(st, p->ev_out, 0);
+    if (ej != cudaSuccess) {
+        cudaStreamSynchronize(p->h2d);
+        cudaStreamSynchronize(p->cs2);
+        cudaStreamSynchronize(p->d2h);
+    }
+    cudaError_t es = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_status(e);
-    return cuda_status(cudaStreamSynchronize(st));
+    if (s != CWTH_OK) return s;
+    if (ej != cudaSuccess) return cuda_status(ej);
+    return cuda_status(es);
+}
+
+cwth_status cwth_plan_set_host_chunks(cwth_plan_t p, int32_t chunks) {
+    if (!valid_plan(p)) return CWTH_ERR_BAD_PLAN;
+    if (chunks < 0) return CWTH_ERR_INVALID_ARG;
+    p->host_chunks = chunks;
+    return CWTH_OK;
 }
 
 cwth_status cwth_destroy(cwth_plan_t p) {

@@ -194,4 +194,9 @@ struct cwth_plan_s {
     size_t stage_out_elems = 0;
     int64_t* d_stage_len = nullptr;
     size_t stage_len_elems = 0;
+    // host-API pipeline: clip chunks whose upload, transform and download
+    // overlap (copy-in stream, caller's stream, copy-out stream)
+    int32_t host_chunks = 0;        // 0 = chosen from the batch size
+    cudaStream_t h2d = nullptr, d2h = nullptr, cs2 = nullptr;
+    cudaEvent_t ev_start = nullptr, ev_in = nullptr, ev_comp = nullptr, ev_out = nullptr;
 };

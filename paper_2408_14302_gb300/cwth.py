@@ -24,7 +24,7 @@ PATH = {"auto": 0, "spectral": 1, "direct": 2}
 EXPORTS = ("cwth_plan", "cwth_execute", "cwth_execute_host", "cwth_destroy",
            "cwth_num_frames", "cwth_status_string", "cwth_plan_query",
            "cwth_plan_scale_paths", "cwth_sync", "cwth_last_error",
-           "cwth_execute_direct_noalloc")
+           "cwth_execute_direct_noalloc", "cwth_plan_set_host_chunks")
 
 
 class CwthError(RuntimeError):
@@ -65,6 +65,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.cwth_execute.restype = ctypes.c_int
     lib.cwth_execute_host.argtypes = [vp, vp, i64, vp, i32, vp, vp]
     lib.cwth_execute_host.restype = ctypes.c_int
+    lib.cwth_plan_set_host_chunks.argtypes = [vp, i32]
+    lib.cwth_plan_set_host_chunks.restype = ctypes.c_int
     lib.cwth_destroy.argtypes = [vp]
     lib.cwth_destroy.restype = ctypes.c_int
     lib.cwth_num_frames.argtypes = [i64, i32]
@@ -211,6 +213,10 @@ class Plan:
                                     ctypes.c_void_p(ptr(out)), ctypes.c_void_p(s))
         _check(st, "cwth_execute_host")
         return out
+
+    def set_host_chunks(self, n: int):
+        """Chunks of execute_host (0 = automatic); see cwth_plan_set_host_chunks."""
+        _check(_lib.cwth_plan_set_host_chunks(self._h, int(n)), "cwth_plan_set_host_chunks")
 
     def sync(self, stream=None):
         """Wait for this plan's work on ``stream`` and raise on device-side

@@ -158,6 +158,32 @@ def test_host_entry_point_matches_device(cw, sig):
         assert np.array_equal(hout2[0], dev[0])
 
 
+def test_host_pipeline_chunks_do_not_change_results(cw, sig):
+    # cwth_execute_host overlaps the upload, transform and download of clip
+    # chunks; every chunk count must give the device path's exact bytes,
+    # with and without lengths, on the spectral and the direct path.
+    n, hop, B = 20000, 64, 7
+    xs = np.stack([sig.machine_clip(90 + i, n) for i in range(B)]).astype(np.float32)
+    lens = np.array([n, 1, 0, 12345, n - 1, 64, 9000], np.int64)
+    sc = sig.scales_for_band(60, 7000, 24, 16000.0)
+    hx = torch.from_numpy(xs).pin_memory()
+    for precision in ("fp32", "bf16x2"):
+        with cw.Plan(sc, hop=hop, max_len=n, precision=precision) as plan:
+            dev = plan.execute(torch.from_numpy(xs).cuda()).cpu().numpy()
+            dl = torch.from_numpy(lens).cuda()
+            devl = torch.full((B, len(sc), plan.frames_max), -1.0, device="cuda")
+            plan.execute(torch.from_numpy(xs).cuda(), lengths=dl, out=devl)
+            devl = devl.cpu().numpy()
+            for chunks in (0, 1, 2, 3, 7, 50):
+                plan.set_host_chunks(chunks)
+                hout = torch.empty((B, len(sc), plan.frames_max), dtype=torch.float32).pin_memory()
+                plan.execute_host(hx, hout)
+                assert np.array_equal(hout.numpy(), dev), (precision, chunks)
+                hout2 = np.full((B, len(sc), plan.frames_max), -1.0, np.float32)
+                plan.execute_host(xs, hout2, lengths=lens)
+                assert np.array_equal(hout2, devl), (precision, chunks)
+
+
 def test_non_default_stream_and_two_plans(cw, sig):
     n = 12000
     x = torch.from_numpy(sig.machine_clip(9, n)).cuda().unsqueeze(0)
