@@ -190,6 +190,19 @@ cwth_status cwth_plan_query(cwth_plan_t plan, cwth_plan_info *info);
  * Errors: CWTH_ERR_BAD_PLAN. */
 cwth_status cwth_sync(cwth_plan_t plan, void *stream);
 
+/*
+ * Failure-path self-test (the paper has no counterpart): enqueues on
+ * `stream` a one-thread kernel that waits on an mbarrier nothing arrives on,
+ * for budget_cycles SM clock cycles (1 .. 4e9, i.e. at most about 2 s), and
+ * then records CWTH_ERR_TIMEOUT in the plan's device status word, exactly as
+ * the tensor-core kernels do when a copy or MMA stage never completes.  The
+ * next cwth_sync(plan, stream) returns CWTH_ERR_TIMEOUT and clears the word;
+ * the CUDA context stays usable.  Nothing faults or hangs.
+ * Errors: CWTH_ERR_BAD_PLAN, CWTH_ERR_INVALID_ARG (budget out of range),
+ * CWTH_ERR_CUDA (allocation of the status word or launch failed).
+ */
+cwth_status cwth_selftest_wait_timeout(cwth_plan_t plan, int64_t budget_cycles, void *stream);
+
 /* Per-scale path decision: paths[s] = CWTH_PATH_SPECTRAL or CWTH_PATH_DIRECT
  * for s < S (host array of S entries). */
 cwth_status cwth_plan_scale_paths(cwth_plan_t plan, int32_t *paths);

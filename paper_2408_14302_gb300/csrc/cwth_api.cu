@@ -30,6 +30,9 @@ constexpr int kNumSms = 152;
 constexpr double kEpsDirect = 1e-9;
 // Largest padded tap count the direct path accepts.
 constexpr int kMaxDirectTaps = 4096;
+// Longest wait cwth_selftest_wait_timeout accepts: the kernels' own budget
+// (about 2 s of SM clock).
+constexpr int64_t kMaxSelftestBudget = 4000000000LL;
 
 bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
 int ilog2(int64_t v) {
@@ -821,6 +824,20 @@ cwth_status cwth_sync(cwth_plan_t p, void* stream) {
         }
     }
     return CWTH_OK;
+}
+
+cwth_status cwth_selftest_wait_timeout(cwth_plan_t p, int64_t budget_cycles, void* stream) {
+    if (!valid_plan(p)) return CWTH_ERR_BAD_PLAN;
+    if (budget_cycles < 1 || budget_cycles > kMaxSelftestBudget) return CWTH_ERR_INVALID_ARG;
+    DeviceGuard g(p->device);
+    if (!g.ok) return CWTH_ERR_CUDA;
+    if (!p->d_status) {
+        cudaError_t e = cudaMalloc((void**)&p->d_status, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int));
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    return cuda_status(
+        cwth::direct_wait_selftest(p->d_status, (long long)budget_cycles, (cudaStream_t)stream));
 }
 
 cwth_status cwth_plan_scale_paths(cwth_plan_t p, int32_t* paths) {

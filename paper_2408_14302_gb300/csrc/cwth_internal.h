@@ -117,6 +117,7 @@ int direct_window_rows(int hop, int k_pad);
 // part (bit 16 of .y); returns 2 n.
 int direct_split_schedule(const int2* in, int n, int2* out);
 cudaError_t direct_prepare_device();
+cudaError_t direct_wait_selftest(int* status, long long budget, cudaStream_t st);
 cudaError_t direct_prepare_f32(size_t smem);
 cudaError_t direct_make_bank(const double* d_scales, const int32_t* d_h, int n_scales, int ncols,
                              int k_pad, int h_group, double B, double C, __nv_bfloat16* hi,

@@ -24,7 +24,8 @@ PATH = {"auto": 0, "spectral": 1, "direct": 2}
 EXPORTS = ("cwth_plan", "cwth_execute", "cwth_execute_host", "cwth_destroy",
            "cwth_num_frames", "cwth_status_string", "cwth_plan_query",
            "cwth_plan_scale_paths", "cwth_sync", "cwth_last_error",
-           "cwth_execute_direct_noalloc", "cwth_plan_set_host_chunks")
+           "cwth_execute_direct_noalloc", "cwth_plan_set_host_chunks",
+           "cwth_selftest_wait_timeout")
 
 
 class CwthError(RuntimeError):
@@ -67,6 +68,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.cwth_execute_host.restype = ctypes.c_int
     lib.cwth_plan_set_host_chunks.argtypes = [vp, i32]
     lib.cwth_plan_set_host_chunks.restype = ctypes.c_int
+    lib.cwth_selftest_wait_timeout.argtypes = [vp, i64, vp]
+    lib.cwth_selftest_wait_timeout.restype = ctypes.c_int
     lib.cwth_destroy.argtypes = [vp]
     lib.cwth_destroy.restype = ctypes.c_int
     lib.cwth_num_frames.argtypes = [i64, i32]

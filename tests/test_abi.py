@@ -91,6 +91,7 @@ def test_null_plan_handles(cw):
     assert lib.cwth_execute(None, None, 0, None, 0, None, None) == 6
     assert lib.cwth_execute_host(None, None, 0, None, 0, None, None) == 6
     assert lib.cwth_plan_set_host_chunks(None, 2) == 6
+    assert lib.cwth_selftest_wait_timeout(None, 1000, None) == 6
     info = cw.PlanInfo()
     assert lib.cwth_plan_query(None, ctypes.byref(info)) == 6
     assert lib.cwth_plan_scale_paths(None, None) == 6
