@@ -273,15 +273,44 @@ def cpu_baseline(min_s: float = 3.0):
         if time.perf_counter() - t0 >= min_s or passes >= 20:
             break
     dt = time.perf_counter() - t0
+    cores = oracle.max_threads()
     t1 = time.perf_counter()
     oracle.cwth_magnitude(xs[0], scales, 1)
     dt1 = time.perf_counter() - t1
+    # One thread, on two clips of the same workload.
+    t2 = time.perf_counter()
+    for c in range(2):
+        oracle.cwth_magnitude(xs[c], scales, HOP, threads=1)
+    dt2 = time.perf_counter() - t2
     return {"value": passes * N_CLIPS * (N_SAMPLES / FS) / dt, "unit": UNIT,
-            "cores": oracle.max_threads(), "kind": "oracle",
+            "cores": cores, "kind": "oracle",
             "sample": f"{passes} pass(es) over the whole workload ({N_CLIPS} clips x 10 s, "
                       f"{S} scales, hop {HOP}), float64 direct sum, OpenMP, {dt:.1f} s wall; "
-                      f"hop 1: one clip, {dt1:.1f} s",
-            "hop1_value": (N_SAMPLES / FS) / dt1}
+                      f"hop 1: one clip, {dt1:.1f} s; one thread: 2 clips, {dt2:.1f} s",
+            "hop1_value": (N_SAMPLES / FS) / dt1,
+            "value_1thread": 2 * (N_SAMPLES / FS) / dt2,
+            "cpu_model": cpu_model()}
+
+
+def cpu_model() -> str:
+    """The host CPU: /proc/cpuinfo's model name (x86) or implementer/part
+    codes (Arm, e.g. part 0xd4f)."""
+    import platform
+    fields = {}
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if ":" in line:
+                    k, v = line.split(":", 1)
+                    fields.setdefault(k.strip().lower(), v.strip())
+    except OSError:
+        pass
+    if "model name" in fields:
+        return fields["model name"]
+    if "cpu part" in fields:
+        return (f"{platform.machine()}, CPU implementer {fields.get('cpu implementer', '?')} "
+                f"part {fields['cpu part']}")
+    return platform.processor() or platform.machine()
 
 
 # ------------------------------------------------------------------ direct path leg
@@ -411,7 +440,9 @@ def run_ours(args, rank, world, local_rank):
         ms1 = statistics.mean(a.elapsed_time(b) for a, b in e1)
         hop1 = {"ms_per_step": ms1, "audio_sec_per_s": world * audio_s / (ms1 * 1e-3),
                 "scalogram_gbs": world * o1.numel() * 4 / (ms1 * 1e-3) / 1e9,
-                "seg_len": p1.info()["seg_len"], "num_segments": p1.info()["num_segments"]}
+                "seg_len": p1.info()["seg_len"], "num_segments": p1.info()["num_segments"],
+                "bytes_per_launch": int(N_CLIPS * N_SAMPLES * 4 + o1.numel() * 4),
+                "flops_per_launch": algorithmic_flops_per_clip(scales, 1)[0] * N_CLIPS}
         del o1
         p1.close()
 
@@ -454,8 +485,23 @@ def run_ours(args, rank, world, local_rank):
 
     flops_clip, m_unseg = algorithmic_flops_per_clip(scales, HOP)
     flops_launch = flops_clip * N_CLIPS
-    sm_mhz = clocks.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
-    peak_alu = fp32_peak_tflops(pk.get("sm_max_mhz", 2070.0))
+    peak_derived = fp32_peak_tflops(pk.get("sm_max_mhz", 2070.0))
+    try:
+        peak_alu = cwth.measure_fp32_fma_tflops(stream)
+        peak_alu_src = "measured: FP32 FMA microbenchmark (cwth_measure_fp32_fma), best of 3 launches"
+    except cwth.CwthError:
+        peak_alu, peak_alu_src = peak_derived, "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"
+    if hop1 is not None:
+        # Both roofline fractions at hop 1; the binding one is the larger time at peak.
+        t_alu = hop1["flops_per_launch"] / (peak_alu * 1e12)
+        t_hbm = hop1["bytes_per_launch"] / (pk["hbm_gbs"] * 1e9)
+        s1 = hop1["ms_per_step"] * 1e-3
+        hop1["roofline"] = {
+            "bound": "alu" if t_alu >= t_hbm else "hbm",
+            "alu": {"achieved": hop1["flops_per_launch"] / s1 / 1e12, "peak": peak_alu,
+                    "unit": "TFLOP/s", "frac": t_alu / s1},
+            "hbm": {"achieved": hop1["bytes_per_launch"] / s1 / 1e9, "peak": pk["hbm_gbs"],
+                    "unit": "GB/s", "frac": t_hbm / s1}}
     achieved = flops_launch / (statistics.mean(step_ms) * 1e-3) / 1e12
     bytes_launch = N_CLIPS * (N_SAMPLES * 4 + S * plan.frames_max * 4)
     hbm_achieved = bytes_launch / (statistics.mean(step_ms) * 1e-3) / 1e9
@@ -478,7 +524,7 @@ def run_ours(args, rank, world, local_rank):
                      "frac": achieved / peak_alu,
                      "traffic": kernel_traffic("spectral_segment_kernel", "spectral.cu"),
                      "algorithmic_flops_per_launch": flops_launch,
-                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
+                     "peak_source": peak_alu_src, "peak_derived": peak_derived,
                      "hbm_view": {"algorithmic_bytes_per_launch": bytes_launch,
                                   "achieved_gbs": hbm_achieved, "peak_gbs": pk["hbm_gbs"],
                                   "frac": hbm_achieved / pk["hbm_gbs"],

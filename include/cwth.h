@@ -203,6 +203,16 @@ cwth_status cwth_sync(cwth_plan_t plan, void *stream);
  */
 cwth_status cwth_selftest_wait_timeout(cwth_plan_t plan, int64_t budget_cycles, void *stream);
 
+/*
+ * FP32 FMA throughput of the current device in TFLOP/s (no paper
+ * counterpart): the roofline denominator of the spectral path.  Runs a few
+ * launches of an FMA-only kernel (8 independent chains per thread, every SM
+ * full) on `stream`, times them with CUDA events and returns the best.
+ * Synchronous; about 10 ms.
+ * Errors: CWTH_ERR_INVALID_ARG (NULL tflops), CWTH_ERR_CUDA.
+ */
+cwth_status cwth_measure_fp32_fma(double *tflops, void *stream);
+
 /* Per-scale path decision: paths[s] = CWTH_PATH_SPECTRAL or CWTH_PATH_DIRECT
  * for s < S (host array of S entries). */
 cwth_status cwth_plan_scale_paths(cwth_plan_t plan, int32_t *paths);

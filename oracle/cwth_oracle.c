@@ -69,9 +69,9 @@ int oracle_cwth(const double *x, int64_t n, double bandwidth, double center,
     const int64_t F = oracle_num_frames(n, hop);
     int rc = 0;
 
+    /* Threads of this call only (the process-wide OpenMP default is left as is). */
 #ifdef _OPENMP
-    if (threads > 0)
-        omp_set_num_threads(threads);
+    const int nt = threads > 0 ? threads : omp_get_max_threads();
 #else
     (void)threads;
 #endif
@@ -99,7 +99,7 @@ int oracle_cwth(const double *x, int64_t n, double bandwidth, double center,
             gim[t + h] = -env * sin(ph); /* conjugate */
         }
 
-#pragma omp parallel for schedule(dynamic, 16)
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nt)
         for (int64_t k = 0; k < F; ++k) {
             const int64_t b = k * (int64_t)hop;
             int64_t t0 = -h, t1 = h;

@@ -25,7 +25,7 @@ EXPORTS = ("cwth_plan", "cwth_execute", "cwth_execute_host", "cwth_destroy",
            "cwth_num_frames", "cwth_status_string", "cwth_plan_query",
            "cwth_plan_scale_paths", "cwth_sync", "cwth_last_error",
            "cwth_execute_direct_noalloc", "cwth_plan_set_host_chunks",
-           "cwth_selftest_wait_timeout")
+           "cwth_selftest_wait_timeout", "cwth_measure_fp32_fma")
 
 
 class CwthError(RuntimeError):
@@ -70,6 +70,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.cwth_plan_set_host_chunks.restype = ctypes.c_int
     lib.cwth_selftest_wait_timeout.argtypes = [vp, i64, vp]
     lib.cwth_selftest_wait_timeout.restype = ctypes.c_int
+    lib.cwth_measure_fp32_fma.argtypes = [ctypes.POINTER(ctypes.c_double), vp]
+    lib.cwth_measure_fp32_fma.restype = ctypes.c_int
     lib.cwth_destroy.argtypes = [vp]
     lib.cwth_destroy.restype = ctypes.c_int
     lib.cwth_num_frames.argtypes = [i64, i32]
@@ -104,6 +106,14 @@ def _check(status: int, where: str):
         if status in (2, 3, 4):
             detail = (_lib.cwth_last_error() or b"").decode(errors="replace")
         raise CwthError(status, where, detail)
+
+
+def measure_fp32_fma_tflops(stream=None) -> float:
+    """Measured FP32 FMA throughput of the current device (cwth_measure_fp32_fma)."""
+    v = ctypes.c_double()
+    s = 0 if stream is None else stream.cuda_stream
+    _check(_lib.cwth_measure_fp32_fma(ctypes.byref(v), ctypes.c_void_p(s)), "cwth_measure_fp32_fma")
+    return v.value
 
 
 def num_frames(n: int, hop: int) -> int:
