@@ -196,9 +196,9 @@ __device__ __forceinline__ void fft_pass_dispatch(float2* buf, int L, int nbatch
                                                   const TwTab& tw, int tstride, bool rs, bool ws) {
     const int nb = nbatch * (L / R);
     const int per = (nb + blockDim.x - 1) / blockDim.x;
-    // Up to 8 complex values per thread: the caller keeps nbatch * L <=
-    // kMaxFftPoints = 8 * kSpecThreads.
-    constexpr int kMaxB = 8 / R;
+    // Up to 16 complex values per thread: the caller keeps nbatch * L <=
+    // kMaxFftPoints = 16 * kSpecThreads.
+    constexpr int kMaxB = 16 / R;
     if (per <= 1 || kMaxB <= 1)
         fft_pass<R, 1, INV>(buf, L, nbatch, Ns, tw, tstride, rs, ws);
     else if (per <= 2 || kMaxB <= 2)
@@ -312,7 +312,7 @@ __device__ __forceinline__ float2 fold_residue(const float2* __restrict__ X, con
     return make_float2(sc.gscale * (ad.x + am.x), sc.gscale * (ad.y - am.y));
 }
 
-__global__ void __launch_bounds__(kSpecThreads, 1) spectral_segment_kernel(const SpecLaunch p) {
+__global__ void __launch_bounds__(kSpecThreads, 2) spectral_segment_kernel(const SpecLaunch p) {
     extern __shared__ float2 smem[];
     const int M = p.M, Mh = M >> 1, P = p.P;
     const int ntw = (M >> 7) + 128;
