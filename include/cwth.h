@@ -117,6 +117,27 @@ cwth_status cwth_execute(cwth_plan_t plan, const float *d_x, int64_t ld_x,
                          void *stream);
 
 /*
+ * Resample-first reading of the hop (paper Sec. III.B and Fig. 2, against
+ * the output-decimation reading of Sec. II.B that cwth_plan implements): each
+ * clip x of n samples is re-sampled at the hop spacing, y[m] = x[m H] for
+ * m < ceil(n / H), and the CWT of Eq. 1 is evaluated at every sample of y
+ * with scales a_s / H:
+ *
+ *     W_s[m] = (a_s/H)^{-1/2} sum_j y[j] conj(psi((j - m) / (a_s/H))),
+ *
+ * so the output has the same [clip][scale][ceil(n / H)] shape as
+ * cwth_plan's.  Arguments are as for cwth_plan (scales are given in samples
+ * of x, max_len is the longest x); the plan re-samples on the device inside
+ * cwth_execute / cwth_execute_host (inputs and lengths are those of x) and
+ * then runs the hop-1 transform of y.  No anti-alias filter is applied
+ * (plain re-sampling, as the reading states).
+ * Errors: as cwth_plan.
+ */
+cwth_status cwth_plan_resampled(const cwth_morlet *w, const double *scales, int32_t S, int32_t hop,
+                                double sample_rate, int64_t max_len, int32_t precision,
+                                int32_t path, cwth_plan_t *plan);
+
+/*
  * Same transform from and to host memory.  The batch runs in chunks of
  * whole clips: chunk c is uploaded on a copy stream of the plan, transformed
  * on `stream` and downloaded on a second copy stream, so the upload of chunk
@@ -179,6 +200,9 @@ typedef struct {
     int32_t direct_taps;       /* padded tap count of the direct path          */
     int64_t table_bytes;       /* device bytes held by the plan's tables       */
     double sample_rate;        /* as given to cwth_plan                        */
+    int32_t resample;          /* 1, or H of a cwth_plan_resampled plan (whose
+                                  other fields describe its hop-1 transform of
+                                  the re-sampled signal)                       */
 } cwth_plan_info;
 
 /* Fill *info.  Errors: CWTH_ERR_BAD_PLAN, CWTH_ERR_INVALID_ARG (NULL info). */

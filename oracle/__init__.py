@@ -115,6 +115,17 @@ def cwth(x, scales, hop: int, bandwidth: float = 1.5, center: float = 1.0,
     return re + 1j * im
 
 
+def cwth_resampled(x, scales, hop: int, **kw):
+    """Resample-first reading of the hop (paper Sec. III.B and Fig. 2, the
+    alternative to the output decimation of Sec. II.B): the signal is
+    re-sampled at the hop spacing, y[m] = x[m hop] for m < ceil(n / hop),
+    and Eq. 1 is evaluated at every sample of y with scales a / hop.
+    Complex [S, ceil(n / hop)], float64."""
+    h = int(hop)
+    y = np.ascontiguousarray(np.asarray(x, dtype=np.float64).ravel()[::h])
+    return cwth(y, np.asarray(scales, dtype=np.float64) / h, 1, **kw)
+
+
 def cwth_magnitude(x, scales, hop: int, **kw):
     """|W[s, k]| of one real signal, float64 (the scalogram)."""
     return np.abs(cwth(x, scales, hop, **kw))

@@ -25,6 +25,38 @@ constexpr double kEpsBand = 1e-9;
 // room for the kernel's static arrays.  One 1024-thread CTA fills an SM, so
 // the whole budget is available.
 constexpr size_t kSmemCap = 227 * 1024 - 1024;
+// Dynamic shared memory per spectral CTA that still lets two CTAs share an
+// SM (228 KB per SM, 1 KB reserved per CTA).
+constexpr size_t kSmemPair = 113 * 1024;
+// Cost of one pass over a group of scales (fold + inverse FFT + stores, each
+// ending at a CTA barrier) in the model's lane-operation units (~3k cycles
+// measured on GB300).
+constexpr double kPassCost = 64000.0;
+
+// Scales one CTA folds and inverts together within `cap` bytes of shared
+// memory (at most `limit`).
+int nconc_within(int M, int P, int limit, size_t cap) {
+    int nconc = std::max(1, limit);
+    while (nconc > 1 && cwth::spectral_smem_bytes(M, P, nconc) > cap) --nconc;
+    while (nconc > 1 && (int64_t)nconc * P > cwth::kMaxFftPoints) --nconc;
+    return nconc;
+}
+
+// CTA shape of the spectral kernel for a segment length (see
+// cwth_internal.h): two 512-thread CTAs per SM unless they do not fit, or
+// fit at most two scales per pass where one 1024-thread CTA fits more.
+int spectral_threads(int M, int P, int n_scales) {
+    if (cwth::spectral_smem_bytes(M, P, 1) > kSmemPair) return cwth::kSpecThreadsSolo;
+    const int pair = nconc_within(M, P, n_scales, kSmemPair);
+    const int solo = nconc_within(M, P, n_scales, kSmemCap);
+    return (pair <= 2 && solo > pair) ? cwth::kSpecThreadsSolo : cwth::kSpecThreadsPair;
+}
+
+// Scales one spectral CTA folds and inverts together for a segment length
+// and CTA shape.
+int spectral_nconc(int M, int P, int limit, int threads) {
+    return nconc_within(M, P, limit, threads == cwth::kSpecThreadsSolo ? kSmemCap : kSmemPair);
+}
 constexpr int kNumSms = 152;
 // Direct path: taps below this fraction of the wavelet peak are dropped.
 constexpr double kEpsDirect = 1e-9;
@@ -90,6 +122,7 @@ bool choose_segment(const cwth_plan_s& p, const std::vector<double>& sp_scales, 
         const int64_t Fseg = last - kp0 + 1;
         if (Fseg < 1) continue;
         if (cwth::spectral_smem_bytes((int)M, (int)P, 1) > kSmemCap) continue;
+        const int threads = spectral_threads((int)M, (int)P, (int)sp_scales.size());
         if (M / 2 > cwth::kMaxFftPoints || P > cwth::kMaxFftPoints) continue;
         const int64_t n_seg = (p.frames_max + Fseg - 1) / Fseg;
         double fold = 0;
@@ -101,7 +134,9 @@ bool choose_segment(const cwth_plan_s& p, const std::vector<double>& sp_scales, 
         const double fft = 2.5 * (double)(M / 2) * (lg - 1) + 8.0 * (double)M;
         const double ifft = 2.5 * (double)P * ilog2(P) * (double)sp_scales.size();
         const double store = 2.0 * (double)Fseg * (double)sp_scales.size();
-        const double cost = (double)n_seg * (fft + fold + ifft + store);
+        const int nconc = spectral_nconc((int)M, (int)P, (int)sp_scales.size(), threads);
+        const double passes = (double)((sp_scales.size() + nconc - 1) / nconc);
+        const double cost = (double)n_seg * (fft + fold + ifft + store + kPassCost * passes);
         if (!found || cost < out->cost) {
             found = true;
             out->M = (int)M;
@@ -149,6 +184,10 @@ void free_plan_memory(cwth_plan_s* p) {
     p->d_stage_x = nullptr;
     p->d_stage_out = nullptr;
     p->d_stage_len = nullptr;
+    cudaFree(p->d_res);
+    cudaFree(p->d_res_len);
+    p->d_res = nullptr;
+    p->d_res_len = nullptr;
     for (cudaEvent_t* ev : {&p->ev_start, &p->ev_in, &p->ev_comp, &p->ev_out}) {
         if (*ev) cudaEventDestroy(*ev);
         *ev = nullptr;
@@ -407,9 +446,8 @@ cwth_status launch_spectral(const cwth_plan_s* p, const float* d_x, int64_t ld_x
     n_groups = std::max(1, n_groups);
     const int gs = (p->n_sp + n_groups - 1) / n_groups;
     n_groups = (p->n_sp + gs - 1) / gs;
-    int nconc = gs;
-    while (nconc > 1 && cwth::spectral_smem_bytes(p->M, p->P, nconc) > kSmemCap) --nconc;
-    while (nconc > 1 && (int64_t)nconc * p->P > cwth::kMaxFftPoints) --nconc;
+    const int threads = spectral_threads(p->M, p->P, p->n_sp);
+    const int nconc = spectral_nconc(p->M, p->P, gs, threads);
     if (batch > 65535 || p->n_seg > 0x7fffffff) return CWTH_ERR_UNSUPPORTED;
 
     SpecLaunch L;
@@ -434,7 +472,8 @@ cwth_status launch_spectral(const cwth_plan_s* p, const float* d_x, int64_t ld_x
     L.tw = p->d_tw;
     L.sc = p->d_sp;
     const size_t smem = cwth::spectral_smem_bytes(p->M, p->P, nconc);
-    return cuda_status(cwth::spectral_launch(L, p->n_seg, batch, n_groups, smem, st));
+    return cuda_status(
+        cwth::spectral_launch(L, threads, p->n_seg, batch, n_groups, smem, st));
 }
 
 cwth_status launch_direct(cwth_plan_s* p, const float* d_x, int64_t ld_x, const int64_t* d_len,
@@ -532,6 +571,10 @@ cwth_status launch_all(cwth_plan_s* p, const float* d_x, int64_t ld_x, const int
     return launch_spectral(p, d_x, ld_x, d_len, batch, d_out, st, fill_gpu);
 }
 
+// Samples each input row must hold: the longest clip, or for a
+// resample-first plan the longest clip before re-sampling.
+int64_t input_len(const cwth_plan_s* p) { return p->resample > 1 ? p->in_len : p->max_len; }
+
 struct DeviceGuard {
     int prev = -1;
     bool ok = true;
@@ -561,6 +604,25 @@ cwth_status grow(T** ptr, size_t* have, size_t need) {
     }
     *have = need;
     return CWTH_OK;
+}
+
+// The transform of rows [row0, row0 + batch) of a plan's workspace: a
+// resample-first plan first re-samples the inputs into its own buffer (rows
+// from row0 on, so concurrent chunks use disjoint rows).  `ws_rows` is the
+// number of rows the workspace must hold.
+cwth_status launch_transform(cwth_plan_s* p, const float* d_x, int64_t ld_x, const int64_t* d_len,
+                             int32_t batch, float* d_out, cudaStream_t st, bool fill_gpu,
+                             int64_t row0, int64_t ws_rows) {
+    if (p->resample <= 1) return launch_all(p, d_x, ld_x, d_len, batch, d_out, st, fill_gpu);
+    cwth_status s = grow(&p->d_res, &p->res_elems, (size_t)ws_rows * (size_t)p->max_len);
+    if (s == CWTH_OK && d_len) s = grow(&p->d_res_len, &p->res_len_elems, (size_t)ws_rows);
+    if (s != CWTH_OK) return s;
+    float* y = p->d_res + (size_t)row0 * (size_t)p->max_len;
+    int64_t* ly = d_len ? p->d_res_len + row0 : nullptr;
+    cudaError_t e = cwth::resample_launch(d_x, ld_x, d_len, p->in_len, p->resample, y, p->max_len,
+                                          ly, batch, st);
+    if (e != cudaSuccess) return cuda_status(e);
+    return launch_all(p, y, p->max_len, ly, batch, d_out, st, fill_gpu);
 }
 
 }  // namespace
@@ -666,16 +728,36 @@ cwth_status cwth_plan(const cwth_morlet* w, const double* scales, int32_t S, int
     return CWTH_OK;
 }
 
+cwth_status cwth_plan_resampled(const cwth_morlet* w, const double* scales, int32_t S, int32_t hop,
+                                double sample_rate, int64_t max_len, int32_t precision,
+                                int32_t path, cwth_plan_t* out) {
+    if (out) *out = nullptr;
+    if (!w || !scales || !out) return CWTH_ERR_INVALID_ARG;
+    if (S < 1 || hop < 1 || max_len < 1) return CWTH_ERR_INVALID_ARG;
+    if (!(isfinite(sample_rate) && sample_rate > 0)) return CWTH_ERR_INVALID_ARG;
+    std::vector<double> sc(scales, scales + S);
+    for (double& a : sc) {
+        if (!(isfinite(a) && a > 0)) return CWTH_ERR_INVALID_ARG;
+        a /= hop;
+    }
+    cwth_status st = cwth_plan(w, sc.data(), S, 1, sample_rate / hop, cwth_num_frames(max_len, hop),
+                               precision, path, out);
+    if (st != CWTH_OK) return st;
+    (*out)->resample = hop;
+    (*out)->in_len = max_len;
+    return CWTH_OK;
+}
+
 cwth_status cwth_execute(cwth_plan_t p, const float* d_x, int64_t ld_x, const int64_t* d_lengths,
                          int32_t batch, float* d_out, void* stream) {
     if (!valid_plan(p)) return CWTH_ERR_BAD_PLAN;
     if (batch < 0) return CWTH_ERR_INVALID_ARG;
     if (batch == 0) return CWTH_OK;
-    if (!d_x || !d_out || ld_x < p->max_len) return CWTH_ERR_INVALID_ARG;
+    if (!d_x || !d_out || ld_x < input_len(p)) return CWTH_ERR_INVALID_ARG;
     DeviceGuard g(p->device);
     if (!g.ok) return CWTH_ERR_CUDA;
     cudaStream_t st = (cudaStream_t)stream;
-    return launch_all(p, d_x, ld_x, d_lengths, batch, d_out, st);
+    return launch_transform(p, d_x, ld_x, d_lengths, batch, d_out, st, true, 0, batch);
 }
 
 cwth_status cwth_execute_host(cwth_plan_t p, const float* h_x, int64_t ld_x,
@@ -684,7 +766,7 @@ cwth_status cwth_execute_host(cwth_plan_t p, const float* h_x, int64_t ld_x,
     if (!valid_plan(p)) return CWTH_ERR_BAD_PLAN;
     if (batch < 0) return CWTH_ERR_INVALID_ARG;
     if (batch == 0) return CWTH_OK;
-    if (!h_x || !h_out || ld_x < p->max_len) return CWTH_ERR_INVALID_ARG;
+    if (!h_x || !h_out || ld_x < input_len(p)) return CWTH_ERR_INVALID_ARG;
     DeviceGuard g(p->device);
     if (!g.ok) return CWTH_ERR_CUDA;
     cudaStream_t st = (cudaStream_t)stream;
@@ -704,8 +786,8 @@ cwth_status cwth_execute_host(cwth_plan_t p, const float* h_x, int64_t ld_x,
     if (h_lengths) {
         F.resize(batch);
         for (int32_t i = 0; i < batch; ++i) {
-            const int64_t len = std::min<int64_t>(std::max<int64_t>(h_lengths[i], 0), p->max_len);
-            F[i] = cwth_num_frames(len, p->hop);
+            const int64_t len = std::min<int64_t>(std::max<int64_t>(h_lengths[i], 0), input_len(p));
+            F[i] = cwth_num_frames(len, p->hop * p->resample);
         }
     }
     // Chunk c: upload on h2d, transform on `stream`, download on d2h.  Each
@@ -736,8 +818,8 @@ cwth_status cwth_execute_host(cwth_plan_t p, const float* h_x, int64_t ld_x,
         if (e == cudaSuccess) e = cudaEventRecord(p->ev_in, p->h2d);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, p->ev_in, 0);
         if (e != cudaSuccess) break;
-        s = launch_all(p, dx, ld_x, h_lengths ? p->d_stage_len + b0 : nullptr, nb, dout, cs,
-                       nch == 1);
+        s = launch_transform(p, dx, ld_x, h_lengths ? p->d_stage_len + b0 : nullptr, nb, dout, cs,
+                             nch == 1, b0, batch);
         if (s != CWTH_OK) break;
         e = cudaEventRecord(p->ev_comp, cs);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(p->d2h, p->ev_comp, 0);
@@ -805,6 +887,7 @@ cwth_status cwth_plan_query(cwth_plan_t p, cwth_plan_info* info) {
     info->direct_taps = p->dir_taps;
     info->table_bytes = p->table_bytes;
     info->sample_rate = p->fs;
+    info->resample = p->resample;
     return CWTH_OK;
 }
 

@@ -8,18 +8,25 @@
 
 #include <vector>
 
+#include <algorithm>
+
 #include "cwth.h"
 
 namespace cwth {
 
 constexpr uint32_t kPlanMagic = 0xC0A7B17Eu;
-// Spectral CTAs: 512 threads, two per SM (64 registers each), so one CTA's
-// phase barriers are covered by the other's work (measured on GB300: 8 %
-// faster than one 1024-thread CTA per SM at the same work split).
-constexpr int kSpecThreads = 512;
-// Largest batched shared-memory FFT (complex points) one CTA performs: at
-// most 16 points per thread per pass.
-constexpr int kMaxFftPoints = 16 * kSpecThreads;
+// Spectral CTA shapes (64 registers per thread either way): two 512-thread
+// CTAs per SM, so one CTA's phase barriers are covered by the other's work,
+// or one 1024-thread CTA per SM, which has the whole SM's shared memory and
+// so inverts more scales per pass when the inverse FFTs are long.  Measured
+// on GB300 (64 x 10 s clips, 64 scales): the pair is 0-20 % faster unless it
+// fits at most two scales per pass and the single CTA fits more (hops 4-8
+// at M = 16384), where the single CTA is 15-20 % faster.
+constexpr int kSpecThreadsPair = 512;
+constexpr int kSpecThreadsSolo = 1024;
+// Largest batched shared-memory FFT (complex points) one CTA performs: 16
+// points per thread per pass for the 512-thread shape, 8 for 1024.
+constexpr int kMaxFftPoints = 8192;
 
 // Per-scale parameters of the spectral path (one entry per spectral scale).
 // The multiplier at unwrapped bin q_u is
@@ -107,7 +114,7 @@ size_t spectral_smem_bytes(int M, int P, int nconc);
 int spectral_twiddle_entries(int M);
 cudaError_t spectral_prepare_device();
 cudaError_t spectral_make_twiddles(float2* d_tw, int M, cudaStream_t st);
-cudaError_t spectral_launch(const SpecLaunch& L, int n_seg, int batch, int n_groups,
+cudaError_t spectral_launch(const SpecLaunch& L, int threads, int n_seg, int batch, int n_groups,
                             size_t smem, cudaStream_t st);
 
 size_t direct_smem_bytes(int ncols, int stages, bool split, int win_rows, int unit,
@@ -121,6 +128,9 @@ int direct_window_rows(int hop, int k_pad);
 int direct_split_schedule(const int2* in, int n, int2* out);
 cudaError_t direct_prepare_device();
 cudaError_t direct_wait_selftest(int* status, long long budget, cudaStream_t st);
+cudaError_t resample_launch(const float* x, int64_t ld_x, const int64_t* lengths, int64_t in_len,
+                            int32_t H, float* y, int64_t ld_y, int64_t* len_y, int batch,
+                            cudaStream_t st);
 cudaError_t direct_prepare_f32(size_t smem);
 cudaError_t direct_make_bank(const double* d_scales, const int32_t* d_h, int n_scales, int ncols,
                              int k_pad, int h_group, double B, double C, __nv_bfloat16* hi,
@@ -201,6 +211,14 @@ struct cwth_plan_s {
     // host-API pipeline: clip chunks whose upload, transform and download
     // overlap (copy-in stream, caller's stream, copy-out stream)
     int32_t host_chunks = 0;        // 0 = chosen from the batch size
+    // resample-first plans (cwth_plan_resampled): inputs of in_len samples are
+    // re-sampled by `resample` into d_res before the hop-1 transform
+    int32_t resample = 1;
+    int64_t in_len = 0;
+    float* d_res = nullptr;
+    size_t res_elems = 0;
+    int64_t* d_res_len = nullptr;
+    size_t res_len_elems = 0;
     cudaStream_t h2d = nullptr, d2h = nullptr, cs2 = nullptr;
     cudaEvent_t ev_start = nullptr, ev_in = nullptr, ev_comp = nullptr, ev_out = nullptr;
 };

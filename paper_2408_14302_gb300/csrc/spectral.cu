@@ -191,14 +191,14 @@ __device__ __forceinline__ void fft_pass(float2* __restrict__ buf, int L, int nb
     __syncthreads();
 }
 
-template <int R, bool INV>
+template <int R, bool INV, int PPT>
 __device__ __forceinline__ void fft_pass_dispatch(float2* buf, int L, int nbatch, int Ns,
                                                   const TwTab& tw, int tstride, bool rs, bool ws) {
     const int nb = nbatch * (L / R);
     const int per = (nb + blockDim.x - 1) / blockDim.x;
-    // Up to 16 complex values per thread: the caller keeps nbatch * L <=
-    // kMaxFftPoints = 16 * kSpecThreads.
-    constexpr int kMaxB = 16 / R;
+    // Up to PPT complex values per thread: the caller keeps nbatch * L <=
+    // kMaxFftPoints = PPT * blockDim.x.
+    constexpr int kMaxB = PPT / R;
     if (per <= 1 || kMaxB <= 1)
         fft_pass<R, 1, INV>(buf, L, nbatch, Ns, tw, tstride, rs, ws);
     else if (per <= 2 || kMaxB <= 2)
@@ -212,7 +212,7 @@ __device__ __forceinline__ void fft_pass_dispatch(float2* buf, int L, int nbatch
 // Batched power-of-two FFT in shared memory, natural order in and out.
 // ts = M / L maps the transform's twiddles onto the table of exp(-2 pi i m/M).
 // Radices: 8 where possible, a leading 4 (or 4,4) for the remainder of log2 L.
-template <bool INV>
+template <bool INV, int PPT>
 __device__ __forceinline__ void fft_block(float2* buf, int L, int nbatch, const TwTab& tw, int ts) {
     const int e = __ffs(L) - 1;  // L >= 8: the plan keeps P = M/H >= 8 and M/2 >= 256
     const int n4 = (e % 3 == 1) ? 2 : (e % 3 == 2) ? 1 : 0;
@@ -221,10 +221,10 @@ __device__ __forceinline__ void fft_block(float2* buf, int L, int nbatch, const 
     for (int i = 0; i < npass; ++i) {
         const bool rs = i > 0, ws = i + 1 < npass;
         if (i < n4) {
-            fft_pass_dispatch<4, INV>(buf, L, nbatch, Ns, tw, ts * (L / (Ns * 4)), rs, ws);
+            fft_pass_dispatch<4, INV, PPT>(buf, L, nbatch, Ns, tw, ts * (L / (Ns * 4)), rs, ws);
             Ns *= 4;
         } else {
-            fft_pass_dispatch<8, INV>(buf, L, nbatch, Ns, tw, ts * (L / (Ns * 8)), rs, ws);
+            fft_pass_dispatch<8, INV, PPT>(buf, L, nbatch, Ns, tw, ts * (L / (Ns * 8)), rs, ws);
             Ns *= 8;
         }
     }
@@ -312,7 +312,9 @@ __device__ __forceinline__ float2 fold_residue(const float2* __restrict__ X, con
     return make_float2(sc.gscale * (ad.x + am.x), sc.gscale * (ad.y - am.y));
 }
 
-__global__ void __launch_bounds__(kSpecThreads, 2) spectral_segment_kernel(const SpecLaunch p) {
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS, 1024 / THREADS) spectral_segment_kernel(const SpecLaunch p) {
+    constexpr int kPPT = kMaxFftPoints / THREADS;  // FFT points per thread
     extern __shared__ float2 smem[];
     const int M = p.M, Mh = M >> 1, P = p.P;
     const int ntw = (M >> 7) + 128;
@@ -344,7 +346,7 @@ __global__ void __launch_bounds__(kSpecThreads, 2) spectral_segment_kernel(const
     __syncthreads();
 
     // a2: forward FFT of the M/2 points, twiddles exp(-2 pi i m/(M/2)) = tw[2m].
-    fft_block<false>(X, Mh, 1, tab, 2);
+    fft_block<false, kPPT>(X, Mh, 1, tab, 2);
 
     // Real-input split: with Z = FFT(z), E = (Z[q] + conj Z[Mh-q])/2 and
     // O = (Z[q] - conj Z[Mh-q])/(2i) are the spectra of the even and odd
@@ -392,7 +394,7 @@ __global__ void __launch_bounds__(kSpecThreads, 2) spectral_segment_kernel(const
 
         // a4: inverse FFT of length P for every scale of the chunk; the 1/M
         // normalisation is already in gscale.  exp(+2 pi i m/P) = conj(tw[m H]).
-        fft_block<true>(Z, P, nc, tab, p.hop);
+        fft_block<true, kPPT>(Z, P, nc, tab, p.hop);
 
         const int Fs = p.seg_frames;
         for (int i = threadIdx.x; i < nc * Fs; i += blockDim.x) {
@@ -432,7 +434,11 @@ size_t spectral_smem_bytes(int M, int P, int nconc) {
 int spectral_twiddle_entries(int M) { return (M >> 7) + 128; }
 
 cudaError_t spectral_prepare_device() {
-    return cudaFuncSetAttribute(spectral_segment_kernel,
+    cudaError_t e = cudaFuncSetAttribute(spectral_segment_kernel<kSpecThreadsPair>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         227 * 1024 - 1024);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(spectral_segment_kernel<kSpecThreadsSolo>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024 - 1024);
 }
 
@@ -441,10 +447,13 @@ cudaError_t spectral_make_twiddles(float2* d_tw, int M, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t spectral_launch(const SpecLaunch& L, int n_seg, int batch, int n_groups, size_t smem,
-                            cudaStream_t st) {
+cudaError_t spectral_launch(const SpecLaunch& L, int threads, int n_seg, int batch, int n_groups,
+                            size_t smem, cudaStream_t st) {
     dim3 grid(n_seg, batch, n_groups);
-    spectral_segment_kernel<<<grid, kSpecThreads, smem, st>>>(L);
+    if (threads == kSpecThreadsSolo)
+        spectral_segment_kernel<kSpecThreadsSolo><<<grid, kSpecThreadsSolo, smem, st>>>(L);
+    else
+        spectral_segment_kernel<kSpecThreadsPair><<<grid, kSpecThreadsPair, smem, st>>>(L);
     return cudaGetLastError();
 }
 

@@ -25,7 +25,7 @@ EXPORTS = ("cwth_plan", "cwth_execute", "cwth_execute_host", "cwth_destroy",
            "cwth_num_frames", "cwth_status_string", "cwth_plan_query",
            "cwth_plan_scale_paths", "cwth_sync", "cwth_last_error",
            "cwth_execute_direct_noalloc", "cwth_plan_set_host_chunks",
-           "cwth_selftest_wait_timeout", "cwth_measure_fp32_fma")
+           "cwth_selftest_wait_timeout", "cwth_measure_fp32_fma", "cwth_plan_resampled")
 
 
 class CwthError(RuntimeError):
@@ -47,7 +47,8 @@ class PlanInfo(ctypes.Structure):
                 ("seg_len", ctypes.c_int32), ("seg_frames", ctypes.c_int32),
                 ("seg_halo", ctypes.c_int32), ("fold_len", ctypes.c_int32),
                 ("num_segments", ctypes.c_int32), ("direct_taps", ctypes.c_int32),
-                ("table_bytes", ctypes.c_int64), ("sample_rate", ctypes.c_double)]
+                ("table_bytes", ctypes.c_int64), ("sample_rate", ctypes.c_double),
+                ("resample", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -62,6 +63,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.cwth_plan.argtypes = [ctypes.POINTER(Morlet), ctypes.POINTER(ctypes.c_double), i32, i32,
                               dp, i64, i32, i32, ctypes.POINTER(vp)]
     lib.cwth_plan.restype = ctypes.c_int
+    lib.cwth_plan_resampled.argtypes = lib.cwth_plan.argtypes
+    lib.cwth_plan_resampled.restype = ctypes.c_int
     lib.cwth_execute.argtypes = [vp, vp, i64, vp, i32, vp, vp]
     lib.cwth_execute.restype = ctypes.c_int
     lib.cwth_execute_host.argtypes = [vp, vp, i64, vp, i32, vp, vp]
@@ -147,11 +150,14 @@ def execute_direct_noalloc(scales, hop: int, x, out, lengths=None, precision: st
 
 
 class Plan:
-    """A cwth_plan_t: scales (in samples), hop, Morlet B/C and the longest clip."""
+    """A cwth_plan_t: scales (in samples), hop, Morlet B/C and the longest clip.
+    ``resample_first=True`` makes a cwth_plan_resampled plan (the signal is
+    re-sampled at the hop spacing, then transformed at every sample with
+    scales / hop); its inputs and output shape are the same."""
 
     def __init__(self, scales, hop: int, max_len: int, bandwidth: float = 1.5,
                  center: float = 1.0, sample_rate: float = 16000.0,
-                 precision: str = "fp32", path: str = "auto"):
+                 precision: str = "fp32", path: str = "auto", resample_first: bool = False):
         sc = np.ascontiguousarray(np.asarray(scales, dtype=np.float64).ravel())
         self.scales = sc
         self.hop = int(hop)
@@ -159,10 +165,11 @@ class Plan:
         self.S = int(sc.shape[0])
         self._h = ctypes.c_void_p()
         w = Morlet(float(bandwidth), float(center))
-        st = _lib.cwth_plan(ctypes.byref(w), sc.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                            self.S, self.hop, float(sample_rate), self.max_len,
-                            PREC[precision], PATH[path], ctypes.byref(self._h))
-        _check(st, "cwth_plan")
+        make = _lib.cwth_plan_resampled if resample_first else _lib.cwth_plan
+        st = make(ctypes.byref(w), sc.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                  self.S, self.hop, float(sample_rate), self.max_len,
+                  PREC[precision], PATH[path], ctypes.byref(self._h))
+        _check(st, "cwth_plan_resampled" if resample_first else "cwth_plan")
         self.frames_max = num_frames(self.max_len, self.hop)
 
     @property

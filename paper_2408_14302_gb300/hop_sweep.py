@@ -6,7 +6,11 @@ The paper's method computes the CWT only at positions spaced by the hop
 batch of machine-sound clips, a fixed scale bank, and for every hop the time
 of one cwth_execute on the float32 spectral path and, where the hop allows
 the tensor-core direct path (H a multiple of 8), on the split-bf16 automatic
-path (both within 1e-5 of max|W|).
+path (both within 1e-5 of max|W|).  With --resample it also times the
+resample-first reading of the hop (Sec. III.B, Fig. 2: re-sample the signal
+at spacing H, then transform every sample with scales a / H) beside the
+output-decimation transform, both on the scales the re-sampled signal can
+represent (centre frequencies up to fs / (2 H)).
 
     python -m paper_2408_14302_gb300.hop_sweep [--clips 64] [--seconds 10] [--scales 64]
 
@@ -54,6 +58,7 @@ def main(argv=None):
     ap.add_argument("--f-hi", type=float, default=8000.0)
     ap.add_argument("--hops", default="1,2,4,8,16,32,64,128,256,512,1024")
     ap.add_argument("--reps", type=int, default=10)
+    ap.add_argument("--resample", action="store_true")
     a = ap.parse_args(argv)
     import torch
 
@@ -89,6 +94,25 @@ def main(argv=None):
                 "frames": plan.frames_max, "num_spectral": info["num_spectral"],
                 "num_direct": info["num_direct"], "seg_len": info["seg_len"],
                 "num_segments": info["num_segments"]}), flush=True)
+            plan.close()
+            del out
+        if not a.resample:
+            continue
+        f_top = min(a.f_hi, a.fs / (2 * hop))
+        if f_top <= a.f_lo:
+            print(json.dumps({"hop": hop, "resample_first": "skipped: no scale below fs/(2H)"}),
+                  flush=True)
+            continue
+        sc_r = signals.scales_for_band(a.f_lo, f_top, a.scales, a.fs)
+        for first in (False, True):
+            plan = cwth.Plan(sc_r, hop=hop, max_len=n, sample_rate=a.fs, precision="fp32",
+                             path="spectral" if not first else "auto", resample_first=first)
+            out = torch.empty((a.clips, a.scales, plan.frames_max), device=dev)
+            ms = time_execute(torch, plan, x, out, stream, flush, a.reps)
+            print(json.dumps({
+                "hop": hop, "form": "resample_first" if first else "output_decimation",
+                "f_hi_hz": f_top, "precision": "fp32", "ms": ms, "ms_per_clip": ms / a.clips,
+                "audio_sec_per_s": audio / (ms * 1e-3), "frames": plan.frames_max}), flush=True)
             plan.close()
             del out
 

@@ -301,3 +301,51 @@ def test_mutants_are_caught(name, tmp_path, oracle_mod):
     assert src.count(old) == 1, f"mutation anchor for {name} not found"
     cwth, hs = _build_mutant(src.replace(old, new), str(tmp_path), name)
     assert _pins_reject(cwth, hs), f"mutant {name} passed every pin"
+
+
+# ---------------------------------------------------------------- resample-first reading
+# oracle.cwth_resampled(x, a, H) re-samples y[m] = x[m H] and evaluates Eq. 1
+# at every sample of y with scale a / H (paper Sec. III.B, Fig. 2).
+
+def test_resampled_at_hop_1_is_the_cwt(oracle_mod):
+    x = signals.tones_clip(seed=11, n=1500)
+    sc = signals.scales_for_band(100, 8000, 6, 16000.0)
+    assert np.array_equal(oracle_mod.cwth_resampled(x, sc, 1), oracle_mod.cwth(x, sc, 1))
+
+
+def test_resampled_closed_form(oracle_mod):
+    # Re-sampling exp(i 2 pi nu n) at spacing H gives exp(i 2 pi (nu H) m);
+    # at interior frames its response at scale a / H is
+    # exp(i 2 pi nu H m) sqrt(a/H) sum_k exp(-pi^2 B ((a/H)(nu H - k) - C)^2).
+    n, worst = 6000, 0.0
+    for H in (3, 8):
+        for a in (8.0, 20.0, 64.0):
+            ap = a / H
+            h = oracle_mod.half_support(ap, B)
+            for nu in (0.01, 0.03, -0.02, C / a):
+                t = np.arange(n, dtype=np.float64)
+                w = (oracle_mod.cwth_resampled(np.cos(2 * np.pi * nu * t), [a], H)[0]
+                     + 1j * oracle_mod.cwth_resampled(np.sin(2 * np.pi * nu * t), [a], H)[0])
+                m = np.arange(h, len(w) - h)
+                g = poisson_G(ap, nu * H)
+                expect = np.exp(2j * np.pi * nu * H * m) * g
+                worst = max(worst, float(np.max(np.abs(w[m] - expect)) / max(1.0, g)))
+    assert worst < 1e-12
+
+
+def test_resampled_brute_force_tiny(oracle_mod):
+    rng = np.random.default_rng(12)
+    x = rng.standard_normal(37)
+    H, scales = 3, [2.5, 6.0]
+    got = oracle_mod.cwth_resampled(x, scales, H, truncate=False)
+    y = x[::H]
+    for s, a in enumerate(scales):
+        ap = a / H
+        for m in range(len(y)):
+            acc = 0j
+            for j in range(len(y)):
+                u = (j - m) / ap
+                psi = (math.pi * B) ** -0.5 * math.exp(-u * u / B) * complex(
+                    math.cos(2 * math.pi * C * u), math.sin(2 * math.pi * C * u))
+                acc += y[j] * psi.conjugate()
+            assert abs(got[s, m] - acc / math.sqrt(ap)) < 1e-13
