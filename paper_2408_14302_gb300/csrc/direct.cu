@@ -143,10 +143,14 @@ __global__ void bank_kernel(const double* __restrict__ scales, const int32_t* __
 //   windows: [set][tile][part]     only when p.a_shift > 0 (see below)
 //   stage s: [A tile 0 hi][A tile 0 lo][A tile 1 hi][A tile 1 lo] ... [B]
 //            (A parts only without a window; lo parts only when split)
-// Schedule step j: tap block sched[j].x; sched[j].y = columns used (low 16
-// bits, a multiple of 16) | bank part (bit 16: 0 = hi, 1 = lo).  The split
-// variant visits every block twice, once per bank part, so a stage holds one
-// bank tile; the plain variant uses the hi part only.
+// Schedule step j: tap block sched[j].x (low 16 bits; a second block in the
+// high 16 bits when bit 17 of .y is set); sched[j].y = columns used (low 16
+// bits, a multiple of 16) | bank part (bit 16: 0 = hi, 1 = lo) | pair (bit
+// 17).  A pair step carries the bank tiles of two tap blocks with the same
+// column count in one stage (eight MMAs per stage; windowed tiles only), so
+// the narrow outer blocks of the pyramid cost half the stage turns.  The
+// split variant visits every step twice, once per bank part; the plain
+// variant uses the hi part only.
 // When 64 is a multiple of the hop, the frame tile of tap block kb is the
 // tile of block 0 moved down by kb * 64 / H rows of the frame view, so one
 // window of 128 + (blocks - 1) * 64/H rows per tile, loaded once, serves
@@ -282,25 +286,35 @@ __global__ void __launch_bounds__(kDirThreads, 1)
                 }
                 const int2 step = sched_sh[j];
                 if (elect_one()) {
-                    const int kx = step.x * kBK;
+                    const int kx = (step.x & 0xFFFF) * kBK;
                     const int pieces = ((step.y & 0xFFFF) + 63) >> 6;
-                    const CUtensorMap* mb = (SPLIT && (step.y >> 16)) ? &mB_lo : &mB_hi;
+                    const int nblk = 1 + ((step.y >> 17) & 1);
+                    const CUtensorMap* mb = (SPLIT && ((step.y >> 16) & 1)) ? &mB_lo : &mB_hi;
                     uint8_t* st = stage0 + (size_t)s * stage_bytes;
-                    mbar_arrive_expect_tx(&full_bar[s], a_step + (uint32_t)pieces * 64 * kBK * 2);
-                    if (!shift) {
-                        for (int tt = 0; tt < T; ++tt) {
-                            const int m0 = (u * T + tt) * kBM;
-                            for (int q = 0; q < kBM / kAPieceRows; ++q) {
-                                tma_load_2d(st + (tt * kParts) * a_tile + q * kPiece, &mA_hi,
-                                            &full_bar[s], kx, m0 + q * kAPieceRows);
-                                if (SPLIT)
-                                    tma_load_2d(st + (tt * kParts + 1) * a_tile + q * kPiece,
-                                                &mA_lo, &full_bar[s], kx, m0 + q * kAPieceRows);
+                    mbar_arrive_expect_tx(&full_bar[s],
+                                          (uint32_t)nblk * (a_step + (uint32_t)pieces * 64 * kBK * 2));
+                    // block b of the stage: [A tiles (without a window)][bank tile]
+                    const uint32_t blk = a_step + (uint32_t)pieces * 64 * kBK * 2;
+                    for (int b = 0; b < nblk; ++b) {
+                        const int kxb = b ? (step.x >> 16) * kBK : kx;
+                        uint8_t* sb = st + b * blk;
+                        if (!shift) {
+                            for (int tt = 0; tt < T; ++tt) {
+                                const int m0 = (u * T + tt) * kBM;
+                                for (int q = 0; q < kBM / kAPieceRows; ++q) {
+                                    tma_load_2d(sb + (tt * kParts) * a_tile + q * kPiece, &mA_hi,
+                                                &full_bar[s], kxb, m0 + q * kAPieceRows);
+                                    if (SPLIT)
+                                        tma_load_2d(sb + (tt * kParts + 1) * a_tile + q * kPiece,
+                                                    &mA_lo, &full_bar[s], kxb,
+                                                    m0 + q * kAPieceRows);
+                                }
                             }
                         }
+                        for (int q = 0; q < pieces; ++q)
+                            tma_load_2d(sb + a_step + q * 64 * kBK * 2, mb, &full_bar[s], kxb,
+                                        q * 64);
                     }
-                    for (int q = 0; q < pieces; ++q)
-                        tma_load_2d(st + a_step + q * 64 * kBK * 2, mb, &full_bar[s], kx, q * 64);
                 }
                 __syncwarp();
                 ++g;
@@ -361,8 +375,15 @@ __global__ void __launch_bounds__(kDirThreads, 1)
                     // Everything but the MMAs is computed before the wait.
                     const int2 next = sched_sh[j + 1 < nsteps ? j + 1 : j];
                     const uint32_t idesc = idesc0 | ((uint32_t)(step.y & 0xFFFF) >> 3 << 17);
-                    const uint32_t a_lo =
-                        shift ? win_lo + (uint32_t)(step.x * shift) * 8u : b_lo - a_step16;
+                    const int nblk = 1 + ((step.y >> 17) & 1);
+                    // second block of a pair: its A tiles (without a window) and bank
+                    // tile follow the first block's, a_step + pieces x 8 KB further
+                    const uint32_t b_next16 =
+                        a_step16 + (uint32_t)(((step.y & 0xFFFF) + 63) >> 6) * 512u;
+                    const uint32_t a_lo0 = shift ? win_lo + (uint32_t)((step.x & 0xFFFF) * shift) * 8u
+                                                 : b_lo - a_step16;
+                    const uint32_t a_lo1 = shift ? win_lo + (uint32_t)((step.x >> 16) * shift) * 8u
+                                                 : a_lo0 + b_next16;
                     const uint32_t acc0 = j > 0 ? 1u : 0u;
                     if (!mbar_wait(&full_bar[s], sph, kWaitBudget)) {
                         fail();
@@ -370,18 +391,23 @@ __global__ void __launch_bounds__(kDirThreads, 1)
                         break;
                     }
                     tc_fence_after();
-                    for (int tt = 0; tt < T; ++tt) {
-                        const uint32_t dacc = dacc0 + (uint32_t)tt * acc_cols;
-                        const uint32_t ah = a_lo + (uint32_t)(tt * kParts) * pitch16;
-                        const uint32_t al = ah + (uint32_t)(kParts - 1) * pitch16;
+                    for (int b = 0; b < nblk; ++b) {
+                        const uint32_t a_lo = b ? a_lo1 : a_lo0;
+                        const uint32_t bb = b_lo + (uint32_t)b * b_next16;
+                        for (int tt = 0; tt < T; ++tt) {
+                            const uint32_t dacc = dacc0 + (uint32_t)tt * acc_cols;
+                            const uint32_t ah = a_lo + (uint32_t)(tt * kParts) * pitch16;
+                            const uint32_t al = ah + (uint32_t)(kParts - 1) * pitch16;
 #pragma unroll
-                        for (int k = 0; k < kBK / 16; ++k) {
-                            // 16 bf16 = 32 bytes along K -> +2 in the address field
-                            const uint64_t bd = desc_words(b_lo + 2 * k, kDescSw128Hi);
-                            mma_f16(dacc, desc_words(ah + 2 * k, kDescSw128Hi), bd, idesc,
-                                    (acc0 | k) ? 1u : 0u);
-                            if (SPLIT)
-                                mma_f16(dacc, desc_words(al + 2 * k, kDescSw128Hi), bd, idesc, 1u);
+                            for (int k = 0; k < kBK / 16; ++k) {
+                                // 16 bf16 = 32 bytes along K -> +2 in the address field
+                                const uint64_t bd = desc_words(bb + 2 * k, kDescSw128Hi);
+                                mma_f16(dacc, desc_words(ah + 2 * k, kDescSw128Hi), bd, idesc,
+                                        (acc0 | (uint32_t)b | (uint32_t)k) ? 1u : 0u);
+                                if (SPLIT)
+                                    mma_f16(dacc, desc_words(al + 2 * k, kDescSw128Hi), bd, idesc,
+                                            1u);
+                            }
                         }
                     }
                     mma_commit(&empty_bar[s]);
@@ -545,6 +571,16 @@ int direct_split_schedule(const int2* in, int n, int2* out) {
 // output offsets and the schedule: under 2 KB).
 constexpr size_t kDirSmemLimit = 227 * 1024 - 2048;
 
+// Largest bank-piece count (64 columns each) a step may have to share a
+// stage with a second step: a stage holds the A tiles (without a window)
+// and ceil(ncols / 64) pieces; a pair needs two A parts and two bank tiles.
+int direct_pair_pieces(int ncols, bool split, int unit, bool windowed) {
+    const int stage_pieces = (ncols + 63) / 64;
+    if (windowed) return stage_pieces / 2;
+    const int a_pieces = kBM * (split ? 2 : 1) * unit / 64;  // A tiles in 8 KB pieces
+    return std::max(0, (stage_pieces - a_pieces) / 2);
+}
+
 int direct_max_stages(int ncols, bool split, int win_rows, int unit, int win_sets) {
     int s = kMaxDirStages;
     while (s > 2 && direct_smem_bytes(ncols, s, split, win_rows, unit, win_sets) > kDirSmemLimit)
@@ -644,10 +680,12 @@ cudaError_t direct_launch_f32(const float* x, int64_t ld_x, const float2* bank, 
     return cudaGetLastError();
 }
 
-int direct_schedule(const int32_t* h_desc, int n, int h_group, int k_pad, int2* out) {
+int direct_schedule(const int32_t* h_desc, int n, int h_group, int k_pad, int pair_pieces,
+                    int2* out) {
     const int nkb = k_pad / kBK;
     const int center = h_group / kBK;
-    int steps = 0;
+    int blocks = 0;
+    int kbs[kMaxDirSteps], cols[kMaxDirSteps];
     for (int r = 0; r < 2 * nkb; ++r) {
         // centre, centre-1, centre+1, centre-2, centre+2, ...
         const int kb = center + ((r & 1) ? -((r + 1) >> 1) : (r >> 1));
@@ -657,7 +695,21 @@ int direct_schedule(const int32_t* h_desc, int n, int h_group, int k_pad, int2* 
         int cnt = 0;
         while (cnt < n && h_desc[cnt] >= d) ++cnt;  // supports are in descending order
         if (cnt == 0) continue;
-        out[steps++] = make_int2(kb, (2 * cnt + 15) / 16 * 16);
+        kbs[blocks] = kb;
+        cols[blocks++] = (2 * cnt + 15) / 16 * 16;
+    }
+    // Two consecutive blocks share a stage when their tiles fit in it: at
+    // most pair_pieces 64-row bank pieces each (see direct_pair_pieces).
+    int steps = 0;
+    for (int i = 0; i < blocks;) {
+        const int nc = i + 1 < blocks ? std::max(cols[i], cols[i + 1]) : cols[i];
+        if (i > 0 && i + 1 < blocks && (nc + 63) / 64 <= pair_pieces) {
+            out[steps++] = make_int2(kbs[i] | (kbs[i + 1] << 16), nc | (1 << 17));
+            i += 2;
+        } else {
+            out[steps++] = make_int2(kbs[i], cols[i]);
+            i += 1;
+        }
     }
     return steps;
 }
