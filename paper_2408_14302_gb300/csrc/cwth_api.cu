@@ -340,9 +340,8 @@ cwth_status build_direct(cwth_plan_s* p) {
             e = cudaMemcpyAsync(g.d_scales, sc.data(), sizeof(double) * sc.size(), cudaMemcpyHostToDevice, p->setup);
         std::vector<int2> sched(g.k_pad / 64), sched2(2 * (g.k_pad / 64));
         g.nsteps = cwth::direct_schedule(
-            hh.data(), g.n_scales, g.h, g.k_pad,
-            cwth::direct_pair_pieces(g.ncols, split, g.shape.unit, g.shape.win_rows > 0),
-            sched.data());
+            hh.data(), g.n_scales, g.h, g.k_pad, (g.ncols + 63) / 64,
+            cwth::direct_a_pieces(split, g.shape.unit, g.shape.win_rows > 0), sched.data());
         if (split) {
             g.nsteps = cwth::direct_split_schedule(sched.data(), g.nsteps, sched2.data());
             sched.swap(sched2);

@@ -142,9 +142,9 @@ cudaError_t direct_launch_mma(const CUtensorMap* maps, const DirLaunch& L, bool 
                               cudaStream_t st);
 // Centre-out K-block schedule of one group (supports in descending order):
 // out[i] = {tap block, columns}; returns the number of steps (<= k_pad / 64).
-int direct_schedule(const int32_t* h_desc, int n, int h_group, int k_pad, int pair_pieces,
-                    int2* out);
-int direct_pair_pieces(int ncols, bool split, int unit, bool windowed);
+int direct_schedule(const int32_t* h_desc, int n, int h_group, int k_pad, int stage_pieces,
+                    int a_pieces, int2* out);
+int direct_a_pieces(bool split, int unit, bool windowed);
 cudaError_t direct_launch_f32(const float* x, int64_t ld_x, const float2* bank, const int32_t* d_h,
                               const DirLaunch& L, cudaStream_t st);
 

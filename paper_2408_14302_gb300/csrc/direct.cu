@@ -143,13 +143,13 @@ __global__ void bank_kernel(const double* __restrict__ scales, const int32_t* __
 //   windows: [set][tile][part]     only when p.a_shift > 0 (see below)
 //   stage s: [A tile 0 hi][A tile 0 lo][A tile 1 hi][A tile 1 lo] ... [B]
 //            (A parts only without a window; lo parts only when split)
-// Schedule step j: tap block sched[j].x (low 16 bits; a second block in the
-// high 16 bits when bit 17 of .y is set); sched[j].y = columns used (low 16
-// bits, a multiple of 16) | bank part (bit 16: 0 = hi, 1 = lo) | pair (bit
-// 17).  A pair step carries the bank tiles of two tap blocks with the same
-// column count in one stage (eight MMAs per stage; windowed tiles only), so
-// the narrow outer blocks of the pyramid cost half the stage turns.  The
-// split variant visits every step twice, once per bank part; the plain
+// Schedule step j: up to four tap blocks, block b in bits 8b..8b+7 of
+// sched[j].x; sched[j].y = columns used (low 16 bits, a multiple of 16) |
+// bank part (bit 16: 0 = hi, 1 = lo) | blocks - 1 (bits 17-18).  A step of
+// several blocks carries all their tiles in one stage, each block as [A
+// tiles (without a window)][bank tile] at the same column count, so the
+// narrow outer blocks of the pyramid share stage turns (4 MMAs per block).
+// The split variant visits every step twice, once per bank part; the plain
 // variant uses the hi part only.
 // When 64 is a multiple of the hop, the frame tile of tap block kb is the
 // tile of block 0 moved down by kb * 64 / H rows of the frame view, so one
@@ -286,9 +286,8 @@ __global__ void __launch_bounds__(kDirThreads, 1)
                 }
                 const int2 step = sched_sh[j];
                 if (elect_one()) {
-                    const int kx = (step.x & 0xFFFF) * kBK;
                     const int pieces = ((step.y & 0xFFFF) + 63) >> 6;
-                    const int nblk = 1 + ((step.y >> 17) & 1);
+                    const int nblk = 1 + ((step.y >> 17) & 3);
                     const CUtensorMap* mb = (SPLIT && ((step.y >> 16) & 1)) ? &mB_lo : &mB_hi;
                     uint8_t* st = stage0 + (size_t)s * stage_bytes;
                     mbar_arrive_expect_tx(&full_bar[s],
@@ -296,7 +295,7 @@ __global__ void __launch_bounds__(kDirThreads, 1)
                     // block b of the stage: [A tiles (without a window)][bank tile]
                     const uint32_t blk = a_step + (uint32_t)pieces * 64 * kBK * 2;
                     for (int b = 0; b < nblk; ++b) {
-                        const int kxb = b ? (step.x >> 16) * kBK : kx;
+                        const int kxb = ((step.x >> (8 * b)) & 0xFF) * kBK;
                         uint8_t* sb = st + b * blk;
                         if (!shift) {
                             for (int tt = 0; tt < T; ++tt) {
@@ -375,15 +374,12 @@ __global__ void __launch_bounds__(kDirThreads, 1)
                     // Everything but the MMAs is computed before the wait.
                     const int2 next = sched_sh[j + 1 < nsteps ? j + 1 : j];
                     const uint32_t idesc = idesc0 | ((uint32_t)(step.y & 0xFFFF) >> 3 << 17);
-                    const int nblk = 1 + ((step.y >> 17) & 1);
-                    // second block of a pair: its A tiles (without a window) and bank
-                    // tile follow the first block's, a_step + pieces x 8 KB further
+                    const int nblk = 1 + ((step.y >> 17) & 3);
+                    // block b's A tiles (without a window) and bank tile follow block
+                    // b-1's, a_step + pieces x 8 KB further
                     const uint32_t b_next16 =
                         a_step16 + (uint32_t)(((step.y & 0xFFFF) + 63) >> 6) * 512u;
-                    const uint32_t a_lo0 = shift ? win_lo + (uint32_t)((step.x & 0xFFFF) * shift) * 8u
-                                                 : b_lo - a_step16;
-                    const uint32_t a_lo1 = shift ? win_lo + (uint32_t)((step.x >> 16) * shift) * 8u
-                                                 : a_lo0 + b_next16;
+                    const uint32_t kb_all = (uint32_t)step.x;
                     const uint32_t acc0 = j > 0 ? 1u : 0u;
                     if (!mbar_wait(&full_bar[s], sph, kWaitBudget)) {
                         fail();
@@ -392,7 +388,9 @@ __global__ void __launch_bounds__(kDirThreads, 1)
                     }
                     tc_fence_after();
                     for (int b = 0; b < nblk; ++b) {
-                        const uint32_t a_lo = b ? a_lo1 : a_lo0;
+                        const uint32_t kb = (kb_all >> (8 * b)) & 0xFFu;
+                        const uint32_t a_lo = shift ? win_lo + kb * (uint32_t)shift * 8u
+                                                    : b_lo - a_step16 + (uint32_t)b * b_next16;
                         const uint32_t bb = b_lo + (uint32_t)b * b_next16;
                         for (int tt = 0; tt < T; ++tt) {
                             const uint32_t dacc = dacc0 + (uint32_t)tt * acc_cols;
@@ -571,14 +569,9 @@ int direct_split_schedule(const int2* in, int n, int2* out) {
 // output offsets and the schedule: under 2 KB).
 constexpr size_t kDirSmemLimit = 227 * 1024 - 2048;
 
-// Largest bank-piece count (64 columns each) a step may have to share a
-// stage with a second step: a stage holds the A tiles (without a window)
-// and ceil(ncols / 64) pieces; a pair needs two A parts and two bank tiles.
-int direct_pair_pieces(int ncols, bool split, int unit, bool windowed) {
-    const int stage_pieces = (ncols + 63) / 64;
-    if (windowed) return stage_pieces / 2;
-    const int a_pieces = kBM * (split ? 2 : 1) * unit / 64;  // A tiles in 8 KB pieces
-    return std::max(0, (stage_pieces - a_pieces) / 2);
+// A stage's A tiles (frames; none with a frame window) in 8 KB pieces.
+int direct_a_pieces(bool split, int unit, bool windowed) {
+    return windowed ? 0 : kBM * (split ? 2 : 1) * unit / 64;
 }
 
 int direct_max_stages(int ncols, bool split, int win_rows, int unit, int win_sets) {
@@ -680,8 +673,8 @@ cudaError_t direct_launch_f32(const float* x, int64_t ld_x, const float2* bank, 
     return cudaGetLastError();
 }
 
-int direct_schedule(const int32_t* h_desc, int n, int h_group, int k_pad, int pair_pieces,
-                    int2* out) {
+int direct_schedule(const int32_t* h_desc, int n, int h_group, int k_pad, int stage_pieces,
+                    int a_pieces, int2* out) {
     const int nkb = k_pad / kBK;
     const int center = h_group / kBK;
     int blocks = 0;
@@ -698,18 +691,23 @@ int direct_schedule(const int32_t* h_desc, int n, int h_group, int k_pad, int pa
         kbs[blocks] = kb;
         cols[blocks++] = (2 * cnt + 15) / 16 * 16;
     }
-    // Two consecutive blocks share a stage when their tiles fit in it: at
-    // most pair_pieces 64-row bank pieces each (see direct_pair_pieces).
+    // Consecutive blocks (after the centre block, which initialises the
+    // accumulators alone) share a stage while their tiles fit: g blocks of
+    // nc columns need g (a_pieces + ceil(nc / 64)) of the stage's
+    // a_pieces + stage_pieces 8 KB pieces.
     int steps = 0;
     for (int i = 0; i < blocks;) {
-        const int nc = i + 1 < blocks ? std::max(cols[i], cols[i + 1]) : cols[i];
-        if (i > 0 && i + 1 < blocks && (nc + 63) / 64 <= pair_pieces) {
-            out[steps++] = make_int2(kbs[i] | (kbs[i + 1] << 16), nc | (1 << 17));
-            i += 2;
-        } else {
-            out[steps++] = make_int2(kbs[i], cols[i]);
-            i += 1;
+        int g = 1, nc = cols[i];
+        while (i > 0 && g < 4 && i + g < blocks) {
+            const int nc2 = std::max(nc, cols[i + g]);
+            if ((g + 1) * (a_pieces + (nc2 + 63) / 64) > a_pieces + stage_pieces) break;
+            nc = nc2;
+            ++g;
         }
+        int x = 0;
+        for (int b = 0; b < g; ++b) x |= kbs[i + b] << (8 * b);
+        out[steps++] = make_int2(x, nc | ((g - 1) << 17));
+        i += g;
     }
     return steps;
 }

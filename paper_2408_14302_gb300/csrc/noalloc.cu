@@ -224,9 +224,10 @@ cwth_status cwth_execute_direct_noalloc(const cwth_morlet* w, const double* scal
         const int n = std::min(S, first + kScalesPerGroup) - first;
         int2 one[kMaxTaps / 64];
         const cwth::DirShape sh = cwth::direct_shape(ncols[g], split, hop, kpad[g]);
-        nsteps[g] = cwth::direct_schedule(
-            h_sorted + first, n, h_sorted[first], kpad[g],
-            cwth::direct_pair_pieces(ncols[g], split, sh.unit, sh.win_rows > 0), one);
+        nsteps[g] = cwth::direct_schedule(h_sorted + first, n, h_sorted[first], kpad[g],
+                                          (ncols[g] + 63) / 64,
+                                          cwth::direct_a_pieces(split, sh.unit, sh.win_rows > 0),
+                                          one);
         if (split)
             nsteps[g] = cwth::direct_split_schedule(one, nsteps[g], sched[g]);
         else
