@@ -555,7 +555,8 @@ cwth_status launch_direct(cwth_plan_s* p, const float* d_x, int64_t ld_x, const 
         L.sched = g.d_sched;
         L.nsteps = g.nsteps;
         L.win_rows = g.shape.win_rows;
-        L.a_shift = g.shape.win_rows ? 64 / (int)hop : 0;
+        L.a_shift = g.shape.win_rows ? cwth::direct_window_shift((int)hop) : 0;
+        L.a_phases = g.shape.win_rows ? g.shape.phases : 1;
         L.unit = g.shape.unit;
         L.win_sets = g.shape.win_sets;
         L.acc_sets = g.shape.acc_sets;

@@ -94,7 +94,9 @@ struct DirLaunch {
     int* status;            // device status word (CWTH_ERR_TIMEOUT on a bounded-wait expiry)
     const int2* sched;      // per K step: {tap block, columns used | bank part << 16}
     int32_t nsteps;
-    int32_t a_shift;        // frame-view rows per tap block (64 / hop) when one window serves all blocks, else 0
+    int32_t a_shift;        // frame-view rows per tap block (64 / hop; per a_phases blocks
+                            // when a_phases > 1) when windows serve all blocks, else 0
+    int32_t a_phases;       // frame windows per tile: hop / 64 for hops 128..256, else 1
     int32_t win_rows;       // rows of that window (a multiple of 32)
     int32_t unit;           // 128-frame tiles sharing each bank tile (1 or 2)
     int32_t win_sets;       // frame-window sets (2: the next unit's windows load early)
@@ -103,7 +105,7 @@ struct DirLaunch {
 
 // Launch shape of one direct-path group.
 struct DirShape {
-    int32_t unit = 0, acc_sets = 0, win_sets = 0, win_rows = 0, stages = 0;
+    int32_t unit = 0, acc_sets = 0, win_sets = 0, win_rows = 0, stages = 0, phases = 1;
     uint32_t tmem_cols = 0;
 };
 
@@ -118,11 +120,13 @@ cudaError_t spectral_launch(const SpecLaunch& L, int threads, int n_seg, int bat
                             size_t smem, cudaStream_t st);
 
 size_t direct_smem_bytes(int ncols, int stages, bool split, int win_rows, int unit,
-                         int win_sets);
-int direct_max_stages(int ncols, bool split, int win_rows, int unit, int win_sets);
+                         int win_sets, int phases);
+int direct_max_stages(int ncols, bool split, int win_rows, int unit, int win_sets, int phases);
 DirShape direct_shape(int ncols, bool split, int hop, int k_pad);
 // Rows of the frame window for hops dividing 64 (0: per-step frame tiles).
 int direct_window_rows(int hop, int k_pad);
+int direct_window_phases(int hop);
+int direct_window_shift(int hop);
 // The split variant's schedule: every step of `in` twice, hi part then lo
 // part (bit 16 of .y); returns 2 n.
 int direct_split_schedule(const int2* in, int n, int2* out);

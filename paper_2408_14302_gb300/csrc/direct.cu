@@ -42,6 +42,7 @@ constexpr int kBK = 64;              // taps per stage (128 bytes of bf16)
 constexpr int kDirThreads = 192;
 constexpr int kAPieceRows = 32;      // frame-map box height (rows per TMA copy)
 constexpr int kMaxGroupScales = 128; // scales per GEMM group (256 columns)
+constexpr int kMaxPhases = 4;        // frame windows per tile (hops up to 256)
 constexpr long long kWaitBudget = 4000000000LL;  // ~2 s of SM clock
 
 // Square root by the hardware approximation (relative error about 2^-22),
@@ -140,7 +141,7 @@ __global__ void bank_kernel(const double* __restrict__ scales, const int32_t* __
 // overlap this unit's MMAs / epilogue).
 //
 // Shared-memory layout (1024-byte aligned pieces):
-//   windows: [set][tile][part]     only when p.a_shift > 0 (see below)
+//   windows: [set][tile][part][phase]   only when p.a_shift > 0 (see below)
 //   stage s: [A tile 0 hi][A tile 0 lo][A tile 1 hi][A tile 1 lo] ... [B]
 //            (A parts only without a window; lo parts only when split)
 // Schedule step j: up to four tap blocks, block b in bits 8b..8b+7 of
@@ -154,7 +155,11 @@ __global__ void bank_kernel(const double* __restrict__ scales, const int32_t* __
 // When 64 is a multiple of the hop, the frame tile of tap block kb is the
 // tile of block 0 moved down by kb * 64 / H rows of the frame view, so one
 // window of 128 + (blocks - 1) * 64/H rows per tile, loaded once, serves
-// every K step through descriptors that start kb * 64/H rows into it.
+// every K step through descriptors that start kb * 64/H rows into it.  When
+// the hop is r = H / 64 times 64 (r <= 4), block kb = r j + ph reads taps
+// 64 ph .. 64 ph + 63 of frame rows moved down by j: r windows ("phases",
+// loaded at tap offset 64 ph) of 128 + ceil(blocks / r) - 1 rows serve all
+// blocks the same way.
 template <bool SPLIT>
 __global__ void __launch_bounds__(kDirThreads, 1)
     direct_mma_kernel(const __grid_constant__ CUtensorMap mA_hi,
@@ -176,12 +181,13 @@ __global__ void __launch_bounds__(kDirThreads, 1)
     const int N = p.ncols;
     const int T = p.unit;
     const int stages = p.stages;
-    const int shift = p.a_shift;
+    const int shift = p.a_shift;       // window rows per block (per r blocks with phases)
+    const int phases = p.a_phases, lgph = __ffs(phases) - 1;
     const int wsets = p.win_sets, asets = p.acc_sets;
     constexpr uint32_t kPiece = kAPieceRows * kBK * 2;  // one frame-map box
     const uint32_t win_bytes = (uint32_t)p.win_rows * kBK * 2;
     const uint32_t win_span = (win_bytes + 1023) & ~1023u;
-    const uint32_t win_region = shift ? win_span * kParts * T * wsets : 0u;
+    const uint32_t win_region = shift ? win_span * kParts * T * wsets * phases : 0u;
     const uint32_t a_tile = kBM * kBK * 2;
     const uint32_t a_step = shift ? 0u : a_tile * kParts * T;
     const uint32_t b_bytes = (uint32_t)((N + 63) / 64 * 64) * kBK * 2;
@@ -229,8 +235,8 @@ __global__ void __launch_bounds__(kDirThreads, 1)
     tc_fence_after();
     const uint32_t tmem = tmem_base_sh;
 
-    auto win_ptr = [&](int set, int tile, int part) {
-        return smem + ((size_t)(set * T + tile) * kParts + part) * win_span;
+    auto win_ptr = [&](int set, int tile, int part, int ph) {
+        return smem + (((size_t)(set * T + tile) * kParts + part) * phases + ph) * win_span;
     };
     auto aborted = [&]() { return *(volatile int*)&abort_sh != 0; };
     auto fail = [&]() { atomicExch(&abort_sh, 1); };
@@ -254,16 +260,17 @@ __global__ void __launch_bounds__(kDirThreads, 1)
                     break;
                 }
                 if (elect_one()) {
-                    mbar_arrive_expect_tx(&win_full[ws], win_bytes * kParts * T);
+                    mbar_arrive_expect_tx(&win_full[ws], win_bytes * kParts * T * phases);
                     for (int tt = 0; tt < T; ++tt) {
                         const int m0 = (u * T + tt) * kBM;
-                        for (int j = 0; j < p.win_rows / kAPieceRows; ++j) {
-                            tma_load_2d(win_ptr(ws, tt, 0) + j * kPiece, &mA_hi, &win_full[ws], 0,
-                                        m0 + j * kAPieceRows);
-                            if (SPLIT)
-                                tma_load_2d(win_ptr(ws, tt, 1) + j * kPiece, &mA_lo, &win_full[ws],
-                                            0, m0 + j * kAPieceRows);
-                        }
+                        for (int ph = 0; ph < phases; ++ph)
+                            for (int j = 0; j < p.win_rows / kAPieceRows; ++j) {
+                                tma_load_2d(win_ptr(ws, tt, 0, ph) + j * kPiece, &mA_hi,
+                                            &win_full[ws], ph * kBK, m0 + j * kAPieceRows);
+                                if (SPLIT)
+                                    tma_load_2d(win_ptr(ws, tt, 1, ph) + j * kPiece, &mA_lo,
+                                                &win_full[ws], ph * kBK, m0 + j * kAPieceRows);
+                            }
                     }
                 }
                 __syncwarp();
@@ -353,7 +360,8 @@ __global__ void __launch_bounds__(kDirThreads, 1)
             const uint32_t stage16 = stage_bytes >> 4;
             const uint32_t a_step16 = a_step >> 4;
             // distance between the A operands of consecutive (tile, part) pairs
-            const uint32_t pitch16 = (shift ? win_span : a_tile) >> 4;
+            const uint32_t pitch16 = (shift ? win_span * phases : a_tile) >> 4;
+            const uint32_t span16 = win_span >> 4;
             const uint32_t idesc0 = idesc_bf16_f32(kBM, 0);
             uint32_t b_lo = b_lo0;
             for (int u = blockIdx.x; u < nunits && !aborted(); u += gridDim.x, ++i) {
@@ -367,7 +375,7 @@ __global__ void __launch_bounds__(kDirThreads, 1)
                 }
                 tc_fence_after();
                 const uint32_t dacc0 = tmem + (uint32_t)(as * T) * acc_cols;
-                const uint32_t win_lo = desc_sw128_lo(smem_u32(win_ptr(ws, 0, 0)));
+                const uint32_t win_lo = desc_sw128_lo(smem_u32(win_ptr(ws, 0, 0, 0)));
                 bool ok = true;
                 int2 step = sched_sh[0];
                 for (int j = 0; j < nsteps; ++j) {
@@ -389,7 +397,8 @@ __global__ void __launch_bounds__(kDirThreads, 1)
                     tc_fence_after();
                     for (int b = 0; b < nblk; ++b) {
                         const uint32_t kb = (kb_all >> (8 * b)) & 0xFFu;
-                        const uint32_t a_lo = shift ? win_lo + kb * (uint32_t)shift * 8u
+                        const uint32_t a_lo = shift ? win_lo + (kb & (uint32_t)(phases - 1)) * span16 +
+                                                          (kb >> lgph) * (uint32_t)shift * 8u
                                                     : b_lo - a_step16 + (uint32_t)b * b_next16;
                         const uint32_t bb = b_lo + (uint32_t)b * b_next16;
                         for (int tt = 0; tt < T; ++tt) {
@@ -539,20 +548,38 @@ __global__ void __launch_bounds__(128) direct_f32_kernel(const float* __restrict
 constexpr size_t kDirSmemMin = 120 * 1024;
 
 size_t direct_smem_bytes(int ncols, int stages, bool split, int win_rows, int unit,
-                         int win_sets) {
+                         int win_sets, int phases) {
     const size_t parts = split ? 2 : 1;
     const size_t brows = (size_t)(ncols + 63) / 64 * 64;
     const size_t a = win_rows > 0 ? 0 : (size_t)kBM * kBK * 2 * parts * unit;
     const size_t stage = a + brows * kBK * 2;
     const size_t win_span = ((size_t)win_rows * kBK * 2 + 1023) / 1024 * 1024;
-    const size_t bytes = (win_rows > 0 ? win_span * parts * unit * win_sets : 0) +
+    const size_t bytes = (win_rows > 0 ? win_span * parts * unit * win_sets * phases : 0) +
                          stage * stages + 1024;
     return bytes < kDirSmemMin ? kDirSmemMin : bytes;
 }
 
+// Frame windows (see direct_mma_kernel): hops dividing 64 use one window
+// moved 64/H rows per tap block; hops of r * 64 (r <= kMaxPhases) use r
+// phase windows moved one row per r blocks; other hops load A per stage.
+int direct_window_phases(int hop) {
+    return (hop > kBK && hop % kBK == 0 && hop / kBK <= kMaxPhases) ? hop / kBK : 1;
+}
+
+int direct_window_shift(int hop) { return hop > 0 && kBK % hop == 0 ? kBK / hop : 1; }
+
 int direct_window_rows(int hop, int k_pad) {
-    if (hop <= 0 || kBK % hop != 0) return 0;
-    const int rows = kBM + (k_pad / kBK - 1) * (kBK / hop);
+    if (hop <= 0) return 0;
+    const int nkb = k_pad / kBK;
+    int rows;
+    if (kBK % hop == 0) {
+        rows = kBM + (nkb - 1) * (kBK / hop);
+    } else if (direct_window_phases(hop) > 1) {
+        const int r = direct_window_phases(hop);
+        rows = kBM + (nkb + r - 1) / r - 1;
+    } else {
+        return 0;
+    }
     return (rows + kAPieceRows - 1) / kAPieceRows * kAPieceRows;
 }
 
@@ -574,11 +601,13 @@ int direct_a_pieces(bool split, int unit, bool windowed) {
     return windowed ? 0 : kBM * (split ? 2 : 1) * unit / 64;
 }
 
-int direct_max_stages(int ncols, bool split, int win_rows, int unit, int win_sets) {
+int direct_max_stages(int ncols, bool split, int win_rows, int unit, int win_sets, int phases) {
     int s = kMaxDirStages;
-    while (s > 2 && direct_smem_bytes(ncols, s, split, win_rows, unit, win_sets) > kDirSmemLimit)
+    while (s > 2 &&
+           direct_smem_bytes(ncols, s, split, win_rows, unit, win_sets, phases) > kDirSmemLimit)
         --s;
-    return direct_smem_bytes(ncols, s, split, win_rows, unit, win_sets) <= kDirSmemLimit ? s : 0;
+    return direct_smem_bytes(ncols, s, split, win_rows, unit, win_sets, phases) <= kDirSmemLimit ? s
+                                                                                                : 0;
 }
 
 // Launch shape of a group: frame tiles per unit, window and accumulator
@@ -596,13 +625,15 @@ DirShape direct_shape(int ncols, bool split, int hop, int k_pad) {
         if (asets < 1 || (unit == 2 && asets < 2)) continue;
         for (int wrows : {win, 0}) {
             if (wrows == 0 && win > 0 && best.stages > 0) continue;
+            const int ph = wrows ? direct_window_phases(hop) : 1;
             for (int wsets = (wrows ? 2 : 1); wsets >= 1; --wsets) {
-                const int st = direct_max_stages(ncols, split, wrows, unit, wsets);
+                const int st = direct_max_stages(ncols, split, wrows, unit, wsets, ph);
                 if (st >= (wsets == 2 ? 3 : 2)) {
                     best.unit = unit;
                     best.acc_sets = asets;
                     best.win_sets = wsets;
                     best.win_rows = wrows;
+                    best.phases = ph;
                     best.stages = st;
                     best.tmem_cols = asets * unit * cpow;
                     return best;
@@ -654,7 +685,7 @@ cudaError_t direct_launch_mma(const CUtensorMap* maps, const DirLaunch& L, bool 
     const int64_t units = ((L.total_rows + kBM - 1) / kBM + L.unit - 1) / L.unit;
     const int64_t tiles = std::min<int64_t>(units, sms);
     const size_t smem = direct_smem_bytes(L.ncols, L.stages, split, L.a_shift ? L.win_rows : 0,
-                                          L.unit, L.win_sets);
+                                          L.unit, L.win_sets, L.a_phases);
     if (split)
         direct_mma_kernel<true><<<(unsigned)tiles, kDirThreads, smem, st>>>(maps[0], maps[1],
                                                                            maps[2], maps[3], L);

@@ -283,7 +283,8 @@ cwth_status cwth_execute_direct_noalloc(const cwth_morlet* w, const double* scal
         const cwth::DirShape sh = cwth::direct_shape(ncols[g], split, hop, kpad[g]);
         L.stages = sh.stages;
         L.win_rows = sh.win_rows;
-        L.a_shift = sh.win_rows ? 64 / hop : 0;
+        L.a_shift = sh.win_rows ? cwth::direct_window_shift(hop) : 0;
+        L.a_phases = sh.win_rows ? sh.phases : 1;
         L.unit = sh.unit;
         L.win_sets = sh.win_sets;
         L.acc_sets = sh.acc_sets;
