@@ -395,7 +395,10 @@ __global__ void __launch_bounds__(kDirThreads, 1)
                         break;
                     }
                     tc_fence_after();
-                    for (int b = 0; b < nblk; ++b) {
+                    // unrolled: constant shifts, no loop bookkeeping between MMAs
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        if (b >= nblk) break;
                         const uint32_t kb = (kb_all >> (8 * b)) & 0xFFu;
                         const uint32_t a_lo = shift ? win_lo + (kb & (uint32_t)(phases - 1)) * span16 +
                                                           (kb >> lgph) * (uint32_t)shift * 8u
