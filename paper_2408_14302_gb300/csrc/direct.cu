@@ -12,11 +12,11 @@
 // scales whose support reaches it (a pyramid of MMAs instead of a padded
 // rectangle).
 //
-// tcgen05 kernel (bf16 operands, f32 accumulation in tensor memory), one CTA
-// per 128-frame tile of one group, 6 warps:
-//   warp 0      TMA producer (A and B tiles, 64 taps per stage, 128B swizzle)
-//   warp 1      TMEM allocation + single-thread MMA issue (M=128, N<=256, K=16)
-//   warps 2..5  epilogue: tcgen05.ld, |re + i im|, coalesced stores along k
+// tcgen05 kernel (bf16 operands, f32 accumulation in tensor memory): a
+// persistent CTA per SM walks 128-frame tiles of one group with 10 warps:
+//   warp 0      TMA producer (frame windows or A tiles, bank tiles, 128B swizzle)
+//   warp 1      TMEM allocation + elected-lane MMA issue (M=128, N<=256, K=16)
+//   warps 2..9  epilogue: tcgen05.ld, |re + i im|, coalesced stores along k
 // The split variant ("bf16x2") represents x = x_hi + x_lo and g = g_hi + g_lo
 // (each pair within 2^-18 of its value) and accumulates all four products
 // into the same tensor-memory accumulator, so every tap product is within
@@ -39,7 +39,8 @@ using namespace sm100;
 
 constexpr int kBM = 128;             // frames per tile
 constexpr int kBK = 64;              // taps per stage (128 bytes of bf16)
-constexpr int kDirThreads = 192;
+constexpr int kDirThreads = 320;
+constexpr int kEpiWarps = 8;         // two per tensor-memory lane quarter
 constexpr int kAPieceRows = 32;      // frame-map box height (rows per TMA copy)
 constexpr int kMaxGroupScales = 128; // scales per GEMM group (256 columns)
 constexpr int kMaxPhases = 4;        // frame windows per tile (hops up to 256)
@@ -213,7 +214,7 @@ __global__ void __launch_bounds__(kDirThreads, 1)
             mbar_init(&win_full[b], 1);
             mbar_init(&win_empty[b], 1);
             mbar_init(&acc_full[b], 1);
-            mbar_init(&acc_empty[b], 4);  // one arrival per epilogue warp
+            mbar_init(&acc_empty[b], kEpiWarps);  // one arrival per epilogue warp
         }
         // A CTA of a launch that already timed out, or handed a schedule
         // longer than its table, does no work.
@@ -445,8 +446,10 @@ __global__ void __launch_bounds__(kDirThreads, 1)
         }
         __syncwarp();
     } else {
-        // Epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (one frame each).
+        // Epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (one frame each);
+        // the two warps of a lane quarter take alternate 64-column chunks.
         const int quarter = warp & 3;
+        const int half = (warp - 2) >> 2;
         int as = 0;
         uint32_t aph = 0;
         for (int u = blockIdx.x; u < nunits && !aborted(); u += gridDim.x) {
@@ -469,7 +472,7 @@ __global__ void __launch_bounds__(kDirThreads, 1)
                                        ((uint32_t)(quarter * 32) << 16);
                 float* obase = p.out + (valid ? (b * p.S_total) * p.frames_max + k : 0);
                 // 64 columns (32 scales) per wait: four loads in flight at a time.
-                for (int c0 = 0; c0 < N; c0 += 64) {
+                for (int c0 = half * 64; c0 < N; c0 += 128) {
                     uint32_t r[64];
 #pragma unroll
                     for (int q = 0; q < 4; ++q)
