@@ -190,7 +190,7 @@ def algorithmic_flops_per_clip(scales, hop, n=N_SAMPLES):
     a_max = float(np.max(scales))
     h = math.ceil(a_max * math.sqrt(B_MORLET * math.log(1e10)))
     M = hop * smooth_at_least(-(-(n + h) // hop))
-    delta = math.sqrt(math.log(1e9) / (math.pi ** 2 * B_MORLET))
+    delta = math.sqrt(math.log(1e7) / (math.pi ** 2 * B_MORLET))  # the plan's band threshold
     band = sum(math.ceil(M * (C_MORLET + delta) / a) - math.floor(M * (C_MORLET - delta) / a) + 1
                for a in scales)
     P = M // hop
