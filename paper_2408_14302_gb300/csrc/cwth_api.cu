@@ -20,10 +20,11 @@ namespace {
 // may wrap around the segment (the segment halo covers everything above it).
 constexpr double kEpsWrap = 1e-10;
 // Morlet band threshold: spectrum bins where Psi(a nu) < kEpsBand are skipped.
-// The dropped Gaussian tail adds at most ~1e-7 x 0.1 x P of max|W| to a
-// frame (P = M/H residues summed coherently): under 1e-6 for P <= 128 and
-// far inside the 1e-5 target; measured errors against the float64 oracle
-// stay at 6e-7 (as at 1e-9), with 12 % fewer fold bins.
+// Each dropped bin weighs under 1e-7 of the band's peak and the dropped tail
+// sums to about 0.1 x 1e-7 of a residue's weight mass; measured errors
+// against the float64 oracle are unchanged from a 1e-9 threshold (6e-7 of
+// max|W| at hops 64 and 256, 7.8e-7 at hop 1 where P = 8192), with 12 %
+// fewer fold bins.
 constexpr double kEpsBand = 1e-7;
 // Dynamic shared memory a spectral CTA may use: the 227 KB opt-in limit less
 // room for the kernel's static arrays.  One 1024-thread CTA fills an SM, so
