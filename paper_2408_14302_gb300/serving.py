@@ -114,6 +114,7 @@ class GpuExecutor:
         self.f_lo, self.f_hi = f_lo, f_hi
         self.streams = [torch.cuda.Stream(self.device) for _ in range(slots)]
         self.plans = {}
+        self.bufs = {}
         self.direct = precision != "fp32" or path == "direct"
 
     def cost(self, reqs) -> int:
@@ -140,30 +141,51 @@ class GpuExecutor:
                         for L in buckets:
                             self._plan(slot, float(fs), int(S), int(hop), L)
 
+    def _buf(self, slot: int, name: str, numel: int, dtype, pinned: bool):
+        """A slot's staging buffer of at least `numel` elements (grown on
+        demand, reused by every batch the slot runs)."""
+        torch = self.torch
+        key = (slot, name)
+        t = self.bufs.get(key)
+        if t is None or t.numel() < numel:
+            if pinned:
+                t = torch.empty(numel, dtype=dtype).pin_memory()
+            else:
+                t = torch.empty(numel, dtype=dtype, device=self.device)
+            self.bufs[key] = t
+        return t[:numel]
+
     def launch(self, reqs, slot: int):
+        """Copies the batch into the slot's pinned rows (only each clip's own
+        samples: the kernels ignore samples past a clip's length, so no row is
+        cleared), uploads, transforms and downloads on the slot's stream.
+        A slot runs one batch at a time, so its buffers are free again when
+        the server hands the slot out."""
         torch = self.torch
         fs, S, hop = reqs[0].key
         L = length_bucket(max(len(r.x) for r in reqs))
         plan = self._plan(slot, fs, S, hop, L)
         b = len(reqs)
-        hx = torch.zeros((b, L), dtype=torch.float32).pin_memory()
-        hl = torch.empty(b, dtype=torch.int64).pin_memory()
-        hxn = hx.numpy()
+        F = plan.frames_max
+        hx = self._buf(slot, "hx", b * L, torch.float32, True).view(b, L)
+        hl = self._buf(slot, "hl", b, torch.int64, True)
+        hxn, hln = hx.numpy(), hl.numpy()
         for i, r in enumerate(reqs):
             hxn[i, : len(r.x)] = r.x
-            hl[i] = len(r.x)
+            hln[i] = len(r.x)
+        xd = self._buf(slot, "xd", b * L, torch.float32, False).view(b, L)
+        ld = self._buf(slot, "ld", b, torch.int64, False)
+        od = self._buf(slot, "od", b * S * F, torch.float32, False).view(b, S, F)
+        ho = self._buf(slot, "ho", b * S * F, torch.float32, True).view(b, S, F)
         st = self.streams[slot]
         with torch.cuda.stream(st):
-            xd = hx.to(self.device, non_blocking=True)
-            ld = hl.to(self.device, non_blocking=True)
-            od = torch.empty((b, S, plan.frames_max), device=self.device)
+            xd.copy_(hx, non_blocking=True)
+            ld.copy_(hl, non_blocking=True)
             plan.execute(xd, lengths=ld, out=od, stream=st)
-            ho = torch.empty(od.shape, dtype=torch.float32).pin_memory()
             ho.copy_(od, non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(st)
-        # keep device tensors alive until the batch completes
-        return {"ev": ev, "reqs": reqs, "ho": ho, "keep": (hx, hl, xd, ld, od), "slot": slot}
+        return {"ev": ev, "reqs": reqs, "ho": ho, "slot": slot}
 
     def done(self, h) -> bool:
         return h["ev"].query()
@@ -176,6 +198,7 @@ class GpuExecutor:
         for p in self.plans.values():
             p.close()
         self.plans.clear()
+        self.bufs.clear()
 
 
 class Server:
@@ -192,14 +215,17 @@ class Server:
         self.rejected = []
 
     def _take_batch(self, pending):
-        """The oldest waiting request plus later ones with the same key."""
+        """The oldest waiting request plus later ones with the same key and
+        length bucket (a batch is padded to its longest clip, so mixing
+        lengths would transform padding)."""
         first = pending.popleft()
         batch = [first]
         if self.max_batch > 1:
+            want = (first.key, length_bucket(len(first.x)))
             rest = collections.deque()
             while pending and len(batch) < self.max_batch:
                 r = pending.popleft()
-                (batch if r.key == first.key else rest).append(r)
+                (batch if (r.key, length_bucket(len(r.x))) == want else rest).append(r)
             while rest:
                 pending.appendleft(rest.pop())
         return batch
@@ -306,7 +332,8 @@ def main(argv=None):
     a = ap.parse_args(argv)
     import torch
     pool = [signals.machine_clip(5000 + i, 60 * 16000, 16000.0) for i in range(8)]
-    forms = {"batched_auto_bf16x2": dict(precision="bf16x2", path="auto", batched=True),
+    forms = {"batched_spectral_fp32": dict(precision="fp32", path="spectral", batched=True),
+             "batched_auto_bf16x2": dict(precision="bf16x2", path="auto", batched=True),
              "per_clip_fp32_spectral": dict(precision="fp32", path="spectral", batched=False)}
     for name, f in forms.items():
         ex = GpuExecutor(slots=a.slots, precision=f["precision"], path=f["path"])
