@@ -244,10 +244,14 @@ __device__ __forceinline__ float fast_exp2(float x) {
 // take g_j this way, re-anchored from the exact argument every 8 bins (at
 // most ~3.5e-6 relative drift at a chunk's end; D <= 0.35 there, so the
 // ratios stay in range); shorter runs and the remainder use one
-// ex2.approx (~2^-22 relative) per bin.
-__device__ __forceinline__ float2 fold_run(const float2* __restrict__ X, int q0, int dq, int n,
+// ex2.approx (~2^-22 relative) per bin.  LGP > 0 fixes the stride at
+// compile time (dq = SIGN * 2^LGP), so the eight loads of a chunk address X
+// with immediate offsets; LGP = 0 takes dq as passed.
+template <int LGP, int SIGN>
+__device__ __forceinline__ float2 fold_run(const float2* __restrict__ X, int q0, int dq_rt, int n,
                                            float qf, float pf, const SpecScale& sc, float cneg,
                                            float kexp) {
+    const int dq = LGP ? SIGN * (1 << LGP) : dq_rt;
     float2 acc = make_float2(0.f, 0.f);
     const float2* xp = X + q0;
     int j = 0;
@@ -284,10 +288,13 @@ __device__ __forceinline__ float2 fold_run(const float2* __restrict__ X, int q0,
 // Z[r] = gscale * sum over the unwrapped band [q_lo, q_hi] of the bins
 // q_u = r (mod P) of X[q_u mod M] * Psi-weight; bins above M/2 are read as
 // conj(X[M - q]).  The walk is split into runs that stay on one side of M/2,
-// so the inner loop is branch-free.
+// so the inner loop is branch-free.  LGP > 0: P = 2^LGP at compile time.
+template <int LGP>
 __device__ __forceinline__ float2 fold_residue(const float2* __restrict__ X, const SpecScale& sc,
-                                               int r, int M, int Mh, int P, int lgP, float cneg,
-                                               float kexp) {
+                                               int r, int M, int Mh, int P_rt, int lgP_rt,
+                                               float cneg, float kexp) {
+    const int P = LGP ? (1 << LGP) : P_rt;
+    const int lgP = LGP ? LGP : lgP_rt;
     int qu = sc.q_lo + ((r - sc.q_lo) & (P - 1));
     int left = qu <= sc.q_hi ? ((sc.q_hi - qu) >> lgP) + 1 : 0;
     const float pf = (float)P;
@@ -297,12 +304,12 @@ __device__ __forceinline__ float2 fold_residue(const float2* __restrict__ X, con
         int n;
         if (q <= Mh) {
             n = min(left, ((Mh - q) >> lgP) + 1);
-            const float2 t = fold_run(X, q, P, n, (float)qu, pf, sc, cneg, kexp);
+            const float2 t = fold_run<LGP, 1>(X, q, P, n, (float)qu, pf, sc, cneg, kexp);
             ad.x += t.x;
             ad.y += t.y;
         } else {
             n = min(left, ((M - 1 - q) >> lgP) + 1);
-            const float2 t = fold_run(X, M - q, -P, n, (float)qu, pf, sc, cneg, kexp);
+            const float2 t = fold_run<LGP, -1>(X, M - q, -P, n, (float)qu, pf, sc, cneg, kexp);
             am.x += t.x;
             am.y += t.y;
         }
@@ -310,6 +317,31 @@ __device__ __forceinline__ float2 fold_residue(const float2* __restrict__ X, con
         left -= n;
     }
     return make_float2(sc.gscale * (ad.x + am.x), sc.gscale * (ad.y - am.y));
+}
+
+// a3 for one chunk of scales: band multiply + hop fold.  Lane = residue r;
+// one item = 32 consecutive residues of one scale; the loop walks the
+// unwrapped band.  Items are ordered by decreasing band width (scales
+// ascend); they are dealt to warps in a snake order to balance the work.
+template <int LGP>
+__device__ __forceinline__ void fold_items(const SpecLaunch& p, const float2* __restrict__ X,
+                                           float2* __restrict__ Z, int c0, int nc, int M, int P,
+                                           int lgP) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nwarps = blockDim.x >> 5;
+    const int strips = (P + 31) >> 5;
+    const int nitems = nc * strips;
+    const int lgS = __ffs(strips) - 1;
+    const float cneg = -p.center;
+    for (int round = 0;; ++round) {
+        const int it = round * nwarps + ((round & 1) ? nwarps - 1 - warp : warp);
+        if (it >= nitems) break;
+        const int c = it >> lgS;
+        const int r = ((it - (c << lgS)) << 5) + lane;
+        if (r >= P) continue;
+        const SpecScale sc = p.sc[c0 + c];
+        Z[c * P + r] = fold_residue<LGP>(X, sc, r, M, M >> 1, P, lgP, cneg, p.kexp);
+    }
 }
 
 template <int THREADS>
@@ -366,29 +398,21 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) spectral_segment_kern
     }
     __syncthreads();
 
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nwarps = blockDim.x >> 5;
-    const int strips = (P + 31) >> 5;
-
+    const int lgP = __ffs(P) - 1;
     for (int c0 = sp_begin; c0 < sp_end; c0 += p.nconc) {
         const int nc = min(p.nconc, sp_end - c0);
 
-        // a3: band multiply + hop fold.  Lane = residue r; one item = 32
-        // consecutive residues of one scale; the loop walks the unwrapped band.
-        // Items are ordered by decreasing band width (scales ascend); they
-        // are dealt to warps in a snake order to balance the work.
-        const int nitems = nc * strips;
-        const int lgP = __ffs(P) - 1;
-        const int lgS = __ffs(strips) - 1;
-        const float cneg = -p.center;
-        for (int round = 0;; ++round) {
-            const int it = round * nwarps + ((round & 1) ? nwarps - 1 - warp : warp);
-            if (it >= nitems) break;
-            const int c = it >> lgS;
-            const int r = ((it - (c << lgS)) << 5) + lane;
-            if (r >= P) continue;
-            const SpecScale sc = p.sc[c0 + c];
-            Z[c * P + r] = fold_residue(X, sc, r, M, Mh, P, lgP, cneg, p.kexp);
+        // a3: the band walks of 8 or more bins per residue occur for P up to
+        // M/16; those periods get a compile-time stride.
+        switch (lgP) {
+            case 4: fold_items<4>(p, X, Z, c0, nc, M, P, lgP); break;
+            case 5: fold_items<5>(p, X, Z, c0, nc, M, P, lgP); break;
+            case 6: fold_items<6>(p, X, Z, c0, nc, M, P, lgP); break;
+            case 7: fold_items<7>(p, X, Z, c0, nc, M, P, lgP); break;
+            case 8: fold_items<8>(p, X, Z, c0, nc, M, P, lgP); break;
+            case 9: fold_items<9>(p, X, Z, c0, nc, M, P, lgP); break;
+            case 10: fold_items<10>(p, X, Z, c0, nc, M, P, lgP); break;
+            default: fold_items<0>(p, X, Z, c0, nc, M, P, lgP); break;
         }
         __syncthreads();
 
