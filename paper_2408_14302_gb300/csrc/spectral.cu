@@ -236,6 +236,14 @@ __device__ __forceinline__ float fast_exp2(float x) {
     return y;
 }
 
+// Hardware square-root approximation (sqrt.approx), a few ulp, far below
+// the path's 1e-5 tolerance; |z| of the inverse transforms.
+__device__ __forceinline__ float fast_sqrt(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // Sum of X[q] * exp2(kexp * (qf * a_over_m - C)^2) over n bins of one run:
 // indices q0, q0 + dq, ... (dq = +-P) and unwrapped bin positions qf,
 // qf + P, ... .  The weight is a sampled Gaussian: with u_j the argument at
@@ -420,16 +428,26 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) spectral_segment_kern
         // normalisation is already in gscale.  exp(+2 pi i m/P) = conj(tw[m H]).
         fft_block<true, kPPT>(Z, P, nc, tab, p.hop);
 
+        // Stores.  i < 2^24, so the float quotient is off by at most one
+        // and one correction step gives c = i / Fs exactly.
         const int Fs = p.seg_frames;
+        const float inv_fs = 1.0f / (float)Fs;
         for (int i = threadIdx.x; i < nc * Fs; i += blockDim.x) {
-            const int c = i / Fs;
-            const int f = i - c * Fs;
+            int c = (int)((float)i * inv_fs);
+            int f = i - c * Fs;
+            if (f < 0) {
+                --c;
+                f += Fs;
+            } else if (f >= Fs) {
+                ++c;
+                f -= Fs;
+            }
             const int64_t k = k0 + f;
             if (k < F) {
                 const float2 w = Z[c * P + p.kp0 + f];
                 const int row = p.sc[c0 + c].row;
                 p.out[((int64_t)clip * p.S_total + row) * p.frames_max + k] =
-                    sqrtf(fmaf(w.x, w.x, w.y * w.y));
+                    fast_sqrt(fmaf(w.x, w.x, w.y * w.y));
             }
         }
         __syncthreads();
