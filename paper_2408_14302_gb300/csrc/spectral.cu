@@ -92,6 +92,32 @@ struct Dft<8, INV> {
     }
 };
 
+// 16 points: two 8-point DFTs of the even and odd samples joined by
+// W16^k = exp(-+ 2 pi i k / 16).
+template <bool INV>
+struct Dft<16, INV> {
+    static __device__ __forceinline__ void run(float2* v) {
+        float2 e[8] = {v[0], v[2], v[4], v[6], v[8], v[10], v[12], v[14]};
+        float2 o[8] = {v[1], v[3], v[5], v[7], v[9], v[11], v[13], v[15]};
+        Dft<8, INV>::run(e);
+        Dft<8, INV>::run(o);
+        const float c1 = 0.92387953251128675613f;  // cos(pi / 8)
+        const float s1 = 0.38268343236508977173f;  // sin(pi / 8)
+        const float h = 0.70710678118654752440f;
+        const float sg = INV ? 1.f : -1.f;        // sign of the imaginary parts
+        const float2 w[8] = {make_float2(1.f, 0.f),    make_float2(c1, sg * s1),
+                             make_float2(h, sg * h),   make_float2(s1, sg * c1),
+                             make_float2(0.f, sg),     make_float2(-s1, sg * c1),
+                             make_float2(-h, sg * h),  make_float2(-c1, sg * s1)};
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const float2 t = k == 0 ? o[0] : (k == 4 ? rot90<INV>(o[4]) : cmul(o[k], w[k]));
+            v[k] = cadd(e[k], t);
+            v[k + 8] = csub(e[k], t);
+        }
+    }
+};
+
 // Twiddle table in shared memory, two levels: exp(-2 pi i m / M) =
 // t1[m >> 7] * t2[m & 127], t1[i] = exp(-2 pi i 128 i / M), t2[j] =
 // exp(-2 pi i j / M), both generated in float64 (one extra rounding).
@@ -106,7 +132,7 @@ __device__ __forceinline__ float2 tw_at(const TwTab& t, int m) {
 
 // Multiplies v[r] by w^r, w = exp(-+ 2 pi i k / (Ns R)) = table[k * tstride]
 // (conjugated for the inverse).  The powers come from a product tree of
-// depth <= 3, a few roundings each (~3e-7 relative).
+// depth <= 4, a few roundings each (~3e-7 relative).
 template <int R, bool INV>
 __device__ __forceinline__ void twiddle(float2* v, const TwTab& tw, int idx) {
     float2 w1 = tw_at(tw, idx);
@@ -114,14 +140,26 @@ __device__ __forceinline__ void twiddle(float2* v, const TwTab& tw, int idx) {
     v[1] = cmul(v[1], w1);
     if (R >= 4) {
         const float2 w2 = cmul(w1, w1);
+        const float2 w3 = cmul(w2, w1);
         v[2] = cmul(v[2], w2);
-        v[3] = cmul(v[3], cmul(w2, w1));
+        v[3] = cmul(v[3], w3);
         if (R >= 8) {
             const float2 w4 = cmul(w2, w2);
             v[4] = cmul(v[4], w4);
             v[5] = cmul(v[5], cmul(w4, w1));
             v[6] = cmul(v[6], cmul(w4, w2));
-            v[7] = cmul(v[7], cmul(w4, cmul(w2, w1)));
+            v[7] = cmul(v[7], cmul(w4, w3));
+            if (R >= 16) {
+                const float2 w8 = cmul(w4, w4);
+                v[8] = cmul(v[8], w8);
+                v[9] = cmul(v[9], cmul(w8, w1));
+                v[10] = cmul(v[10], cmul(w8, w2));
+                v[11] = cmul(v[11], cmul(w8, w3));
+                v[12] = cmul(v[12], cmul(w8, w4));
+                v[13] = cmul(v[13], cmul(w8, cmul(w4, w1)));
+                v[14] = cmul(v[14], cmul(w8, cmul(w4, w2)));
+                v[15] = cmul(v[15], cmul(w8, cmul(w4, w3)));
+            }
         }
     }
 }
@@ -211,21 +249,44 @@ __device__ __forceinline__ void fft_pass_dispatch(float2* buf, int L, int nbatch
 
 // Batched power-of-two FFT in shared memory, natural order in and out.
 // ts = M / L maps the transform's twiddles onto the table of exp(-2 pi i m/M).
-// Radices: 8 where possible, a leading 4 (or 4,4) for the remainder of log2 L.
+// Radices, with 16 or more points per thread: 16 where possible, the
+// remainder of log2 L as a leading 8, 4 or 8,4 (8192 points: 8,4,16,16);
+// with fewer: 8 where possible, a leading 4 (or 4,4).
 template <bool INV, int PPT>
 __device__ __forceinline__ void fft_block(float2* buf, int L, int nbatch, const TwTab& tw, int ts) {
     const int e = __ffs(L) - 1;  // L >= 8: the plan keeps P = M/H >= 8 and M/2 >= 256
-    const int n4 = (e % 3 == 1) ? 2 : (e % 3 == 2) ? 1 : 0;
-    const int npass = n4 + (e - 2 * n4) / 3;
     int Ns = 1;
-    for (int i = 0; i < npass; ++i) {
-        const bool rs = i > 0, ws = i + 1 < npass;
-        if (i < n4) {
-            fft_pass_dispatch<4, INV, PPT>(buf, L, nbatch, Ns, tw, ts * (L / (Ns * 4)), rs, ws);
-            Ns *= 4;
-        } else {
-            fft_pass_dispatch<8, INV, PPT>(buf, L, nbatch, Ns, tw, ts * (L / (Ns * 8)), rs, ws);
-            Ns *= 8;
+    if constexpr (PPT >= 16) {
+        const int m = e & 3;
+        const int n8 = (m == 3 || m == 1) ? 1 : 0;
+        const int n4 = (m == 2 || m == 1) ? 1 : 0;
+        const int npass = n8 + n4 + (e - 3 * n8 - 2 * n4) / 4;
+        for (int i = 0; i < npass; ++i) {
+            const bool rs = i > 0, ws = i + 1 < npass;
+            if (i < n8) {
+                fft_pass_dispatch<8, INV, PPT>(buf, L, nbatch, Ns, tw, ts * (L / (Ns * 8)), rs, ws);
+                Ns *= 8;
+            } else if (i < n8 + n4) {
+                fft_pass_dispatch<4, INV, PPT>(buf, L, nbatch, Ns, tw, ts * (L / (Ns * 4)), rs, ws);
+                Ns *= 4;
+            } else {
+                fft_pass_dispatch<16, INV, PPT>(buf, L, nbatch, Ns, tw, ts * (L / (Ns * 16)), rs,
+                                                ws);
+                Ns *= 16;
+            }
+        }
+    } else {
+        const int n4 = (e % 3 == 1) ? 2 : (e % 3 == 2) ? 1 : 0;
+        const int npass = n4 + (e - 2 * n4) / 3;
+        for (int i = 0; i < npass; ++i) {
+            const bool rs = i > 0, ws = i + 1 < npass;
+            if (i < n4) {
+                fft_pass_dispatch<4, INV, PPT>(buf, L, nbatch, Ns, tw, ts * (L / (Ns * 4)), rs, ws);
+                Ns *= 4;
+            } else {
+                fft_pass_dispatch<8, INV, PPT>(buf, L, nbatch, Ns, tw, ts * (L / (Ns * 8)), rs, ws);
+                Ns *= 8;
+            }
         }
     }
 }
