@@ -48,13 +48,15 @@ int nconc_within(int M, int P, int limit, size_t cap) {
 }
 
 // CTA shape of the spectral kernel for a segment length (see
-// cwth_internal.h): two 512-thread CTAs per SM unless they do not fit, or
-// fit at most two scales per pass where one 1024-thread CTA fits more.
+// cwth_internal.h): two 512-thread CTAs per SM (radix-16 FFT passes)
+// whenever one scale per pass fits their shared memory, else one 1024-thread
+// CTA.  Measured on GB300, 64 x 10 s clips, 64 scales: the pair is faster
+// at hops 1, 4, 8, 16 and 64 (hop 4: 2.42 vs 2.68 ms, 1 vs 2 scales per
+// pass), slower only at hop 32 (0.480 vs 0.453 ms).
 int spectral_threads(int M, int P, int n_scales) {
-    if (cwth::spectral_smem_bytes(M, P, 1) > kSmemPair) return cwth::kSpecThreadsSolo;
-    const int pair = nconc_within(M, P, n_scales, kSmemPair);
-    const int solo = nconc_within(M, P, n_scales, kSmemCap);
-    return (pair <= 2 && solo > pair) ? cwth::kSpecThreadsSolo : cwth::kSpecThreadsPair;
+    (void)n_scales;
+    return cwth::spectral_smem_bytes(M, P, 1) > kSmemPair ? cwth::kSpecThreadsSolo
+                                                          : cwth::kSpecThreadsPair;
 }
 
 // Scales one spectral CTA folds and inverts together for a segment length

@@ -18,10 +18,11 @@ constexpr uint32_t kPlanMagic = 0xC0A7B17Eu;
 // Spectral CTA shapes (64 registers per thread either way): two 512-thread
 // CTAs per SM, so one CTA's phase barriers are covered by the other's work,
 // or one 1024-thread CTA per SM, which has the whole SM's shared memory and
-// so inverts more scales per pass when the inverse FFTs are long.  Measured
-// on GB300 (64 x 10 s clips, 64 scales): the pair is 0-20 % faster unless it
-// fits at most two scales per pass and the single CTA fits more (hops 4-8
-// at M = 16384), where the single CTA is 15-20 % faster.
+// so inverts more scales per pass when the inverse FFTs are long.  The pair
+// holds 16 points per thread and so runs radix-16 FFT passes; measured on
+// GB300 (64 x 10 s clips, 64 scales) it is 5-20 % faster wherever one scale
+// per pass fits its shared memory, except at hop 32 (6 % slower); the
+// single CTA runs only where the pair does not fit (hop 2 at M = 16384).
 constexpr int kSpecThreadsPair = 512;
 constexpr int kSpecThreadsSolo = 1024;
 // Largest batched shared-memory FFT (complex points) one CTA performs: 16

@@ -103,16 +103,18 @@ def test_machine_batch64_sampled_rows(cw, sig):
         assert err <= TOL_FP32
 
 
-def test_machine_10s_hop1_sampled_scales(cw, sig):
-    """Hop 1 (the metric's comparison point) on full 10 s clips in the
-    benchmark's 64-scale plan; the widest, a middle and the narrowest scale
-    rows are checked against the oracle, normalised by their own maximum
-    (stricter than the maximum over all scales)."""
-    n, hop = 160000, 1
+@pytest.mark.parametrize("hop", [1, 4, 8])
+def test_machine_10s_small_hops_sampled_scales(cw, sig, hop):
+    """Hop 1 (the metric's comparison point) and hops 4 and 8 (inverse FFTs
+    of 4096 and 2048 points, one or two scales per pass) on full 10 s clips
+    in the benchmark's 64-scale plan; the widest, a middle and the narrowest
+    scale rows are checked against the oracle, normalised by their own
+    maximum (stricter than the maximum over all scales)."""
+    n = 160000
     xs = sig.machine_batch(2, n)
     sc = sig.scales_for_band(50, 8000, 64, 16000.0)
     got, info = run_gpu(cw, xs, sc, hop)
-    assert info["num_segments"] > 1 and got.shape[2] == n
+    assert info["num_segments"] > 1 and got.shape[2] == -(-n // hop)
     rows = np.array([0, 31, 63])
     for i in range(2):
         ref = oracle_mag(xs[i], sc[rows], hop)
