@@ -388,26 +388,27 @@ __device__ __forceinline__ float2 fold_residue(const float2* __restrict__ X, con
     return make_float2(sc.gscale * (ad.x + am.x), sc.gscale * (ad.y - am.y));
 }
 
-// a3 for one chunk of scales: band multiply + hop fold.  Lane = residue r;
-// one item = 32 consecutive residues of one scale; the loop walks the
-// unwrapped band.  Items are ordered by decreasing band width (scales
-// ascend); they are dealt to warps in a snake order to balance the work.
+// a3 for one chunk of scales: band multiply + hop fold.  The chunk's
+// (scale, residue) pairs are numbered g = c P + r; one item = 32
+// consecutive g (32 residues of one scale, or 32 / P whole scales when
+// P < 32), one lane each; the loop walks the unwrapped band.  Items are
+// ordered by decreasing band width (scales ascend); they are dealt to warps
+// in a snake order to balance the work.
 template <int LGP>
 __device__ __forceinline__ void fold_items(const SpecLaunch& p, const float2* __restrict__ X,
                                            float2* __restrict__ Z, int c0, int nc, int M, int P,
                                            int lgP) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nwarps = blockDim.x >> 5;
-    const int strips = (P + 31) >> 5;
-    const int nitems = nc * strips;
-    const int lgS = __ffs(strips) - 1;
+    const int nitems = (nc * P + 31) >> 5;
     const float cneg = -p.center;
     for (int round = 0;; ++round) {
         const int it = round * nwarps + ((round & 1) ? nwarps - 1 - warp : warp);
         if (it >= nitems) break;
-        const int c = it >> lgS;
-        const int r = ((it - (c << lgS)) << 5) + lane;
-        if (r >= P) continue;
+        const int g = (it << 5) + lane;
+        const int c = g >> lgP;
+        const int r = g & (P - 1);
+        if (c >= nc) continue;
         const SpecScale sc = p.sc[c0 + c];
         Z[c * P + r] = fold_residue<LGP>(X, sc, r, M, M >> 1, P, lgP, cneg, p.kexp);
     }
