@@ -7,8 +7,10 @@
 // (overlap-save).  Everything after the input load stays in shared memory:
 //
 //   a1  stage    z[n] = x[s0+2n] + i x[s0+2n+1], zero outside [0, len)
-//   a2  FFT      Stockham radix-4/8 FFT of the M/2 complex points, then the
-//                real-input split to X[q], q = 0 .. M/2
+//   a2  FFT      Stockham FFT of the M/2 complex points (radix 16 with a
+//                leading 8 / 4 in the 512-thread shape, radix 8 with a
+//                leading 4 in the 1024-thread one), then the real-input
+//                split to X[q], q = 0 .. M/2
 //   a3  fold     Z_s[r] = sum_{q = r (mod P)} X[q] * sqrt(a)/M * Psi(a q/M)
 //                over the unwrapped Morlet band of scale s (P = M/H); the
 //                spectrum is summed over the H aliases of each bin, which is

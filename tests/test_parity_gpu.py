@@ -103,13 +103,15 @@ def test_machine_batch64_sampled_rows(cw, sig):
         assert err <= TOL_FP32
 
 
-@pytest.mark.parametrize("hop", [1, 4, 8])
-def test_machine_10s_small_hops_sampled_scales(cw, sig, hop):
-    """Hop 1 (the metric's comparison point) and hops 4 and 8 (inverse FFTs
-    of 4096 and 2048 points, one or two scales per pass) on full 10 s clips
-    in the benchmark's 64-scale plan; the widest, a middle and the narrowest
-    scale rows are checked against the oracle, normalised by their own
-    maximum (stricter than the maximum over all scales)."""
+@pytest.mark.parametrize("hop", [1, 4, 8, 512, 1024])
+def test_machine_10s_sampled_scales(cw, sig, hop):
+    """Full 10 s clips in the benchmark's 64-scale plan at hop 1 (the
+    metric's comparison point), hops 4 and 8 (inverse FFTs of 4096 and 2048
+    points, one or two scales per pass) and hops 512 and 1024 (periods of 32
+    and 16 residues: one fold warp covers one or two scales); the widest, a
+    middle and the narrowest scale rows are checked against the oracle,
+    normalised by their own maximum (stricter than the maximum over all
+    scales)."""
     n = 160000
     xs = sig.machine_batch(2, n)
     sc = sig.scales_for_band(50, 8000, 64, 16000.0)
