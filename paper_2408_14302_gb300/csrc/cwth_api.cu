@@ -53,8 +53,7 @@ int nconc_within(int M, int P, int limit, size_t cap) {
 // CTA.  Measured on GB300, 64 x 10 s clips, 64 scales: the pair is faster
 // at hops 1, 4, 8, 16 and 64 (hop 4: 2.42 vs 2.68 ms, 1 vs 2 scales per
 // pass), slower only at hop 32 (0.480 vs 0.453 ms).
-int spectral_threads(int M, int P, int n_scales) {
-    (void)n_scales;
+int spectral_threads(int M, int P) {
     return cwth::spectral_smem_bytes(M, P, 1) > kSmemPair ? cwth::kSpecThreadsSolo
                                                           : cwth::kSpecThreadsPair;
 }
@@ -129,7 +128,7 @@ bool choose_segment(const cwth_plan_s& p, const std::vector<double>& sp_scales, 
         const int64_t Fseg = last - kp0 + 1;
         if (Fseg < 1) continue;
         if (cwth::spectral_smem_bytes((int)M, (int)P, 1) > kSmemCap) continue;
-        const int threads = spectral_threads((int)M, (int)P, (int)sp_scales.size());
+        const int threads = spectral_threads((int)M, (int)P);
         if (M / 2 > cwth::kMaxFftPoints || P > cwth::kMaxFftPoints) continue;
         const int64_t n_seg = (p.frames_max + Fseg - 1) / Fseg;
         double fold = 0;
@@ -456,7 +455,7 @@ cwth_status launch_spectral(const cwth_plan_s* p, const float* d_x, int64_t ld_x
     n_groups = std::max(1, n_groups);
     const int gs = (p->n_sp + n_groups - 1) / n_groups;
     n_groups = (p->n_sp + gs - 1) / gs;
-    const int threads = spectral_threads(p->M, p->P, p->n_sp);
+    const int threads = spectral_threads(p->M, p->P);
     const int nconc = spectral_nconc(p->M, p->P, gs, threads);
     if (batch > 65535 || p->n_seg > 0x7fffffff) return CWTH_ERR_UNSUPPORTED;
 
