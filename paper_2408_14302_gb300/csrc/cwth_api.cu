@@ -103,6 +103,42 @@ void band_limits(double a, double B, double C, int M, int64_t* q_lo, int64_t* q_
     *q_hi = (int64_t)ceil((double)M * (C + delta) / a);
 }
 
+// Pass plan of the spectral kernel's FFTs (the device's fft_radix): with
+// 16 points per thread (512-thread CTAs) radix 16 and a leading 8, 4 or
+// 8,4; with 8, radix 8 and a leading 4 or 4,4.
+std::vector<int> spectral_fft_radices(int L, int threads) {
+    const int e = ilog2(L);
+    std::vector<int> r;
+    if (threads == cwth::kSpecThreadsPair) {
+        const int m = e & 3;
+        if (m == 3 || m == 1) r.push_back(8);
+        if (m == 2 || m == 1) r.push_back(4);
+        for (int b = e - (m == 3 ? 3 : m == 2 ? 2 : m == 1 ? 5 : 0); b > 0; b -= 4) r.push_back(16);
+    } else {
+        const int n4 = (e % 3 == 1) ? 2 : (e % 3 == 2) ? 1 : 0;
+        for (int i = 0; i < n4; ++i) r.push_back(4);
+        for (int b = e - 2 * n4; b > 0; b -= 3) r.push_back(8);
+    }
+    return r;
+}
+
+// Whether the pruned kernel (inverse FFTs skip the leading passes a narrow
+// band leaves trivial) is worth its extra register pressure: only when the
+// skipped passes would be at least a tenth of all inverse-FFT passes.
+// Measured on GB300, 64 x 10 s clips, 64 scales: hop 1 (22 % of passes
+// skipped) 12.23 -> 11.43 ms and hop 2 (15 %) 6.02 -> 5.44 ms with pruning;
+// hop 4 (6 %) 2.38 -> 2.62 ms, so it stays off there.
+bool spectral_prune_pays(const std::vector<SpecScale>& sc, int P, int threads) {
+    const std::vector<int> rad = spectral_fft_radices(P, threads);
+    int64_t skipped = 0;
+    for (const SpecScale& s : sc) {
+        const int64_t w = std::min<int64_t>(P, s.q_hi - s.q_lo + 1);
+        int64_t ns = 1;
+        for (size_t i = 0; i + 1 < rad.size() && w * ns * rad[i] <= P; ++i, ++skipped) ns *= rad[i];
+    }
+    return 10 * skipped >= (int64_t)sc.size() * (int64_t)rad.size();
+}
+
 struct SegChoice {
     int M = 0, P = 0, halo = 0, kp0 = 0, seg_frames = 0, n_seg = 0;
     double cost = 0;
@@ -391,11 +427,18 @@ cwth_status build_direct(cwth_plan_s* p) {
 cwth_status build_spectral(cwth_plan_s* p) {
     std::vector<double> sp;
     std::vector<int32_t> rows;
+    // Spectral scales in ascending scale order (descending band width; each
+    // keeps its output row), so that a chunk's first scale has its widest
+    // band and the fold deals its widest items first.
+    std::vector<int32_t> order;
     for (int s = 0; s < p->S; ++s)
-        if (p->scale_path[s] == CWTH_PATH_SPECTRAL) {
-            sp.push_back(p->scales[s]);
-            rows.push_back(s);
-        }
+        if (p->scale_path[s] == CWTH_PATH_SPECTRAL) order.push_back(s);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int32_t i, int32_t j) { return p->scales[i] < p->scales[j]; });
+    for (int32_t s : order) {
+        sp.push_back(p->scales[s]);
+        rows.push_back(s);
+    }
     p->n_sp = (int32_t)sp.size();
     if (p->n_sp == 0) return CWTH_OK;
     if (!is_pow2(p->hop)) return CWTH_ERR_UNSUPPORTED;
@@ -423,7 +466,11 @@ cwth_status build_spectral(cwth_plan_s* p) {
         const double dlt = sp[i] * (double)p->P / (double)p->M;
         s.dlt = (float)dlt;
         s.q2 = (float)exp2(2.0 * kexp * (double)s.dlt * (double)s.dlt);
+        s.wsuf = (int32_t)std::min<int64_t>(p->P, hi - lo + 1);
     }
+    for (size_t i = host.size(); i-- > 1;)
+        host[i - 1].wsuf = std::max(host[i - 1].wsuf, host[i].wsuf);
+    p->spec_prune = spectral_prune_pays(host, p->P, spectral_threads(p->M, p->P));
     const size_t ntw = (size_t)cwth::spectral_twiddle_entries(p->M);
     cudaError_t e = cudaMalloc(&p->d_tw, sizeof(float2) * ntw);
     if (e != cudaSuccess) return cuda_status(e);
@@ -482,7 +529,7 @@ cwth_status launch_spectral(const cwth_plan_s* p, const float* d_x, int64_t ld_x
     L.sc = p->d_sp;
     const size_t smem = cwth::spectral_smem_bytes(p->M, p->P, nconc);
     return cuda_status(
-        cwth::spectral_launch(L, threads, p->n_seg, batch, n_groups, smem, st));
+        cwth::spectral_launch(L, threads, p->spec_prune, p->n_seg, batch, n_groups, smem, st));
 }
 
 cwth_status launch_direct(cwth_plan_s* p, const float* d_x, int64_t ld_x, const int64_t* d_len,

@@ -44,7 +44,11 @@ struct SpecScale {
     int32_t row;     // output row (index into the caller's scale list)
     float dlt;       // a P / M: argument step between the bins a residue visits
     float q2;        // 2^(2 kexp dlt^2): ratio of successive weight ratios
-    int32_t pad_;
+    // Upper bound on the folded band width, min(P, q_hi - q_lo + 1), of this
+    // and every later scale in the table (a suffix maximum): the band of
+    // any chunk of scales starting here fits in wsuf residues once shifted
+    // to start at residue 0.
+    int32_t wsuf;
 };
 
 struct SpecLaunch {
@@ -117,8 +121,8 @@ size_t spectral_smem_bytes(int M, int P, int nconc);
 int spectral_twiddle_entries(int M);
 cudaError_t spectral_prepare_device();
 cudaError_t spectral_make_twiddles(float2* d_tw, int M, cudaStream_t st);
-cudaError_t spectral_launch(const SpecLaunch& L, int threads, int n_seg, int batch, int n_groups,
-                            size_t smem, cudaStream_t st);
+cudaError_t spectral_launch(const SpecLaunch& L, int threads, bool prune, int n_seg, int batch,
+                            int n_groups, size_t smem, cudaStream_t st);
 
 size_t direct_smem_bytes(int ncols, int stages, bool split, int win_rows, int unit,
                          int win_sets, int phases);
@@ -185,6 +189,7 @@ struct cwth_plan_s {
     // spectral path
     int32_t n_sp = 0;
     int32_t M = 0, P = 0, halo = 0, kp0 = 0, seg_frames = 0, n_seg = 0;
+    bool spec_prune = false;  // narrow bands let inverse FFTs skip passes
     float2* d_tw = nullptr;
     cwth::SpecScale* d_sp = nullptr;
 

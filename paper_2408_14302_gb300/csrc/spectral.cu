@@ -174,7 +174,11 @@ __device__ __forceinline__ void twiddle(float2* v, const TwTab& tw, int idx) {
 // (j - k) R + k.  All reads finish before any write (barrier), so the pass
 // runs in place; rs / ws select the layout read and written.  tstride is
 // the twiddle-table step for one unit of r*k.
-template <int R, int MAXB, bool INV>
+// BC: the passes before this one, of total size Ns, were skipped because
+// every input is zero from index L / Ns on; their result is read in place:
+// element i of transform b is x[b L + (i >> log2 Ns)] (x in natural order),
+// since each skipped sub-transform saw a single nonzero sample.
+template <int R, int MAXB, bool INV, bool BC = false>
 __device__ __forceinline__ void fft_pass(float2* __restrict__ buf, int L, int nbatch, int Ns,
                                          const TwTab& tw, int tstride, bool rs, bool ws) {
     const int LR = L / R;
@@ -190,7 +194,11 @@ __device__ __forceinline__ void fft_pass(float2* __restrict__ buf, int L, int nb
             const int base = b * L + jj;
             // The swizzle only mixes bits 4..7 into bits 0..3, so a stride
             // that is a multiple of 256 moves a swizzled address linearly.
-            if (!rs) {
+            if constexpr (BC) {
+                const int lgN = __ffs(Ns) - 1;
+#pragma unroll
+                for (int r = 0; r < R; ++r) v[u][r] = buf[b * L + ((jj + r * LR) >> lgN)];
+            } else if (!rs) {
 #pragma unroll
                 for (int r = 0; r < R; ++r) v[u][r] = buf[base + r * LR];
             } else if ((LR & 255) == 0) {
@@ -231,7 +239,7 @@ __device__ __forceinline__ void fft_pass(float2* __restrict__ buf, int L, int nb
     __syncthreads();
 }
 
-template <int R, bool INV, int PPT>
+template <int R, bool INV, int PPT, bool BC = false>
 __device__ __forceinline__ void fft_pass_dispatch(float2* buf, int L, int nbatch, int Ns,
                                                   const TwTab& tw, int tstride, bool rs, bool ws) {
     const int nb = nbatch * (L / R);
@@ -240,25 +248,86 @@ __device__ __forceinline__ void fft_pass_dispatch(float2* buf, int L, int nbatch
     // kMaxFftPoints = PPT * blockDim.x.
     constexpr int kMaxB = PPT / R;
     if (per <= 1 || kMaxB <= 1)
-        fft_pass<R, 1, INV>(buf, L, nbatch, Ns, tw, tstride, rs, ws);
+        fft_pass<R, 1, INV, BC>(buf, L, nbatch, Ns, tw, tstride, rs, ws);
     else if (per <= 2 || kMaxB <= 2)
-        fft_pass<R, 2, INV>(buf, L, nbatch, Ns, tw, tstride, rs, ws);
+        fft_pass<R, 2, INV, BC>(buf, L, nbatch, Ns, tw, tstride, rs, ws);
     else if (per <= 4 || kMaxB <= 4)
-        fft_pass<R, (kMaxB < 4 ? kMaxB : 4), INV>(buf, L, nbatch, Ns, tw, tstride, rs, ws);
+        fft_pass<R, (kMaxB < 4 ? kMaxB : 4), INV, BC>(buf, L, nbatch, Ns, tw, tstride, rs, ws);
     else
-        fft_pass<R, kMaxB, INV>(buf, L, nbatch, Ns, tw, tstride, rs, ws);
+        fft_pass<R, kMaxB, INV, BC>(buf, L, nbatch, Ns, tw, tstride, rs, ws);
+}
+
+// Radix of pass i of a transform of 2^e points.  With 16 or more points
+// per thread: 16 where possible, the remainder of e as a leading 8, 4 or
+// 8,4 (8192 points: 8,4,16,16); with fewer: 8 where possible, a leading 4
+// (or 4,4).
+template <int PPT>
+__device__ __forceinline__ int fft_radix(int e, int i) {
+    if constexpr (PPT >= 16) {
+        const int m = e & 3;
+        const int n8 = (m == 3 || m == 1) ? 1 : 0;
+        const int n4 = (m == 2 || m == 1) ? 1 : 0;
+        return i < n8 ? 8 : (i < n8 + n4 ? 4 : 16);
+    } else {
+        const int n4 = (e % 3 == 1) ? 2 : (e % 3 == 2) ? 1 : 0;
+        return i < n4 ? 4 : 8;
+    }
+}
+
+template <int PPT>
+__device__ __forceinline__ int fft_npass(int e) {
+    if constexpr (PPT >= 16) {
+        const int m = e & 3;
+        const int n8 = (m == 3 || m == 1) ? 1 : 0;
+        const int n4 = (m == 2 || m == 1) ? 1 : 0;
+        return n8 + n4 + (e - 3 * n8 - 2 * n4) / 4;
+    } else {
+        const int n4 = (e % 3 == 1) ? 2 : (e % 3 == 2) ? 1 : 0;
+        return n4 + (e - 2 * n4) / 3;
+    }
+}
+
+template <bool INV, int PPT, bool BC>
+__device__ __forceinline__ void fft_pass_radix(int R, float2* buf, int L, int nbatch, int Ns,
+                                               const TwTab& tw, int ts, bool rs, bool ws) {
+    if (R == 4) {
+        fft_pass_dispatch<4, INV, PPT, BC>(buf, L, nbatch, Ns, tw, ts * (L / (Ns * 4)), rs, ws);
+    } else if (R == 8) {
+        fft_pass_dispatch<8, INV, PPT, BC>(buf, L, nbatch, Ns, tw, ts * (L / (Ns * 8)), rs, ws);
+    } else if constexpr (PPT >= 16) {
+        fft_pass_dispatch<16, INV, PPT, BC>(buf, L, nbatch, Ns, tw, ts * (L / (Ns * 16)), rs, ws);
+    }
 }
 
 // Batched power-of-two FFT in shared memory, natural order in and out.
 // ts = M / L maps the transform's twiddles onto the table of exp(-2 pi i m/M).
-// Radices, with 16 or more points per thread: 16 where possible, the
-// remainder of log2 L as a leading 8, 4 or 8,4 (8192 points: 8,4,16,16);
-// with fewer: 8 where possible, a leading 4 (or 4,4).
-template <bool INV, int PPT>
-__device__ __forceinline__ void fft_block(float2* buf, int L, int nbatch, const TwTab& tw, int ts) {
+// PRUNE: every input is zero from index wmax on, so the leading passes
+// whose radices multiply to at most L / wmax (all but the last, at most)
+// are skipped and the next pass reads their result directly (see BC).
+template <bool INV, int PPT, bool PRUNE = false>
+__device__ __forceinline__ void fft_block(float2* buf, int L, int nbatch, const TwTab& tw, int ts,
+                                          int wmax = 0) {
     const int e = __ffs(L) - 1;  // L >= 8: the plan keeps P = M/H >= 8 and M/2 >= 256
     int Ns = 1;
-    if constexpr (PPT >= 16) {
+    if constexpr (PRUNE) {
+        const int npass = fft_npass<PPT>(e);
+        int i = 0;
+        while (i + 1 < npass && (int64_t)wmax * Ns * fft_radix<PPT>(e, i) <= L)
+            Ns *= fft_radix<PPT>(e, i++);
+        if (i > 0) {
+            const int R = fft_radix<PPT>(e, i);
+            fft_pass_radix<INV, PPT, true>(R, buf, L, nbatch, Ns, tw, ts, false, i + 1 < npass);
+            Ns *= R;
+            ++i;
+        }
+        for (; i < npass; ++i) {
+            const int R = fft_radix<PPT>(e, i);
+            fft_pass_radix<INV, PPT, false>(R, buf, L, nbatch, Ns, tw, ts, i > 0, i + 1 < npass);
+            Ns *= R;
+        }
+    } else if constexpr (PPT >= 16) {
+        // The same plan as fft_radix, with the passes unrolled by kind
+        // (measured faster than dispatching on the radix at run time).
         const int m = e & 3;
         const int n8 = (m == 3 || m == 1) ? 1 : 0;
         const int n4 = (m == 2 || m == 1) ? 1 : 0;
@@ -396,7 +465,7 @@ __device__ __forceinline__ float2 fold_residue(const float2* __restrict__ X, con
 // P < 32), one lane each; the loop walks the unwrapped band.  Items are
 // ordered by decreasing band width (scales ascend); they are dealt to warps
 // in a snake order to balance the work.
-template <int LGP>
+template <int LGP, bool SHIFT>
 __device__ __forceinline__ void fold_items(const SpecLaunch& p, const float2* __restrict__ X,
                                            float2* __restrict__ Z, int c0, int nc, int M, int P,
                                            int lgP) {
@@ -412,11 +481,17 @@ __device__ __forceinline__ void fold_items(const SpecLaunch& p, const float2* __
         const int r = g & (P - 1);
         if (c >= nc) continue;
         const SpecScale sc = p.sc[c0 + c];
-        Z[c * P + r] = fold_residue<LGP>(X, sc, r, M, M >> 1, P, lgP, cneg, p.kexp);
+        // SHIFT: stored shifted by the band's first residue (a unit-modulus
+        // phase on the inverse transform, so |W| is unchanged); the band
+        // then occupies residues [0, min(P, q_hi - q_lo + 1)).
+        const int zr = SHIFT ? ((r - sc.q_lo) & (P - 1)) : r;
+        Z[c * P + zr] = fold_residue<LGP>(X, sc, r, M, M >> 1, P, lgP, cneg, p.kexp);
     }
 }
 
-template <int THREADS>
+// PRUNE: inverse FFTs skip the passes that a chunk's narrow bands leave
+// trivial (plans whose narrowest folded band fits a small fraction of P).
+template <int THREADS, bool PRUNE>
 __global__ void __launch_bounds__(THREADS, 1024 / THREADS) spectral_segment_kernel(const SpecLaunch p) {
     constexpr int kPPT = kMaxFftPoints / THREADS;  // FFT points per thread
     extern __shared__ float2 smem[];
@@ -477,20 +552,22 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) spectral_segment_kern
         // a3: the band walks of 8 or more bins per residue occur for P up to
         // M/16; those periods get a compile-time stride.
         switch (lgP) {
-            case 4: fold_items<4>(p, X, Z, c0, nc, M, P, lgP); break;
-            case 5: fold_items<5>(p, X, Z, c0, nc, M, P, lgP); break;
-            case 6: fold_items<6>(p, X, Z, c0, nc, M, P, lgP); break;
-            case 7: fold_items<7>(p, X, Z, c0, nc, M, P, lgP); break;
-            case 8: fold_items<8>(p, X, Z, c0, nc, M, P, lgP); break;
-            case 9: fold_items<9>(p, X, Z, c0, nc, M, P, lgP); break;
-            case 10: fold_items<10>(p, X, Z, c0, nc, M, P, lgP); break;
-            default: fold_items<0>(p, X, Z, c0, nc, M, P, lgP); break;
+            case 4: fold_items<4, PRUNE>(p, X, Z, c0, nc, M, P, lgP); break;
+            case 5: fold_items<5, PRUNE>(p, X, Z, c0, nc, M, P, lgP); break;
+            case 6: fold_items<6, PRUNE>(p, X, Z, c0, nc, M, P, lgP); break;
+            case 7: fold_items<7, PRUNE>(p, X, Z, c0, nc, M, P, lgP); break;
+            case 8: fold_items<8, PRUNE>(p, X, Z, c0, nc, M, P, lgP); break;
+            case 9: fold_items<9, PRUNE>(p, X, Z, c0, nc, M, P, lgP); break;
+            case 10: fold_items<10, PRUNE>(p, X, Z, c0, nc, M, P, lgP); break;
+            default: fold_items<0, PRUNE>(p, X, Z, c0, nc, M, P, lgP); break;
         }
         __syncthreads();
 
         // a4: inverse FFT of length P for every scale of the chunk; the 1/M
         // normalisation is already in gscale.  exp(+2 pi i m/P) = conj(tw[m H]).
-        fft_block<true, kPPT>(Z, P, nc, tab, p.hop);
+        // With PRUNE every band of the chunk lies in its first sc[c0].wsuf
+        // residues.
+        fft_block<true, kPPT, PRUNE>(Z, P, nc, tab, p.hop, PRUNE ? p.sc[c0].wsuf : 0);
 
         // Stores.  i < 2^24, so the float quotient is off by at most one
         // and one correction step gives c = i / Fs exactly.
@@ -540,12 +617,15 @@ size_t spectral_smem_bytes(int M, int P, int nconc) {
 int spectral_twiddle_entries(int M) { return (M >> 7) + 128; }
 
 cudaError_t spectral_prepare_device() {
-    cudaError_t e = cudaFuncSetAttribute(spectral_segment_kernel<kSpecThreadsPair>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         227 * 1024 - 1024);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(spectral_segment_kernel<kSpecThreadsSolo>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024 - 1024);
+    cudaError_t e = cudaSuccess;
+    for (const void* f : {(const void*)spectral_segment_kernel<kSpecThreadsPair, false>,
+                          (const void*)spectral_segment_kernel<kSpecThreadsPair, true>,
+                          (const void*)spectral_segment_kernel<kSpecThreadsSolo, false>,
+                          (const void*)spectral_segment_kernel<kSpecThreadsSolo, true>})
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     227 * 1024 - 1024);
+    return e;
 }
 
 cudaError_t spectral_make_twiddles(float2* d_tw, int M, cudaStream_t st) {
@@ -553,13 +633,20 @@ cudaError_t spectral_make_twiddles(float2* d_tw, int M, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t spectral_launch(const SpecLaunch& L, int threads, int n_seg, int batch, int n_groups,
-                            size_t smem, cudaStream_t st) {
+cudaError_t spectral_launch(const SpecLaunch& L, int threads, bool prune, int n_seg, int batch,
+                            int n_groups, size_t smem, cudaStream_t st) {
     dim3 grid(n_seg, batch, n_groups);
-    if (threads == kSpecThreadsSolo)
-        spectral_segment_kernel<kSpecThreadsSolo><<<grid, kSpecThreadsSolo, smem, st>>>(L);
-    else
-        spectral_segment_kernel<kSpecThreadsPair><<<grid, kSpecThreadsPair, smem, st>>>(L);
+    if (threads == kSpecThreadsSolo) {
+        if (prune)
+            spectral_segment_kernel<kSpecThreadsSolo, true><<<grid, kSpecThreadsSolo, smem, st>>>(L);
+        else
+            spectral_segment_kernel<kSpecThreadsSolo, false><<<grid, kSpecThreadsSolo, smem, st>>>(L);
+    } else {
+        if (prune)
+            spectral_segment_kernel<kSpecThreadsPair, true><<<grid, kSpecThreadsPair, smem, st>>>(L);
+        else
+            spectral_segment_kernel<kSpecThreadsPair, false><<<grid, kSpecThreadsPair, smem, st>>>(L);
+    }
     return cudaGetLastError();
 }
 
