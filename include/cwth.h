@@ -203,6 +203,12 @@ typedef struct {
     int32_t resample;          /* 1, or H of a cwth_plan_resampled plan (whose
                                   other fields describe its hop-1 transform of
                                   the re-sampled signal)                       */
+    int32_t spectral_threads;  /* threads per spectral CTA: 512 (two CTAs per
+                                  SM) or 1024 (one); 0 without spectral scales */
+    int32_t spectral_pass_scales; /* most scales one spectral CTA folds and
+                                  inverts together                             */
+    int32_t spectral_pruned;   /* 1 if the inverse FFTs skip the leading passes
+                                  that narrow Morlet bands leave trivial       */
 } cwth_plan_info;
 
 /* Fill *info.  Errors: CWTH_ERR_BAD_PLAN, CWTH_ERR_INVALID_ARG (NULL info). */

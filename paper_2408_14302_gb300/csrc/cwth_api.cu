@@ -945,6 +945,11 @@ cwth_status cwth_plan_query(cwth_plan_t p, cwth_plan_info* info) {
     info->table_bytes = p->table_bytes;
     info->sample_rate = p->fs;
     info->resample = p->resample;
+    if (p->n_sp > 0) {
+        info->spectral_threads = spectral_threads(p->M, p->P);
+        info->spectral_pass_scales = spectral_nconc(p->M, p->P, p->n_sp, info->spectral_threads);
+        info->spectral_pruned = p->spec_prune ? 1 : 0;
+    }
     return CWTH_OK;
 }
 

@@ -48,7 +48,8 @@ class PlanInfo(ctypes.Structure):
                 ("seg_halo", ctypes.c_int32), ("fold_len", ctypes.c_int32),
                 ("num_segments", ctypes.c_int32), ("direct_taps", ctypes.c_int32),
                 ("table_bytes", ctypes.c_int64), ("sample_rate", ctypes.c_double),
-                ("resample", ctypes.c_int32)]
+                ("resample", ctypes.c_int32), ("spectral_threads", ctypes.c_int32),
+                ("spectral_pass_scales", ctypes.c_int32), ("spectral_pruned", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

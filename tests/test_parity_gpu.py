@@ -103,6 +103,22 @@ def test_machine_batch64_sampled_rows(cw, sig):
         assert err <= TOL_FP32
 
 
+def test_pruned_inverse_ffts_several_scales_per_pass(cw, sig):
+    """Hop 1 on a short clip with narrow Morlet bands (200-2000 Hz): the plan
+    takes the pruned kernel (leading inverse-FFT passes skipped) with
+    several scales per pass, so each chunk's pruning bound comes from the
+    suffix maximum of its band widths.  Scales are given in descending order
+    to check that the plan's internal ascending order keeps every output
+    row in the caller's order."""
+    n, hop = 3000, 1
+    x = sig.tones_clip(7, n)
+    sc = sig.scales_for_band(200, 2000, 16, 16000.0)[::-1].copy()
+    got, info = run_gpu(cw, x, sc, hop)
+    assert info["spectral_pruned"] == 1 and info["spectral_pass_scales"] > 1, info
+    ref = oracle_mag(x, sc, hop)
+    assert rel_err(got[0], ref) <= TOL_FP32
+
+
 @pytest.mark.parametrize("hop", [1, 4, 8, 512, 1024])
 def test_machine_10s_sampled_scales(cw, sig, hop):
     """Full 10 s clips in the benchmark's 64-scale plan at hop 1 (the
