@@ -95,6 +95,26 @@ cwth_status cwth_plan(const cwth_morlet *w, const double *scales, int32_t S, int
                       int32_t path, cwth_plan_t *out);
 
 /*
+ * cwth_plan with the spectral path's FFT segment length M fixed instead of
+ * chosen by the plan's cost model (an autotuner's knob; results agree with
+ * any other segment length within the float32 tolerance: every valid
+ * segment gives the linear correlation of Eq. 1 at its frames).
+ *
+ *   seg_len   0: automatic (exactly cwth_plan); else a power of two M in
+ *             [512, 32768] with M / hop >= 8.
+ *
+ * Errors: those of cwth_plan; CWTH_ERR_INVALID_ARG for a seg_len that is
+ * negative or not a power of two in range; CWTH_ERR_UNSUPPORTED when the
+ * plan has spectral-path scales and M cannot serve them (M / hop < 8, the
+ * wavelet support leaves no valid frame, or the segment's shared-memory
+ * footprint exceeds a CTA's).
+ */
+cwth_status cwth_plan_segment(const cwth_morlet *w, const double *scales, int32_t S,
+                              int32_t hop, double sample_rate, int64_t max_len,
+                              int32_t precision, int32_t path, int32_t seg_len,
+                              cwth_plan_t *out);
+
+/*
  * Scalograms of a batch of clips, asynchronous on `stream`.
  *
  *   d_x       device, float32, clip i occupies d_x[i*ld_x .. i*ld_x + len_i).

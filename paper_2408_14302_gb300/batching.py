@@ -6,10 +6,11 @@ whose clips are packed into one padded device batch with a lengths vector,
 so a group runs as one `cwth_execute` (every kernel already honours per-clip
 lengths).  All groups' executes are captured into one CUDA graph, so a whole
 batch is a single host-side launch.  An autotuner times the candidate
-evaluations of each group once (float32 spectral path vs the automatic path
-at split-bf16 precision, both within 1e-5 of max|W|) and remembers the
-faster one in a JSON cache keyed by GPU, sample rate, scale count, hop and
-length bucket.
+evaluations of each group once (the float32 spectral path at the plan's own
+FFT segment length and at half and twice it, and the automatic path at
+split-bf16 precision, all within 1e-5 of max|W|) and remembers the fastest
+in a JSON cache keyed by GPU, sample rate, scale count, hop and length
+bucket.
 
 Python orchestration only: the transform runs in libcwth.so.
 """
@@ -37,7 +38,8 @@ def default_cache_path() -> str:
 
 
 class TuneCache:
-    """Persisted autotuning decisions: key -> {"path", "precision", "ms"}."""
+    """Persisted autotuning decisions: key -> {"path", "precision", "seg_len", "ms"}
+    (seg_len 0: the plan's own segment length)."""
 
     def __init__(self, path: str | None = None):
         self.path = path or default_cache_path()
@@ -118,33 +120,45 @@ class BatchRunner:
         self.stream = torch.cuda.Stream(self.device)
 
     # ------------------------------------------------------------ planning
-    def _plan(self, g, path, precision):
+    def _plan(self, g, path, precision, seg_len=0):
         gfs, S, hop = g["key"]
         return cwth.Plan(g["scales"], hop=hop, max_len=g["max_len"], bandwidth=self.bandwidth,
-                         center=self.center, sample_rate=gfs, precision=precision, path=path)
+                         center=self.center, sample_rate=gfs, precision=precision, path=path,
+                         seg_len=seg_len)
 
     def _choose(self, g, gpu):
+        """(path, precision, seg_len) of the group: cached, else the fastest
+        candidate; the spectral path also tries half and twice the segment
+        length its cost model picks."""
         gfs, S, hop = g["key"]
         key = f"{gpu}|{gfs:g}|{S}|{hop}|{length_bucket(g['max_len'])}|{self.accuracy}"
         if self.cache is not None:
             hit = self.cache.get(key)
             if hit:
-                return hit["path"], hit["precision"]
+                return hit["path"], hit["precision"], int(hit.get("seg_len", 0))
         best = None
         for path, prec in CANDIDATES[self.accuracy]:
-            try:
-                plan = self._plan(g, path, prec)
-            except cwth.CwthError:
-                continue
-            ms = self._time(plan, g)
-            plan.close()
-            if best is None or ms < best[2]:
-                best = (path, prec, ms)
+            segs = [0]
+            while segs:
+                seg = segs.pop(0)
+                try:
+                    plan = self._plan(g, path, prec, seg)
+                except cwth.CwthError:
+                    continue
+                info = plan.info()
+                if seg == 0 and path == "spectral" and info["seg_len"] > 0:
+                    segs = [m for m in (info["seg_len"] // 2, info["seg_len"] * 2)
+                            if 512 <= m <= 32768]
+                ms = self._time(plan, g)
+                plan.close()
+                if best is None or ms < best[3]:
+                    best = (path, prec, seg, ms)
         if best is None:
             raise cwth.CwthError(4, f"no evaluation serves group {g['key']}")
         if self.cache is not None:
-            self.cache.put(key, {"path": best[0], "precision": best[1], "ms": best[2]})
-        return best[0], best[1]
+            self.cache.put(key, {"path": best[0], "precision": best[1], "seg_len": best[2],
+                                 "ms": best[3]})
+        return best[0], best[1], best[2]
 
     def _time(self, plan, g, reps: int = 3) -> float:
         torch = self.torch

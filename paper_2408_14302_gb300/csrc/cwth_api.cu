@@ -157,6 +157,7 @@ bool choose_segment(const cwth_plan_s& p, const std::vector<double>& sp_scales, 
     bool found = false;
     for (int lg = 9; lg <= 15; ++lg) {
         const int64_t M = int64_t(1) << lg;
+        if (p.seg_force > 0 && M != p.seg_force) continue;
         if (M < 8 * (int64_t)hop) continue;
         const int64_t P = M / hop;
         if (M - 1 - h < 0) continue;
@@ -710,9 +711,32 @@ const char* cwth_status_string(cwth_status s) {
     return "CWTH_ERR_UNKNOWN";
 }
 
+namespace {
+cwth_status plan_create(const cwth_morlet* w, const double* scales, int32_t S, int32_t hop,
+                        double sample_rate, int64_t max_len, int32_t precision, int32_t path,
+                        int32_t seg_len, cwth_plan_t* out);
+}
+
 cwth_status cwth_plan(const cwth_morlet* w, const double* scales, int32_t S, int32_t hop,
                       double sample_rate, int64_t max_len, int32_t precision, int32_t path,
                       cwth_plan_t* out) {
+    return plan_create(w, scales, S, hop, sample_rate, max_len, precision, path, 0, out);
+}
+
+cwth_status cwth_plan_segment(const cwth_morlet* w, const double* scales, int32_t S,
+                              int32_t hop, double sample_rate, int64_t max_len,
+                              int32_t precision, int32_t path, int32_t seg_len,
+                              cwth_plan_t* out) {
+    if (out) *out = nullptr;
+    if (seg_len < 0 || (seg_len > 0 && (seg_len < 512 || seg_len > 32768 || !is_pow2(seg_len))))
+        return CWTH_ERR_INVALID_ARG;
+    return plan_create(w, scales, S, hop, sample_rate, max_len, precision, path, seg_len, out);
+}
+
+namespace {
+cwth_status plan_create(const cwth_morlet* w, const double* scales, int32_t S, int32_t hop,
+                        double sample_rate, int64_t max_len, int32_t precision, int32_t path,
+                        int32_t seg_len, cwth_plan_t* out) {
     if (out) *out = nullptr;
     if (!w || !scales || !out) return CWTH_ERR_INVALID_ARG;
     if (S < 1 || hop < 1 || max_len < 1) return CWTH_ERR_INVALID_ARG;
@@ -741,6 +765,7 @@ cwth_status cwth_plan(const cwth_morlet* w, const double* scales, int32_t S, int
         p->precision = precision;
         p->path = path;
         p->max_len = max_len;
+        p->seg_force = seg_len;
         p->frames_max = cwth_num_frames(max_len, hop);
         p->scales.assign(scales, scales + S);
         p->scale_path.assign(S, CWTH_PATH_SPECTRAL);
@@ -784,6 +809,8 @@ cwth_status cwth_plan(const cwth_morlet* w, const double* scales, int32_t S, int
     *out = p;
     return CWTH_OK;
 }
+
+}  // namespace
 
 cwth_status cwth_plan_resampled(const cwth_morlet* w, const double* scales, int32_t S, int32_t hop,
                                 double sample_rate, int64_t max_len, int32_t precision,

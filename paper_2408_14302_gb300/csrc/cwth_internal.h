@@ -190,6 +190,7 @@ struct cwth_plan_s {
     int32_t n_sp = 0;
     int32_t M = 0, P = 0, halo = 0, kp0 = 0, seg_frames = 0, n_seg = 0;
     bool spec_prune = false;  // narrow bands let inverse FFTs skip passes
+    int32_t seg_force = 0;    // segment length fixed by cwth_plan_segment (0: cost model)
     float2* d_tw = nullptr;
     cwth::SpecScale* d_sp = nullptr;
 

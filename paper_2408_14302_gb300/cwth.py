@@ -25,7 +25,8 @@ EXPORTS = ("cwth_plan", "cwth_execute", "cwth_execute_host", "cwth_destroy",
            "cwth_num_frames", "cwth_status_string", "cwth_plan_query",
            "cwth_plan_scale_paths", "cwth_sync", "cwth_last_error",
            "cwth_execute_direct_noalloc", "cwth_plan_set_host_chunks",
-           "cwth_selftest_wait_timeout", "cwth_measure_fp32_fma", "cwth_plan_resampled")
+           "cwth_selftest_wait_timeout", "cwth_measure_fp32_fma", "cwth_plan_resampled",
+           "cwth_plan_segment")
 
 
 class CwthError(RuntimeError):
@@ -66,6 +67,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.cwth_plan.restype = ctypes.c_int
     lib.cwth_plan_resampled.argtypes = lib.cwth_plan.argtypes
     lib.cwth_plan_resampled.restype = ctypes.c_int
+    lib.cwth_plan_segment.argtypes = lib.cwth_plan.argtypes[:8] + [i32, ctypes.POINTER(vp)]
+    lib.cwth_plan_segment.restype = ctypes.c_int
     lib.cwth_execute.argtypes = [vp, vp, i64, vp, i32, vp, vp]
     lib.cwth_execute.restype = ctypes.c_int
     lib.cwth_execute_host.argtypes = [vp, vp, i64, vp, i32, vp, vp]
@@ -154,11 +157,13 @@ class Plan:
     """A cwth_plan_t: scales (in samples), hop, Morlet B/C and the longest clip.
     ``resample_first=True`` makes a cwth_plan_resampled plan (the signal is
     re-sampled at the hop spacing, then transformed at every sample with
-    scales / hop); its inputs and output shape are the same."""
+    scales / hop); its inputs and output shape are the same.  ``seg_len`` > 0
+    fixes the spectral path's FFT segment length (cwth_plan_segment)."""
 
     def __init__(self, scales, hop: int, max_len: int, bandwidth: float = 1.5,
                  center: float = 1.0, sample_rate: float = 16000.0,
-                 precision: str = "fp32", path: str = "auto", resample_first: bool = False):
+                 precision: str = "fp32", path: str = "auto", resample_first: bool = False,
+                 seg_len: int = 0):
         sc = np.ascontiguousarray(np.asarray(scales, dtype=np.float64).ravel())
         self.scales = sc
         self.hop = int(hop)
@@ -166,11 +171,17 @@ class Plan:
         self.S = int(sc.shape[0])
         self._h = ctypes.c_void_p()
         w = Morlet(float(bandwidth), float(center))
-        make = _lib.cwth_plan_resampled if resample_first else _lib.cwth_plan
-        st = make(ctypes.byref(w), sc.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                  self.S, self.hop, float(sample_rate), self.max_len,
-                  PREC[precision], PATH[path], ctypes.byref(self._h))
-        _check(st, "cwth_plan_resampled" if resample_first else "cwth_plan")
+        args = (ctypes.byref(w), sc.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                self.S, self.hop, float(sample_rate), self.max_len, PREC[precision], PATH[path])
+        if resample_first:
+            if seg_len:
+                raise ValueError("seg_len applies to cwth_plan_segment plans only")
+            _check(_lib.cwth_plan_resampled(*args, ctypes.byref(self._h)), "cwth_plan_resampled")
+        elif seg_len:
+            _check(_lib.cwth_plan_segment(*args, int(seg_len), ctypes.byref(self._h)),
+                   "cwth_plan_segment")
+        else:
+            _check(_lib.cwth_plan(*args, ctypes.byref(self._h)), "cwth_plan")
         self.frames_max = num_frames(self.max_len, self.hop)
 
     @property

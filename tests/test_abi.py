@@ -85,6 +85,18 @@ def test_empty_scale_list_rejected(cw):
     assert lib.cwth_plan(ctypes.byref(w), sc, 0, 64, 16000.0, 100, 0, 0, ctypes.byref(h)) == 1
 
 
+def test_plan_segment_rejects_bad_segment_lengths(cw):
+    # Argument checks run before any device call, so no GPU is needed.
+    lib = cw.lib()
+    h = ctypes.c_void_p()
+    w = cw.Morlet(1.5, 1.0)
+    sc = (ctypes.c_double * 1)(2.0)
+    for seg in (-1, 256, 3000, 65536):
+        assert lib.cwth_plan_segment(ctypes.byref(w), sc, 1, 64, 16000.0, 100, 0, 0, seg,
+                                     ctypes.byref(h)) == 1, seg
+        assert not h.value
+
+
 def test_null_plan_handles(cw):
     lib = cw.lib()
     assert lib.cwth_destroy(None) == 0

@@ -47,10 +47,10 @@ def test_alone_equals_in_the_mix(batch):
     runner, clips, fs, ns, hs, _ = batch
     for i in (0, 5, 11):
         gi, _ = runner.where[i]
-        path, prec = runner.groups[gi]["choice"]
+        path, prec, seg = runner.groups[gi]["choice"]
         sc = signals.scales_for_band(50.0, 8000.0, ns[i], fs[i])
         with cwth.Plan(sc, hop=hs[i], max_len=len(clips[i]), sample_rate=fs[i], path=path,
-                       precision=prec) as p:
+                       precision=prec, seg_len=seg) as p:
             alone = p.execute(torch.from_numpy(np.asarray(clips[i], np.float32)).cuda())[0]
             alone = alone.cpu().numpy()
         mixed = runner.result(i)

@@ -103,6 +103,25 @@ def test_machine_batch64_sampled_rows(cw, sig):
         assert err <= TOL_FP32
 
 
+def test_forced_segment_lengths_agree(cw, sig):
+    """cwth_plan_segment: every valid segment length gives the oracle's
+    scalogram (each one evaluates the linear correlation of Eq. 1 at its
+    frames), and an unusable one is refused."""
+    n, hop = 20000, 64
+    x = sig.machine_clip(31, n)
+    sc = sig.scales_for_band(50, 8000, 24, 16000.0)
+    ref = oracle_mag(x, sc, hop)
+    xd = torch.from_numpy(np.asarray(x, np.float32)[None]).cuda()
+    for seg in (4096, 8192, 16384):
+        with cw.Plan(sc, hop=hop, max_len=n, path="spectral", seg_len=seg) as plan:
+            assert plan.info()["seg_len"] == seg
+            got = plan.execute(xd).cpu().numpy()[0].astype(np.float64)
+        assert rel_err(got, ref) <= TOL_FP32, seg
+    with pytest.raises(cw.CwthError):
+        # 512 samples hold no valid frame next to the 50 Hz wavelet's support
+        cw.Plan(sc, hop=hop, max_len=n, path="spectral", seg_len=512)
+
+
 def test_pruned_inverse_ffts_several_scales_per_pass(cw, sig):
     """Hop 1 on a short clip with narrow Morlet bands (200-2000 Hz): the plan
     takes the pruned kernel (leading inverse-FFT passes skipped) with
