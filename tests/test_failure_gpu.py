@@ -9,7 +9,6 @@ plan still produce the same scalograms afterwards.
 """
 from __future__ import annotations
 
-
 import numpy as np
 import pytest
 
