@@ -129,9 +129,3 @@ def cwth_resampled(x, scales, hop: int, **kw):
 def cwth_magnitude(x, scales, hop: int, **kw):
     """|W[s, k]| of one real signal, float64 (the scalogram)."""
     return np.abs(cwth(x, scales, hop, **kw))
-
-
-def cwth_batch_magnitude(xs, lengths, scales, hop: int, **kw):
-    """|W| for a batch: ``xs`` [B][>=len], returns a list of [S, F_i] arrays."""
-    return [cwth_magnitude(np.asarray(xs[i])[: int(lengths[i])], scales, hop, **kw)
-            for i in range(len(lengths))]
