@@ -1,8 +1,8 @@
 """Precision study: tones generator, 1 s at 16 kHz, 128 scales 100-8000 Hz,
 hops 64/128/256/512.  Each variant's max and RMS relative error against the
 float64 oracle (max|err|/max|W| and rms(err)/rms(W) over the clip) must meet
-its tolerance; the figures are written to gpurun_out/precision_study.json
-when that directory exists."""
+its tolerance; the figures are written to precision_study.json in the
+directory named by the CWTH_RESULTS_DIR environment variable, if set."""
 from __future__ import annotations
 
 import json
@@ -14,7 +14,6 @@ import pytest
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 VARIANTS = [("direct", "bf16", 2e-2), ("direct", "bf16x2", 1e-5), ("direct", "fp32", 1e-5),
             ("spectral", "fp32", 1e-5)]
 
@@ -39,7 +38,8 @@ def test_precision_study():
             rms = float(np.sqrt(np.mean(err ** 2)) / np.sqrt(np.mean(ref ** 2)))
             report[f"hop{hop}_{path}_{prec}"] = {"max_rel": mx, "rms_rel": rms, "tol": tol}
             assert mx <= tol, (hop, path, prec, mx)
-    out = os.path.join(ROOT, "gpurun_out")
-    if os.path.isdir(out):
+    out = os.environ.get("CWTH_RESULTS_DIR")
+    if out:
+        os.makedirs(out, exist_ok=True)
         with open(os.path.join(out, "precision_study.json"), "w") as f:
             json.dump(report, f, indent=1)
