@@ -4,7 +4,8 @@ b = k*H per Sec. II.B), not by the oracle's own code.
 
 * closed form: the response to exp(i 2 pi nu n) is exp(i 2 pi nu b) G_a(nu)
   with G_a(nu) = sqrt(a) sum_m exp(-pi^2 B (a(nu - m) - C)^2) (Poisson
-  summation of the sampled Gaussian-windowed wavelet);
+  summation of the sampled Gaussian-windowed wavelet), and the scalogram of
+  a real cosine is half the modulus of the two such terms at +nu and -nu;
 * hop semantics: CWTH(H) is the full transform CWTH(1) kept at every H-th
   sample, bitwise; delaying the input by one hop delays the frames by one,
   bitwise;
@@ -160,6 +161,21 @@ def fft_error(cwth_fn) -> float:
 
 def test_closed_form_complex_exponential(oracle_mod):
     assert closed_form_error(oracle_mod.cwth, oracle_mod.half_support) < 1e-12
+
+
+def test_closed_form_real_cosine_magnitude(oracle_mod):
+    # cos(2 pi nu n) = (e^{i 2 pi nu n} + e^{-i 2 pi nu n}) / 2, so at interior
+    # frames |W(b)| = |e^{i 2 pi nu b} G_a(nu) + e^{-i 2 pi nu b} G_a(-nu)| / 2:
+    # the scalogram itself (cwth_magnitude) against the two-term closed form.
+    n = 2000
+    t = np.arange(n, dtype=np.float64)
+    for a, nu in ((2.0, 0.3), (4.0, 0.25), (12.0, 0.08), (30.0, 0.02)):
+        h = oracle_mod.half_support(a, B)
+        mag = oracle_mod.cwth_magnitude(np.cos(2 * np.pi * nu * t), [a], 1)[0]
+        b = np.arange(h, n - h)
+        expect = np.abs(np.exp(2j * np.pi * nu * b) * poisson_G(a, nu)
+                        + np.exp(-2j * np.pi * nu * b) * poisson_G(a, -nu)) / 2
+        assert np.max(np.abs(mag[b] - expect)) <= 1e-12 * max(1.0, float(np.max(expect)))
 
 
 def test_alias_term_matters_at_small_scale():
