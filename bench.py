@@ -11,6 +11,7 @@ Prints ONE JSON line (rank 0).  `--impl reference` times the float64 CPU
 oracle instead (on rank 0 only; other ranks exit without work).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    python bench.py --profile-case [--path ... --hop ...]   (one workload, for ncu)
 """
 from __future__ import annotations
 
@@ -543,7 +544,63 @@ def run_ours(args, rank, world, local_rank):
     return line
 
 
+# ------------------------------------------------------------------ profiler driver
+def profile_case(argv):
+    """`bench.py --profile-case ...`: one workload executed repeatedly for a
+    profiler (ncu).  Builds the plan, runs --warmup executes, then --reps
+    executes, and prints the mean CUDA-event time per execute.  Inputs are
+    the seeded synthetic generators; results are not checked here (the
+    test-suite does that)."""
+    ap = argparse.ArgumentParser(prog="bench.py --profile-case")
+    ap.add_argument("--path", default="spectral", choices=["auto", "spectral", "direct"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "bf16x2"])
+    ap.add_argument("--signal", default="machine", choices=["machine", "tones"])
+    ap.add_argument("--clips", type=int, default=64)
+    ap.add_argument("--seconds", type=float, default=10.0)
+    ap.add_argument("--fs", type=float, default=16000.0)
+    ap.add_argument("--scales", type=int, default=64)
+    ap.add_argument("--f-lo", type=float, default=50.0)
+    ap.add_argument("--f-hi", type=float, default=8000.0)
+    ap.add_argument("--hop", type=int, default=256)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--reps", type=int, default=10)
+    a = ap.parse_args(argv)
+
+    import torch
+
+    from paper_2408_14302_gb300 import cwth
+
+    n = int(round(a.seconds * a.fs))
+    distinct = min(a.clips, 64)
+    if a.signal == "machine":
+        base = np.stack([signals.machine_clip(1000 + i, n, a.fs) for i in range(distinct)])
+    else:
+        base = np.stack([signals.tones_clip(seed=i, n=n, fs=a.fs) for i in range(distinct)])
+    xs = np.ascontiguousarray(np.resize(base.astype(np.float32), (a.clips, n)))
+    scales = signals.scales_for_band(a.f_lo, a.f_hi, a.scales, a.fs)
+    plan = cwth.Plan(scales, hop=a.hop, max_len=n, precision=a.precision, path=a.path,
+                     sample_rate=a.fs)
+    x = torch.from_numpy(xs).cuda()
+    out = torch.empty((a.clips, a.scales, plan.frames_max), device="cuda")
+    for _ in range(a.warmup):
+        plan.execute(x, out=out)
+    plan.sync()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(a.reps):
+        plan.execute(x, out=out)
+    t1.record()
+    plan.sync()
+    print(f"{a.path}/{a.precision} hop {a.hop} clips {a.clips}: "
+          f"{t0.elapsed_time(t1) / max(a.reps, 1):.4f} ms per execute; plan {plan.info()}")
+
+
 def main():
+    if "--profile-case" in sys.argv[1:]:
+        argv = [v for v in sys.argv[1:] if v != "--profile-case"]
+        profile_case(argv)
+        return
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)

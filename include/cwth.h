@@ -229,6 +229,8 @@ typedef struct {
                                   inverts together                             */
     int32_t spectral_pruned;   /* 1 if the inverse FFTs skip the leading passes
                                   that narrow Morlet bands leave trivial       */
+    int32_t num_fused;         /* of num_direct: short-support scales summed in
+                                  the time domain inside the spectral kernel   */
 } cwth_plan_info;
 
 /* Fill *info.  Errors: CWTH_ERR_BAD_PLAN, CWTH_ERR_INVALID_ARG (NULL info). */

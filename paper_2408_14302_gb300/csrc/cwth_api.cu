@@ -39,10 +39,11 @@ constexpr size_t kSmemPair = 113 * 1024;
 constexpr double kPassCost = 64000.0;
 
 // Scales one CTA folds and inverts together within `cap` bytes of shared
-// memory (at most `limit`).
-int nconc_within(int M, int P, int limit, size_t cap) {
+// memory (at most `limit`); fd_bytes is the fused time-domain phase's share
+// of the same buffer.
+int nconc_within(int M, int P, int limit, size_t cap, size_t fd_bytes) {
     int nconc = std::max(1, limit);
-    while (nconc > 1 && cwth::spectral_smem_bytes(M, P, nconc) > cap) --nconc;
+    while (nconc > 1 && cwth::spectral_smem_bytes(M, P, nconc, fd_bytes) > cap) --nconc;
     while (nconc > 1 && (int64_t)nconc * P > cwth::kMaxFftPoints) --nconc;
     return nconc;
 }
@@ -53,19 +54,44 @@ int nconc_within(int M, int P, int limit, size_t cap) {
 // CTA.  Measured on GB300, 64 x 10 s clips, 64 scales: the pair is faster
 // at hops 1, 4, 8, 16 and 64 (hop 4: 2.42 vs 2.68 ms, 1 vs 2 scales per
 // pass), slower only at hop 32 (0.480 vs 0.453 ms).
-int spectral_threads(int M, int P) {
-    return cwth::spectral_smem_bytes(M, P, 1) > kSmemPair ? cwth::kSpecThreadsSolo
-                                                          : cwth::kSpecThreadsPair;
+int spectral_threads(int M, int P, size_t fd_bytes) {
+    return cwth::spectral_smem_bytes(M, P, 1, fd_bytes) > kSmemPair ? cwth::kSpecThreadsSolo
+                                                                    : cwth::kSpecThreadsPair;
 }
 
 // Scales one spectral CTA folds and inverts together for a segment length
 // and CTA shape.
-int spectral_nconc(int M, int P, int limit, int threads) {
-    return nconc_within(M, P, limit, threads == cwth::kSpecThreadsSolo ? kSmemCap : kSmemPair);
+int spectral_nconc(int M, int P, int limit, int threads, size_t fd_bytes) {
+    return nconc_within(M, P, limit, threads == cwth::kSpecThreadsSolo ? kSmemCap : kSmemPair,
+                        fd_bytes);
 }
-constexpr int kNumSms = 152;
+
+// Internal path marker: a short-support scale summed in the time domain
+// inside the spectral kernel (reported as CWTH_PATH_DIRECT).
+constexpr int32_t kPathFused = 3;
+// Largest half support a fused scale may have (window rows 2h + 1).
+constexpr int kFdMaxHalf = 256;
+// Cost model, in the segment model's lane-operation units (a fold bin is
+// 12): one tap row of one table column for one frame lane of the fused
+// phase.  Measured on GB300: a fold bin issues about 5 instructions per
+// lane, a fused row of a two-column group about 6.75 (window load, tap
+// load, four FMAs, loop share), i.e. 3.4 per column.
+constexpr double kFdCost = 9.0;
 // Direct path: taps below this fraction of the wavelet peak are dropped.
 constexpr double kEpsDirect = 1e-9;
+
+// Streaming multiprocessors of a device (queried once per device).
+int num_sms(int dev) {
+    static int cache[64] = {0};
+    if (dev < 0 || dev >= 64) return 1;
+    if (cache[dev] == 0) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1)
+            n = 1;
+        cache[dev] = n;
+    }
+    return cache[dev];
+}
 // Largest padded tap count the direct path accepts.
 constexpr int kMaxDirectTaps = 4096;
 // Longest wait cwth_selftest_wait_timeout accepts: the kernels' own budget
@@ -139,21 +165,88 @@ bool spectral_prune_pays(const std::vector<SpecScale>& sc, int P, int threads) {
     return 10 * skipped >= (int64_t)sc.size() * (int64_t)rad.size();
 }
 
+// Whether the paired kernel's inverse FFTs take the radix-8 plan instead
+// of radix 16: a lane-operation model of mean thread work plus the busiest
+// thread's critical path (butterflies per thread rounded up), for one pass
+// over nc scales of period P.  With few points per thread, radix-16
+// butterflies leave most warps idle.  The radix-8 plan holds one radix-8
+// butterfly per thread (nc * P <= 8 * threads); pruned plans keep the
+// default (their skipped passes follow it); the switch needs a 10 % gain
+// in the model.
+bool inverse_fft_radix8(int P, int nc, int threads, bool prune) {
+    if (prune || threads != cwth::kSpecThreadsPair || (int64_t)nc * P > 8 * threads) return false;
+    auto cost = [](int R, bool tw) {
+        return R == 4 ? (tw ? 58.0 : 34.0) : R == 8 ? (tw ? 126.0 : 78.0) : (tw ? 340.0 : 212.0);
+    };
+    auto score = [&](const std::vector<int>& rad) {
+        double total = 0, crit = 0;
+        for (size_t i = 0; i < rad.size(); ++i) {
+            const double nb = (double)nc * P / rad[i];
+            const double c = cost(rad[i], i > 0);
+            total += nb * c;
+            crit += ceil(nb / threads) * c;
+        }
+        return total / threads + crit;
+    };
+    const double r16 = score(spectral_fft_radices(P, cwth::kSpecThreadsPair));
+    const double r8 = score(spectral_fft_radices(P, cwth::kSpecThreadsSolo));
+    return r16 > 1.1 * r8;
+}
+
 struct SegChoice {
-    int M = 0, P = 0, halo = 0, kp0 = 0, seg_frames = 0, n_seg = 0;
+    int M = 0, P = 0, halo = 0, kp0 = 0, seg_frames = 0, n_seg = 0, threads = 0;
     double cost = 0;
 };
 
-// Segment length for the spectral path: the power of two M (P = M/H >= 8,
+// Half support of a fused time-domain scale (taps below kEpsDirect of the
+// peak dropped, as on the direct path).
+int32_t fd_half_support(double a, double B) {
+    return (int32_t)ceil(a * sqrt(B * log(1.0 / kEpsDirect)));
+}
+
+// Tap groups of the fused scales, given their half supports in descending
+// order: consecutive runs of up to kFdMaxG scales sharing the first one's
+// tap range.  Fills off / hg / n / gp; rows are the indices into h_desc.
+std::vector<cwth::FdGroup> fd_make_groups(const std::vector<int32_t>& h_desc, int* taps_n,
+                                          int* hw, double* cost_rows) {
+    std::vector<cwth::FdGroup> g;
+    int off = 0;
+    *hw = 0;
+    *cost_rows = 0;
+    for (size_t i = 0; i < h_desc.size(); i += cwth::kFdMaxG) {
+        cwth::FdGroup q;
+        memset(&q, 0, sizeof(q));
+        q.n = (int32_t)std::min<size_t>(cwth::kFdMaxG, h_desc.size() - i);
+        q.gp = (q.n + 1) & ~1;
+        q.hg = h_desc[i];
+        q.off = off;
+        for (int j = 0; j < q.n; ++j) q.row[j] = (int32_t)(i + j);
+        off += (2 * q.hg + 1) * q.gp;
+        *hw = std::max(*hw, (int)q.hg);
+        *cost_rows += (double)(2 * q.hg + 1) * q.gp;
+        g.push_back(q);
+    }
+    *taps_n = off;
+    return g;
+}
+
+// Segment length for the spectral kernel: the power of two M (P = M/H >= 8,
 // shared memory within bounds) minimising a lane-operation cost model of
-// FFT + fold + inverse FFTs + stores per clip.
-bool choose_segment(const cwth_plan_s& p, const std::vector<double>& sp_scales, SegChoice* out) {
+// staging + FFT + fold + inverse FFTs + stores + the fused time-domain
+// phase per clip.  fd_h: half supports of the fused scales, descending.
+bool choose_segment(const cwth_plan_s& p, const std::vector<double>& sp_scales,
+                    const std::vector<int32_t>& fd_h, SegChoice* out) {
     double a_max = 0;
     for (double a : sp_scales) a_max = std::max(a_max, a);
     const int hop = p.hop;
-    const int64_t h = (int64_t)ceil(a_max * sqrt(p.B * log(1.0 / kEpsWrap)));
+    int fd_taps = 0, fd_hw = 0;
+    double fd_rows = 0;
+    if (!fd_h.empty()) fd_make_groups(fd_h, &fd_taps, &fd_hw, &fd_rows);
+    const int64_t h = std::max<int64_t>(
+        sp_scales.empty() ? 0 : (int64_t)ceil(a_max * sqrt(p.B * log(1.0 / kEpsWrap))), fd_hw);
     const int64_t halo = ((h + hop - 1) / hop) * hop;
     const int64_t kp0 = halo / hop;
+    const bool sp = !sp_scales.empty();
     bool found = false;
     for (int lg = 9; lg <= 15; ++lg) {
         const int64_t M = int64_t(1) << lg;
@@ -164,8 +257,10 @@ bool choose_segment(const cwth_plan_s& p, const std::vector<double>& sp_scales, 
         const int64_t last = (M - 1 - h) / hop;
         const int64_t Fseg = last - kp0 + 1;
         if (Fseg < 1) continue;
-        if (cwth::spectral_smem_bytes((int)M, (int)P, 1) > kSmemCap) continue;
-        const int threads = spectral_threads((int)M, (int)P);
+        const int fst = (int)(Fseg | 1);
+        const size_t fdb = cwth::spectral_fd_bytes(fd_taps, fd_hw, fst);
+        if (cwth::spectral_smem_bytes((int)M, (int)P, 1, fdb) > kSmemCap) continue;
+        const int threads = spectral_threads((int)M, (int)P, fdb);
         if (M / 2 > cwth::kMaxFftPoints || P > cwth::kMaxFftPoints) continue;
         const int64_t n_seg = (p.frames_max + Fseg - 1) / Fseg;
         double fold = 0;
@@ -174,12 +269,16 @@ bool choose_segment(const cwth_plan_s& p, const std::vector<double>& sp_scales, 
             band_limits(a, p.B, p.C, (int)M, &lo, &hi);
             fold += 12.0 * (double)(hi - lo + 1) + 4.0 * (double)P;
         }
-        const double fft = 2.5 * (double)(M / 2) * (lg - 1) + 8.0 * (double)M;
+        const double fft = sp ? 2.5 * (double)(M / 2) * (lg - 1) + 8.0 * (double)M : 2.0 * (double)M;
         const double ifft = 2.5 * (double)P * ilog2(P) * (double)sp_scales.size();
         const double store = 2.0 * (double)Fseg * (double)sp_scales.size();
-        const int nconc = spectral_nconc((int)M, (int)P, (int)sp_scales.size(), threads);
+        const int nconc = spectral_nconc((int)M, (int)P, std::max<int>(1, (int)sp_scales.size()),
+                                         threads, fdb);
         const double passes = (double)((sp_scales.size() + nconc - 1) / nconc);
-        const double cost = (double)n_seg * (fft + fold + ifft + store + kPassCost * passes);
+        const double fd = fd_h.empty() ? 0.0
+                                       : kFdCost * fd_rows * (double)((Fseg + 31) / 32 * 32) +
+                                             2.0 * (2.0 * fd_hw + 1) * (double)Fseg + kPassCost;
+        const double cost = (double)n_seg * (fft + fold + ifft + store + kPassCost * passes + fd);
         if (!found || cost < out->cost) {
             found = true;
             out->M = (int)M;
@@ -188,15 +287,49 @@ bool choose_segment(const cwth_plan_s& p, const std::vector<double>& sp_scales, 
             out->kp0 = (int)kp0;
             out->seg_frames = (int)Fseg;
             out->n_seg = (int)n_seg;
+            out->threads = threads;
             out->cost = cost;
         }
     }
     return found;
 }
 
+// CWTH_PATH_AUTO at float32 with a power-of-two hop: how many of the
+// smallest scales the spectral kernel sums in the time domain.  Every
+// prefix of the scales in ascending order whose supports stay within
+// kFdMaxHalf is costed with its best segment length; the cheapest wins.
+// A prefix whose window buffer would push the kernel from two CTAs per SM
+// to one is not taken (the model does not price the lost overlap).
+int choose_fused_count(const cwth_plan_s& p, const std::vector<int32_t>& asc) {
+    int best_n = 0, base_threads = 0;
+    double best = -1;
+    std::vector<double> sp;
+    std::vector<int32_t> fd;
+    for (size_t n = 0; n <= asc.size(); ++n) {
+        if (n > 0 && fd_half_support(p.scales[asc[n - 1]], p.B) > kFdMaxHalf) break;
+        sp.clear();
+        fd.clear();
+        for (size_t i = n; i < asc.size(); ++i) sp.push_back(p.scales[asc[i]]);
+        for (size_t i = n; i-- > 0;) fd.push_back(fd_half_support(p.scales[asc[i]], p.B));
+        SegChoice ch;
+        if (!choose_segment(p, sp, fd, &ch)) continue;
+        if (n == 0) base_threads = ch.threads;
+        if (base_threads > 0 && ch.threads > base_threads) continue;
+        if (best < 0 || ch.cost < best) {
+            best = ch.cost;
+            best_n = (int)n;
+        }
+    }
+    return best_n;
+}
+
 void free_plan_memory(cwth_plan_s* p) {
     cudaFree(p->d_tw);
     cudaFree(p->d_sp);
+    cudaFree(p->d_fd_taps);
+    cudaFree(p->d_fd_grp);
+    p->d_fd_taps = nullptr;
+    p->d_fd_grp = nullptr;
     cudaFree(p->d_stage_x);
     cudaFree(p->d_stage_out);
     cudaFree(p->d_stage_len);
@@ -324,6 +457,11 @@ bool encode_bf16_2d(CUtensorMap* map, const void* base, uint64_t inner, uint64_t
            CUDA_SUCCESS;
 }
 
+// Shared-memory bytes of a plan's fused time-domain phase (0 without one).
+size_t fd_bytes(const cwth_plan_s* p) {
+    return p->n_fd > 0 ? cwth::spectral_fd_bytes(p->fd_taps_n, p->fd_hw, p->fd_fst) : 0;
+}
+
 cwth_status build_direct(cwth_plan_s* p) {
     std::vector<int> idx;
     for (int s = 0; s < p->S; ++s)
@@ -441,10 +579,19 @@ cwth_status build_spectral(cwth_plan_s* p) {
         rows.push_back(s);
     }
     p->n_sp = (int32_t)sp.size();
-    if (p->n_sp == 0) return CWTH_OK;
+    // Fused time-domain scales, descending support (descending scale).
+    std::vector<int32_t> fd_idx;
+    for (int s = 0; s < p->S; ++s)
+        if (p->scale_path[s] == kPathFused) fd_idx.push_back(s);
+    std::stable_sort(fd_idx.begin(), fd_idx.end(),
+                     [&](int32_t i, int32_t j) { return p->scales[i] > p->scales[j]; });
+    std::vector<int32_t> fd_h;
+    for (int32_t s : fd_idx) fd_h.push_back(fd_half_support(p->scales[s], p->B));
+    p->n_fd = (int32_t)fd_idx.size();
+    if (p->n_sp == 0 && p->n_fd == 0) return CWTH_OK;
     if (!is_pow2(p->hop)) return CWTH_ERR_UNSUPPORTED;
     SegChoice ch;
-    if (!choose_segment(*p, sp, &ch)) return CWTH_ERR_UNSUPPORTED;
+    if (!choose_segment(*p, sp, fd_h, &ch)) return CWTH_ERR_UNSUPPORTED;
     p->M = ch.M;
     p->P = ch.P;
     p->halo = ch.halo;
@@ -471,9 +618,68 @@ cwth_status build_spectral(cwth_plan_s* p) {
     }
     for (size_t i = host.size(); i-- > 1;)
         host[i - 1].wsuf = std::max(host[i - 1].wsuf, host[i].wsuf);
-    p->spec_prune = spectral_prune_pays(host, p->P, spectral_threads(p->M, p->P));
+    cudaError_t e = cudaSuccess;
+    if (p->n_fd > 0) {
+        double rows = 0;
+        p->fd_groups = fd_make_groups(fd_h, &p->fd_taps_n, &p->fd_hw, &rows);
+        p->fd_fst = p->seg_frames | 1;
+        // Columns of group g are fused scales fd_idx[row[j]]: the generator
+        // reads their scale and support through gidx, the kernel writes
+        // output row fd_idx[...].
+        const int ng = (int)p->fd_groups.size();
+        std::vector<int32_t> gidx((size_t)ng * cwth::kFdMaxG, 0);
+        std::vector<double> fsc(fd_idx.size());
+        for (size_t i = 0; i < fd_idx.size(); ++i) fsc[i] = p->scales[fd_idx[i]];
+        for (int g = 0; g < ng; ++g)
+            for (int j = 0; j < p->fd_groups[g].n; ++j) {
+                const int i = p->fd_groups[g].row[j];
+                gidx[(size_t)g * cwth::kFdMaxG + j] = i;
+                p->fd_groups[g].row[j] = fd_idx[i];
+            }
+        double* d_sc = nullptr;
+        int32_t *d_h = nullptr, *d_gi = nullptr;
+        e = cudaMalloc(&p->d_fd_taps, sizeof(float2) * (size_t)p->fd_taps_n);
+        if (e == cudaSuccess) e = cudaMalloc(&p->d_fd_grp, sizeof(cwth::FdGroup) * (size_t)ng);
+        if (e == cudaSuccess) e = cudaMalloc(&d_sc, sizeof(double) * fsc.size());
+        if (e == cudaSuccess) e = cudaMalloc(&d_h, sizeof(int32_t) * fd_h.size());
+        if (e == cudaSuccess) e = cudaMalloc(&d_gi, sizeof(int32_t) * gidx.size());
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(p->d_fd_grp, p->fd_groups.data(), sizeof(cwth::FdGroup) * (size_t)ng,
+                                cudaMemcpyHostToDevice, p->setup);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d_sc, fsc.data(), sizeof(double) * fsc.size(),
+                                cudaMemcpyHostToDevice, p->setup);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d_h, fd_h.data(), sizeof(int32_t) * fd_h.size(),
+                                cudaMemcpyHostToDevice, p->setup);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d_gi, gidx.data(), sizeof(int32_t) * gidx.size(),
+                                cudaMemcpyHostToDevice, p->setup);
+        if (e == cudaSuccess)
+            e = cwth::spectral_make_fd_taps(d_sc, d_h, d_gi, p->d_fd_grp, ng, p->fd_taps_n, p->B,
+                                            p->C, p->d_fd_taps, p->setup);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(p->setup);
+        cudaFree(d_sc);
+        cudaFree(d_h);
+        cudaFree(d_gi);
+        if (e != cudaSuccess) return cuda_status(e);
+        p->table_bytes += (int64_t)(sizeof(float2) * (size_t)p->fd_taps_n +
+                                    sizeof(cwth::FdGroup) * (size_t)ng);
+    }
+    if (p->n_sp == 0) {
+        e = cwth::spectral_prepare_device();
+        if (e != cudaSuccess) return cuda_status(e);
+        return cuda_status(cudaStreamSynchronize(p->setup));
+    }
+    const int threads = spectral_threads(p->M, p->P, fd_bytes(p));
+    p->spec_prune = spectral_prune_pays(host, p->P, threads);
+    // Decided once per plan, for its largest pass, so that every launch (any
+    // scale grouping, any host chunk) runs the same inverse FFTs and gives
+    // the same bytes.
+    p->inv_r8 = inverse_fft_radix8(
+        p->P, spectral_nconc(p->M, p->P, p->n_sp, threads, fd_bytes(p)), threads, p->spec_prune);
     const size_t ntw = (size_t)cwth::spectral_twiddle_entries(p->M);
-    cudaError_t e = cudaMalloc(&p->d_tw, sizeof(float2) * ntw);
+    e = cudaMalloc(&p->d_tw, sizeof(float2) * ntw);
     if (e != cudaSuccess) return cuda_status(e);
     e = cudaMalloc(&p->d_sp, sizeof(SpecScale) * host.size());
     if (e != cudaSuccess) return cuda_status(e);
@@ -489,22 +695,30 @@ cwth_status build_spectral(cwth_plan_s* p) {
     return cuda_status(e);
 }
 
-cwth_status launch_spectral(const cwth_plan_s* p, const float* d_x, int64_t ld_x,
+cwth_status launch_spectral(cwth_plan_s* p, const float* d_x, int64_t ld_x,
                             const int64_t* d_len, int32_t batch, float* d_out, cudaStream_t st,
                             bool fill_gpu) {
-    if (p->n_sp == 0 || batch == 0) return CWTH_OK;
+    if ((p->n_sp == 0 && p->n_fd == 0) || batch == 0) return CWTH_OK;
     // Scale groups: enough CTAs for two waves, each group at least 8 scales
     // (every group repeats its segment's forward FFT).  A launch that shares
-    // the GPU with other chunks of the same batch keeps one group.
+    // the GPU with other chunks of the same batch keeps one group.  The
+    // fused time-domain tap groups are dealt round-robin over the scale
+    // groups.
     const int64_t base = (int64_t)p->n_seg * batch;
-    int n_groups = !fill_gpu ? 1
-                             : (int)std::min<int64_t>((2 * kNumSms + base - 1) / base,
-                                                      std::max(1, p->n_sp / 8));
-    n_groups = std::max(1, n_groups);
-    const int gs = (p->n_sp + n_groups - 1) / n_groups;
-    n_groups = (p->n_sp + gs - 1) / gs;
-    const int threads = spectral_threads(p->M, p->P);
-    const int nconc = spectral_nconc(p->M, p->P, gs, threads);
+    const int64_t want = (2 * (int64_t)num_sms(p->device) + base - 1) / base;
+    const int fdg = (int)p->fd_groups.size();
+    int n_groups = 1, gs = 0;
+    if (p->n_sp > 0) {
+        n_groups = !fill_gpu ? 1 : (int)std::min<int64_t>(want, std::max(1, p->n_sp / 8));
+        n_groups = std::max(1, n_groups);
+        gs = (p->n_sp + n_groups - 1) / n_groups;
+        n_groups = (p->n_sp + gs - 1) / gs;
+    } else {
+        n_groups = !fill_gpu ? 1 : (int)std::max<int64_t>(1, std::min<int64_t>(want, fdg));
+    }
+    const size_t fdb = fd_bytes(p);
+    const int threads = spectral_threads(p->M, p->P, fdb);
+    const int nconc = spectral_nconc(p->M, p->P, std::max(1, gs), threads, fdb);
     if (batch > 65535 || p->n_seg > 0x7fffffff) return CWTH_ERR_UNSUPPORTED;
 
     SpecLaunch L;
@@ -528,7 +742,18 @@ cwth_status launch_spectral(const cwth_plan_s* p, const float* d_x, int64_t ld_x
     L.kexp = (float)(-M_PI * M_PI * p->B / M_LN2);
     L.tw = p->d_tw;
     L.sc = p->d_sp;
-    const size_t smem = cwth::spectral_smem_bytes(p->M, p->P, nconc);
+    L.vec4 = (ld_x % 4 == 0 && ((uintptr_t)d_x & 15) == 0 && p->halo % 4 == 0 &&
+              ((int64_t)p->seg_frames * p->hop) % 4 == 0)
+                 ? 1
+                 : 0;
+    L.fd_groups = fdg;
+    L.fd_hw = p->fd_hw;
+    L.fd_fst = p->fd_fst;
+    L.fd_taps_n = p->fd_taps_n;
+    L.fd_taps = p->d_fd_taps;
+    L.fd_grp = p->d_fd_grp;
+    L.inv_r8 = p->inv_r8 ? 1 : 0;
+    const size_t smem = cwth::spectral_smem_bytes(p->M, p->P, nconc, fdb);
     return cuda_status(
         cwth::spectral_launch(L, threads, p->spec_prune, p->n_seg, batch, n_groups, smem, st));
 }
@@ -786,6 +1011,18 @@ cwth_status plan_create(const cwth_morlet* w, const double* scales, int32_t S, i
             else
                 p->scale_path[s] = choice;
         }
+        // Float32 automatic plans with a power-of-two hop: the cost model
+        // moves the short-support scales, whose hop fold would cost more
+        // than their direct sums, into the spectral kernel's time-domain
+        // phase.
+        if (st == CWTH_OK && path == CWTH_PATH_AUTO && precision == CWTH_PREC_FP32 && spectral_ok) {
+            std::vector<int32_t> asc(S);
+            for (int32_t s = 0; s < S; ++s) asc[s] = s;
+            std::stable_sort(asc.begin(), asc.end(),
+                             [&](int32_t i, int32_t j) { return scales[i] < scales[j]; });
+            const int nf = choose_fused_count(*p, asc);
+            for (int i = 0; i < nf; ++i) p->scale_path[asc[i]] = kPathFused;
+        }
         // Tables are made on a private non-blocking stream and only that
         // stream is waited for, so planning never stalls other work.
         if (st == CWTH_OK && cudaStreamCreateWithFlags(&p->setup, cudaStreamNonBlocking) != cudaSuccess)
@@ -962,7 +1199,8 @@ cwth_status cwth_plan_query(cwth_plan_t p, cwth_plan_info* info) {
     info->max_len = p->max_len;
     info->frames_max = p->frames_max;
     info->num_spectral = p->n_sp;
-    info->num_direct = p->n_dir;
+    info->num_direct = p->n_dir + p->n_fd;
+    info->num_fused = p->n_fd;
     info->seg_len = p->M;
     info->seg_frames = p->seg_frames;
     info->seg_halo = p->halo;
@@ -972,9 +1210,10 @@ cwth_status cwth_plan_query(cwth_plan_t p, cwth_plan_info* info) {
     info->table_bytes = p->table_bytes;
     info->sample_rate = p->fs;
     info->resample = p->resample;
-    if (p->n_sp > 0) {
-        info->spectral_threads = spectral_threads(p->M, p->P);
-        info->spectral_pass_scales = spectral_nconc(p->M, p->P, p->n_sp, info->spectral_threads);
+    if (p->n_sp > 0 || p->n_fd > 0) {
+        info->spectral_threads = spectral_threads(p->M, p->P, fd_bytes(p));
+        info->spectral_pass_scales =
+            p->n_sp > 0 ? spectral_nconc(p->M, p->P, p->n_sp, info->spectral_threads, fd_bytes(p)) : 0;
         info->spectral_pruned = p->spec_prune ? 1 : 0;
     }
     return CWTH_OK;
@@ -1015,7 +1254,8 @@ cwth_status cwth_selftest_wait_timeout(cwth_plan_t p, int64_t budget_cycles, voi
 cwth_status cwth_plan_scale_paths(cwth_plan_t p, int32_t* paths) {
     if (!valid_plan(p)) return CWTH_ERR_BAD_PLAN;
     if (!paths) return CWTH_ERR_INVALID_ARG;
-    for (int s = 0; s < p->S; ++s) paths[s] = p->scale_path[s];
+    for (int s = 0; s < p->S; ++s)
+        paths[s] = p->scale_path[s] == kPathFused ? CWTH_PATH_DIRECT : p->scale_path[s];
     return CWTH_OK;
 }
 

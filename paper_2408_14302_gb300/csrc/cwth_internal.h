@@ -51,6 +51,22 @@ struct SpecScale {
     int32_t wsuf;
 };
 
+// Short-support scales evaluated inside the spectral CTA as time-domain
+// sums over the segment's staged samples (Eq. 1 at the hop positions, taps
+// g[t] = a^{-1/2} conj(psi(t/a)) for |t| <= h): their Morlet bands are wide,
+// so folding them by the hop costs about H/a spectrum bins per frame, while
+// the direct sum costs 2h + 1 ~ 11 a taps per frame.  Scales are packed in
+// groups of up to kFdMaxG with a common tap range; one warp item is one
+// group over 32 consecutive frames of the segment.
+constexpr int kFdMaxG = 2;
+struct FdGroup {
+    int32_t off;   // first complex tap of the group's table (an even index)
+    int32_t hg;    // the group's half support: table rows tau = 0 .. 2 hg (t = tau - hg)
+    int32_t n;     // scales in the group, 1 .. kFdMaxG
+    int32_t gp;    // table row length: n rounded up to even (zero taps beyond n)
+    int32_t row[kFdMaxG];  // output row of each scale
+};
+
 struct SpecLaunch {
     const float* x;
     int64_t ld_x;
@@ -72,6 +88,17 @@ struct SpecLaunch {
     float kexp;        // -pi^2 B log2(e)
     const float2* tw;  // two-level table: exp(-2 pi i 128 i / M), i < M/128, then exp(-2 pi i j / M), j < 128
     const SpecScale* sc;
+    int32_t vec4;      // 1: x rows and segment starts are 16-byte aligned (float4 staging)
+    // fused time-domain scales (none when fd_groups == 0)
+    int32_t fd_groups;   // tap groups; scale group z of the grid takes groups z, z + nz, ...
+    int32_t fd_hw;       // half width of the frame windows: max hg over the groups
+    int32_t fd_fst;      // row stride (floats) of the window buffer, odd, >= seg_frames
+    int32_t fd_taps_n;   // complex taps of all group tables
+    const float2* fd_taps;   // group tables, [2 hg + 1][gp] complex each
+    const FdGroup* fd_grp;
+    // 1: the inverse FFTs of the 512-thread shape use the radix-8 plan (one
+    // radix-8 butterfly per thread: nc * P <= 4096), else radix 16
+    int32_t inv_r8;
 };
 
 // Direct (GEMM) path launch parameters; one launch per scale group.
@@ -117,7 +144,14 @@ struct DirShape {
 // Records the detail string cwth_last_error() returns in the calling thread.
 void set_last_error(const char* msg);
 
-size_t spectral_smem_bytes(int M, int P, int nconc);
+size_t spectral_smem_bytes(int M, int P, int nconc, size_t fd_bytes = 0);
+// Shared-memory bytes of the fused time-domain scales, held in the fold's
+// buffer before the fold: their tap tables (taps_n complex) and frame
+// windows ((2 hw + 1) rows of fst floats, plus slack).
+size_t spectral_fd_bytes(int taps_n, int hw, int fst);
+cudaError_t spectral_make_fd_taps(const double* d_scales, const int32_t* d_h, const int32_t* d_gidx,
+                                  const FdGroup* d_grp, int n_groups, int taps_n, double B,
+                                  double C, float2* d_taps, cudaStream_t st);
 int spectral_twiddle_entries(int M);
 cudaError_t spectral_prepare_device();
 cudaError_t spectral_make_twiddles(float2* d_tw, int M, cudaStream_t st);
@@ -190,9 +224,17 @@ struct cwth_plan_s {
     int32_t n_sp = 0;
     int32_t M = 0, P = 0, halo = 0, kp0 = 0, seg_frames = 0, n_seg = 0;
     bool spec_prune = false;  // narrow bands let inverse FFTs skip passes
+    bool inv_r8 = false;      // inverse FFTs on the radix-8 plan
     int32_t seg_force = 0;    // segment length fixed by cwth_plan_segment (0: cost model)
     float2* d_tw = nullptr;
     cwth::SpecScale* d_sp = nullptr;
+    // short-support scales summed in the time domain inside the spectral
+    // kernel (chosen by the cost model of CWTH_PATH_AUTO at float32)
+    int32_t n_fd = 0;
+    int32_t fd_hw = 0, fd_fst = 0, fd_taps_n = 0;
+    std::vector<cwth::FdGroup> fd_groups;
+    float2* d_fd_taps = nullptr;
+    cwth::FdGroup* d_fd_grp = nullptr;
 
     // direct path
     int32_t n_dir = 0;

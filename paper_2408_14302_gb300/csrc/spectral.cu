@@ -18,6 +18,10 @@
 //   a4  IFFT     length-P inverse FFT of every Z_s, |.|, store the valid
 //                frames of row s
 //
+// Short-support scales, whose bands span many hop aliases, skip a2-a4: the
+// plan's cost model hands them to a time-domain phase in the same CTA that
+// sums x[kH + t] g[t] over the staged samples (see fd_item below).
+//
 // The correlation taps g[t] = a^{-1/2} conj(psi(t/a)) have the real
 // spectrum sqrt(a) sum_m Psi(a(nu - m)) (Poisson summation of the sampled
 // Gaussian), so no complex multiplier is needed; bins q > M/2 come from
@@ -304,28 +308,31 @@ __device__ __forceinline__ void fft_pass_radix(int R, float2* buf, int L, int nb
 // PRUNE: every input is zero from index wmax on, so the leading passes
 // whose radices multiply to at most L / wmax (all but the last, at most)
 // are skipped and the next pass reads their result directly (see BC).
-template <bool INV, int PPT, bool PRUNE = false>
+// R8: the radix-8 plan (radix 8 with a leading 4 or 4, 4) whatever the
+// points per thread (PPT bounds only the butterflies a thread holds).
+template <bool INV, int PPT, bool PRUNE = false, bool R8 = false>
 __device__ __forceinline__ void fft_block(float2* buf, int L, int nbatch, const TwTab& tw, int ts,
                                           int wmax = 0) {
+    constexpr int PLAN = R8 ? 8 : PPT;
     const int e = __ffs(L) - 1;  // L >= 8: the plan keeps P = M/H >= 8 and M/2 >= 256
     int Ns = 1;
     if constexpr (PRUNE) {
-        const int npass = fft_npass<PPT>(e);
+        const int npass = fft_npass<PLAN>(e);
         int i = 0;
-        while (i + 1 < npass && (int64_t)wmax * Ns * fft_radix<PPT>(e, i) <= L)
-            Ns *= fft_radix<PPT>(e, i++);
+        while (i + 1 < npass && (int64_t)wmax * Ns * fft_radix<PLAN>(e, i) <= L)
+            Ns *= fft_radix<PLAN>(e, i++);
         if (i > 0) {
-            const int R = fft_radix<PPT>(e, i);
+            const int R = fft_radix<PLAN>(e, i);
             fft_pass_radix<INV, PPT, true>(R, buf, L, nbatch, Ns, tw, ts, false, i + 1 < npass);
             Ns *= R;
             ++i;
         }
         for (; i < npass; ++i) {
-            const int R = fft_radix<PPT>(e, i);
+            const int R = fft_radix<PLAN>(e, i);
             fft_pass_radix<INV, PPT, false>(R, buf, L, nbatch, Ns, tw, ts, i > 0, i + 1 < npass);
             Ns *= R;
         }
-    } else if constexpr (PPT >= 16) {
+    } else if constexpr (PLAN >= 16) {
         // The same plan as fft_radix, with the passes unrolled by kind
         // (measured faster than dispatching on the radix at run time).
         const int m = e & 3;
@@ -459,6 +466,137 @@ __device__ __forceinline__ float2 fold_residue(const float2* __restrict__ X, con
     return make_float2(sc.gscale * (ad.x + am.x), sc.gscale * (ad.y - am.y));
 }
 
+// Fused time-domain scales.  The window buffer Xw[tau][f] =
+// xs[halo + f H - hw + tau] (tau = 0 .. 2 hw, f < seg_frames, rows fst
+// floats apart, fst odd) is copied from the staged samples before the
+// forward FFT overwrites them: each warp reads consecutive samples and
+// writes a column with an odd stride, both free of bank conflicts.
+__device__ __forceinline__ void fd_copy_windows(const SpecLaunch& p, const float* __restrict__ xs,
+                                                float* __restrict__ Xw, float2* __restrict__ T) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    const int wlen = 2 * p.fd_hw + 1, fst = p.fd_fst, H = p.hop;
+    const float* src = xs + p.halo - p.fd_hw;
+    // Four rows chunks of 32 per step: loads first, then stores.
+    for (int f = warp; f < p.seg_frames; f += nwarps) {
+        const float* sf = src + f * H;
+        for (int t0 = lane; t0 < wlen; t0 += 128) {
+            float v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = t0 + 32 * u < wlen ? sf[t0 + 32 * u] : 0.f;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (t0 + 32 * u < wlen) Xw[(t0 + 32 * u) * fst + f] = v[u];
+        }
+    }
+    for (int i = threadIdx.x; i < p.fd_taps_n; i += blockDim.x) T[i] = __ldg(p.fd_taps + i);
+}
+
+// One fused item: the n scales of tap group g over the 32 frames
+// f = fb * 32 + lane of the segment, W[f] = sum_tau Xw[tau'][f] T[tau] with
+// tau' = tau + hw - hg and T[tau] the group's taps at t = tau - hg (zero
+// beyond each scale's own support).  Lanes read one window row per tap
+// (consecutive frames: conflict-free); every lane reads the same taps
+// (a broadcast through L1).  GP2 = gp / 2 float4 tap loads per row.
+template <int GP2>
+__device__ __forceinline__ void fd_sum(const float* __restrict__ xc, int fst,
+                                       const float4* __restrict__ tp, int ntau, float2* acc) {
+#pragma unroll
+    for (int j = 0; j < 2 * GP2; ++j) acc[j] = make_float2(0.f, 0.f);
+    int tau = 0;
+    // Four rows per step, every load of the step issued before its FMAs.
+    for (; tau + 4 <= ntau; tau += 4) {
+        float x[4];
+        float4 t[4][GP2];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            x[u] = xc[u * fst];
+#pragma unroll
+            for (int j = 0; j < GP2; ++j) t[u][j] = tp[u * GP2 + j];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int j = 0; j < GP2; ++j) {
+                acc[2 * j].x = fmaf(x[u], t[u][j].x, acc[2 * j].x);
+                acc[2 * j].y = fmaf(x[u], t[u][j].y, acc[2 * j].y);
+                acc[2 * j + 1].x = fmaf(x[u], t[u][j].z, acc[2 * j + 1].x);
+                acc[2 * j + 1].y = fmaf(x[u], t[u][j].w, acc[2 * j + 1].y);
+            }
+        xc += 4 * fst;
+        tp += 4 * GP2;
+    }
+    for (; tau < ntau; ++tau) {
+        const float x0 = xc[0];
+#pragma unroll
+        for (int j = 0; j < GP2; ++j) {
+            const float4 t0 = tp[j];
+            acc[2 * j].x = fmaf(x0, t0.x, acc[2 * j].x);
+            acc[2 * j].y = fmaf(x0, t0.y, acc[2 * j].y);
+            acc[2 * j + 1].x = fmaf(x0, t0.z, acc[2 * j + 1].x);
+            acc[2 * j + 1].y = fmaf(x0, t0.w, acc[2 * j + 1].y);
+        }
+        xc += fst;
+        tp += GP2;
+    }
+}
+
+__device__ __forceinline__ void fd_item(const SpecLaunch& p, const float* __restrict__ Xw,
+                                        const float2* __restrict__ T, int clip, int64_t k0,
+                                        int64_t F, int g, int fb) {
+    const int lane = threadIdx.x & 31;
+    const FdGroup gr = p.fd_grp[g];
+    const int Fs = p.seg_frames, fst = p.fd_fst;
+    const int f = fb * 32 + lane;
+    const int fc = f < Fs ? f : Fs - 1;  // idle lanes re-read a valid column
+    const float* xc = Xw + (p.fd_hw - gr.hg) * fst + fc;
+    const float4* tp = reinterpret_cast<const float4*>(T + gr.off);
+    const int ntau = 2 * gr.hg + 1;
+    float2 acc[kFdMaxG];
+    if (gr.gp <= 2)
+        fd_sum<1>(xc, fst, tp, ntau, acc);
+    else
+        fd_sum<2>(xc, fst, tp, ntau, acc);
+    const int64_t k = k0 + f;
+    if (f < Fs && k < F) {
+        float* o = p.out + (int64_t)clip * p.S_total * p.frames_max + k;
+#pragma unroll
+        for (int j = 0; j < kFdMaxG; ++j)
+            if (j < gr.n)
+                o[(int64_t)gr.row[j] * p.frames_max] =
+                    fast_sqrt(fmaf(acc[j].x, acc[j].x, acc[j].y * acc[j].y));
+    }
+}
+
+// Fused items of the CTA of scale group grp (of ngrp): tap groups grp,
+// grp + ngrp, ... times the frame blocks; item i is (group grp + (i / nfb)
+// ngrp, frame block i % nfb).
+struct FdWork {
+    const float* Xw;
+    const float2* T;
+    int clip, grp, ngrp, nfb, nitems;
+    int64_t k0, F;
+};
+
+__device__ __forceinline__ FdWork fd_work(const SpecLaunch& p, const float* Xw, const float2* T,
+                                          int clip, int64_t k0, int64_t F, int grp, int ngrp) {
+    FdWork w;
+    w.Xw = Xw;
+    w.T = T;
+    w.clip = clip;
+    w.grp = grp;
+    w.ngrp = ngrp;
+    w.nfb = (p.seg_frames + 31) >> 5;
+    w.nitems = grp < p.fd_groups ? ((p.fd_groups - grp + ngrp - 1) / ngrp) * w.nfb : 0;
+    w.k0 = k0;
+    w.F = F;
+    return w;
+}
+
+__device__ __forceinline__ void fd_run(const SpecLaunch& p, const FdWork& w, int i) {
+    const int q = i / w.nfb;
+    fd_item(p, w.Xw, w.T, w.clip, w.k0, w.F, w.grp + q * w.ngrp, i - q * w.nfb);
+}
+
 // a3 for one chunk of scales: band multiply + hop fold.  The chunk's
 // (scale, residue) pairs are numbered g = c P + r; one item = 32
 // consecutive g (32 residues of one scale, or 32 / P whole scales when
@@ -489,10 +627,33 @@ __device__ __forceinline__ void fold_items(const SpecLaunch& p, const float2* __
     }
 }
 
+// Clip length (clamped to [0, max_len]), frame count and first frame of the
+// CTA's segment.  reload: read the length again with a load the compiler
+// may not merge with an earlier one.
+__device__ __forceinline__ void cta_pos(const SpecLaunch& p, bool reload, int64_t* len, int64_t* F,
+                                        int64_t* k0) {
+    int64_t n = p.max_len;
+    if (p.lengths) {
+        const int64_t* a = p.lengths + blockIdx.y;
+        if (reload)
+            asm volatile("ld.global.nc.s64 %0, [%1];" : "=l"(n) : "l"(a));
+        else
+            n = __ldg(a);
+    }
+    n = n < 0 ? 0 : (n > p.max_len ? p.max_len : n);
+    *len = n;
+    *F = (n + p.hop - 1) / p.hop;
+    *k0 = (int64_t)blockIdx.x * p.seg_frames;
+}
+
+template <int THREADS, bool PRUNE>
+__device__ __forceinline__ void spectral_body(const SpecLaunch& p);
+
 // PRUNE: inverse FFTs skip the passes that a chunk's narrow bands leave
 // trivial (plans whose narrowest folded band fits a small fraction of P).
 template <int THREADS, bool PRUNE>
-__global__ void __launch_bounds__(THREADS, 1024 / THREADS) spectral_segment_kernel(const SpecLaunch p) {
+__global__ void __launch_bounds__(THREADS, THREADS >= 1024 ? 1 : 2)
+    spectral_segment_kernel(const SpecLaunch p) {
     constexpr int kPPT = kMaxFftPoints / THREADS;  // FFT points per thread
     extern __shared__ float2 smem[];
     const int M = p.M, Mh = M >> 1, P = p.P;
@@ -502,27 +663,115 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) spectral_segment_kern
     float2* Z = smem + ntw + Mh + 2;  // nconc * P used
     const TwTab tab{T, T + (M >> 7)};
 
-    const int seg = blockIdx.x, clip = blockIdx.y, grp = blockIdx.z;
-    int64_t len = p.lengths ? p.lengths[clip] : p.max_len;
-    len = len < 0 ? 0 : (len > p.max_len ? p.max_len : len);
-    const int64_t F = (len + p.hop - 1) / p.hop;
-    const int64_t k0 = (int64_t)seg * p.seg_frames;
-    const int sp_begin = grp * p.group_size;
-    if (k0 >= F || sp_begin >= p.n_sp) return;
-    const int sp_end = min(p.n_sp, sp_begin + p.group_size);
+    const int clip = blockIdx.y, grp = blockIdx.z;
+    int64_t len, F, k0;
+    cta_pos(p, false, &len, &F, &k0);
+    const bool has_sp = grp * p.group_size < p.n_sp;
+    const bool has_fd = grp < p.fd_groups;
+    if (k0 >= F || !(has_sp || has_fd)) return;
 
-    for (int i = threadIdx.x; i < ntw; i += blockDim.x) T[i] = __ldg(p.tw + i);
+    if (has_sp)
+        for (int i = threadIdx.x; i < ntw; i += blockDim.x) T[i] = __ldg(p.tw + i);
 
-    // a1: stage the segment as M/2 complex points.
+    // a1: stage the segment as M/2 complex points (x[s0 + i] is float i of X).
     const int64_t s0 = k0 * p.hop - p.halo;
     const float* xr = p.x + (int64_t)clip * p.ld_x;
-    for (int n = threadIdx.x; n < Mh; n += blockDim.x) {
-        const int64_t i0 = s0 + 2 * (int64_t)n;
-        const float a = (i0 >= 0 && i0 < len) ? __ldg(xr + i0) : 0.f;
-        const float b = (i0 + 1 >= 0 && i0 + 1 < len) ? __ldg(xr + i0 + 1) : 0.f;
-        X[n] = make_float2(a, b);
+    if (p.vec4 && s0 >= 0 && s0 + M <= len) {
+        // Interior segment: plain float4 copies, loads issued together.
+        float4* X4 = reinterpret_cast<float4*>(X);
+        const float4* x4 = reinterpret_cast<const float4*>(xr + s0);
+        const int n4 = M >> 2;
+        for (int base = threadIdx.x; base < n4; base += 4 * blockDim.x) {
+            float4 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int n = base + u * blockDim.x;
+                if (n < n4) v[u] = __ldg(x4 + n);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int n = base + u * blockDim.x;
+                if (n < n4) X4[n] = v[u];
+            }
+        }
+    } else if (p.vec4) {
+        // Four samples per load; the loads of a thread are issued together.
+        float4* X4 = reinterpret_cast<float4*>(X);
+        const int n4 = M >> 2;
+        for (int base = threadIdx.x; base < n4; base += 4 * blockDim.x) {
+            float4 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int n = base + u * blockDim.x;
+                const int64_t i0 = s0 + 4 * (int64_t)n;
+                if (n < n4 && i0 >= 0 && i0 + 3 < len) {
+                    v[u] = __ldg(reinterpret_cast<const float4*>(xr + i0));
+                } else {
+                    float e[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        e[q] = (n < n4 && i0 + q >= 0 && i0 + q < len) ? __ldg(xr + i0 + q) : 0.f;
+                    v[u] = make_float4(e[0], e[1], e[2], e[3]);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int n = base + u * blockDim.x;
+                if (n < n4) X4[n] = v[u];
+            }
+        }
+    } else {
+        for (int n = threadIdx.x; n < Mh; n += blockDim.x) {
+            const int64_t i0 = s0 + 2 * (int64_t)n;
+            const float a = (i0 >= 0 && i0 < len) ? __ldg(xr + i0) : 0.f;
+            const float b = (i0 + 1 >= 0 && i0 + 1 < len) ? __ldg(xr + i0 + 1) : 0.f;
+            X[n] = make_float2(a, b);
+        }
     }
     __syncthreads();
+
+    // Short-support scales: their frame windows leave X for a buffer of
+    // their own (after the fold's) before the forward FFT overwrites X; the
+    // FFT's first pass writes only after a barrier that follows this copy.
+    // Their sums run as items of the first fold phase (or here, alone, when
+    // the CTA has no spectral scales).
+    if (has_fd) {
+        // Fused time-domain scales: taps and frame windows in the fold's
+        // buffer (unused until the fold), items dealt to whichever warp is
+        // free (a shared counter, largest groups first).
+        float2* Tfd = Z;
+        float* Xw = reinterpret_cast<float*>(Tfd + p.fd_taps_n);
+        __shared__ int s_ctr;
+        if (threadIdx.x == 0) s_ctr = 0;
+        fd_copy_windows(p, reinterpret_cast<const float*>(X), Xw, Tfd);
+        __syncthreads();
+        const FdWork fw = fd_work(p, Xw, Tfd, clip, k0, F, grp, gridDim.z);
+        const int lane = threadIdx.x & 31;
+        for (;;) {
+            int it = 0;
+            if (lane == 0) it = atomicAdd(&s_ctr, 1);
+            it = __shfl_sync(0xffffffffu, it, 0);
+            if (it >= fw.nitems) break;
+            fd_run(p, fw, it);
+        }
+        __syncthreads();
+    }
+    if (!has_sp) return;
+    spectral_body<THREADS, PRUNE>(p);
+}
+
+// Everything from the forward FFT on.  Its per-CTA values are derived again
+// from the launch parameters (the clip length reloaded), so that none of
+// them occupies a register through the FFT passes.
+template <int THREADS, bool PRUNE>
+__device__ __forceinline__ void spectral_body(const SpecLaunch& p) {
+    constexpr int kPPT = kMaxFftPoints / THREADS;  // FFT points per thread
+    extern __shared__ float2 smem[];
+    const int M = p.M, Mh = M >> 1;
+    const int ntw = (M >> 7) + 128;
+    float2* T = smem;
+    float2* X = smem + ntw;
+    const TwTab tab{T, T + (M >> 7)};
 
     // a2: forward FFT of the M/2 points, twiddles exp(-2 pi i m/(M/2)) = tw[2m].
     fft_block<false, kPPT>(X, Mh, 1, tab, 2);
@@ -545,6 +794,13 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) spectral_segment_kern
     }
     __syncthreads();
 
+    const int P = p.P;
+    float2* Z = smem + ntw + Mh + 2;
+    const int clip = blockIdx.y, grp = blockIdx.z;
+    int64_t len, F, k0;
+    cta_pos(p, true, &len, &F, &k0);
+    const int sp_begin = grp * p.group_size;
+    const int sp_end = min(p.n_sp, sp_begin + p.group_size);
     const int lgP = __ffs(P) - 1;
     for (int c0 = sp_begin; c0 < sp_end; c0 += p.nconc) {
         const int nc = min(p.nconc, sp_end - c0);
@@ -567,7 +823,12 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) spectral_segment_kern
         // normalisation is already in gscale.  exp(+2 pi i m/P) = conj(tw[m H]).
         // With PRUNE every band of the chunk lies in its first sc[c0].wsuf
         // residues.
-        fft_block<true, kPPT, PRUNE>(Z, P, nc, tab, p.hop, PRUNE ? p.sc[c0].wsuf : 0);
+        // Few points per thread: the radix-8 plan (radix 8 with a leading 4
+        // or 4, 4) keeps more warps busy than radix-16 butterflies would.
+        if (!PRUNE && kPPT > 8 && p.inv_r8)
+            fft_block<true, 8>(Z, P, nc, tab, p.hop);
+        else
+            fft_block<true, kPPT, PRUNE>(Z, P, nc, tab, p.hop, PRUNE ? p.sc[c0].wsuf : 0);
 
         // Stores.  i < 2^24, so the float quotient is off by at most one
         // and one correction step gives c = i / Fs exactly.
@@ -608,10 +869,55 @@ __global__ void twiddle_kernel(float2* tw, int M) {
     }
 }
 
+// Tap tables of the fused time-domain scales, float64 then rounded once:
+// table g, row tau, column j holds g_j[t] = a^{-1/2} conj(psi(t / a)) =
+// a^{-1/2} (pi B)^{-1/2} exp(-(t/a)^2 / B) exp(-2 pi i C t / a) at
+// t = tau - hg for |t| <= h_j, zero elsewhere and in padding columns.
+// gidx[g * kFdMaxG + j] is the fused-scale index of column j.
+__global__ void fd_taps_kernel(const double* __restrict__ scales, const int32_t* __restrict__ h_of,
+                               const int32_t* __restrict__ gidx, const FdGroup* __restrict__ grp,
+                               double B, double C, float2* __restrict__ taps) {
+    const FdGroup g = grp[blockIdx.x];
+    const int n = (2 * g.hg + 1) * g.gp;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int tau = i / g.gp, j = i - tau * g.gp;
+        const int t = tau - g.hg;
+        float2 v = make_float2(0.f, 0.f);
+        if (j < g.n) {
+            const int s = gidx[blockIdx.x * kFdMaxG + j];
+            if (t >= -h_of[s] && t <= h_of[s]) {
+                const double a = scales[s];
+                const double u = (double)t / a;
+                const double env = exp(-(u * u) / B) / sqrt(a * M_PI * B);
+                double sn, cs;
+                sincospi(2.0 * C * u, &sn, &cs);
+                v = make_float2((float)(env * cs), (float)(-env * sn));
+            }
+        }
+        taps[g.off + i] = v;
+    }
+}
+
 }  // namespace
 
-size_t spectral_smem_bytes(int M, int P, int nconc) {
-    return (size_t)(spectral_twiddle_entries(M) + M / 2 + 2 + (long)nconc * P) * sizeof(float2);
+size_t spectral_smem_bytes(int M, int P, int nconc, size_t fd_bytes) {
+    const size_t z = std::max((size_t)nconc * P * sizeof(float2), fd_bytes);
+    return (size_t)(spectral_twiddle_entries(M) + M / 2 + 2) * sizeof(float2) + z;
+}
+
+size_t spectral_fd_bytes(int taps_n, int hw, int fst) {
+    if (taps_n <= 0) return 0;
+    return (size_t)taps_n * sizeof(float2) +
+           (((size_t)(2 * hw + 1) * fst + 4) * sizeof(float) + 15) / 16 * 16;
+}
+
+cudaError_t spectral_make_fd_taps(const double* d_scales, const int32_t* d_h, const int32_t* d_gidx,
+                                  const FdGroup* d_grp, int n_groups, int taps_n, double B,
+                                  double C, float2* d_taps, cudaStream_t st) {
+    if (n_groups <= 0) return cudaSuccess;
+    (void)taps_n;
+    fd_taps_kernel<<<n_groups, 256, 0, st>>>(d_scales, d_h, d_gidx, d_grp, B, C, d_taps);
+    return cudaGetLastError();
 }
 
 int spectral_twiddle_entries(int M) { return (M >> 7) + 128; }

@@ -265,6 +265,50 @@ def test_deterministic(cw, sig):
         assert torch.equal(a, b)
 
 
+def test_cost_model_split_fused_scales(cw, sig):
+    """Automatic float32 plans: the cost model sends the short-support
+    scales (wide Morlet bands, whose hop fold costs about H/a bins per
+    frame) to the spectral kernel's time-domain phase.  The fused scales are
+    the smallest ones; the result matches the oracle, including ragged
+    lengths, and so does the all-spectral plan of the same scales."""
+    n, hop = 40000, 256
+    lengths = [40000, 39999, 257, 0, 30001]
+    xs = np.stack([sig.machine_clip(400 + i, n) for i in range(len(lengths))])
+    sc = sig.scales_for_band(50, 8000, 64, 16000.0)
+    got, info = run_gpu(cw, xs, sc, hop, lengths=lengths, fill=-3.0)
+    assert info["num_fused"] > 0 and info["num_spectral"] > 0, info
+    assert info["num_direct"] == info["num_fused"]
+    with cw.Plan(sc, hop=hop, max_len=n) as p:
+        paths = p.scale_paths()
+    fused = paths == 2
+    assert fused.sum() == info["num_fused"] and sc[fused].max() < sc[~fused].min()
+    spec, info2 = run_gpu(cw, xs, sc, hop, lengths=lengths, path="spectral", fill=-3.0)
+    assert info2["num_fused"] == 0 and info2["num_spectral"] == 64
+    for i, L in enumerate(lengths):
+        F = -(-L // hop)
+        assert np.all(got[i, :, F:] == -3.0) and np.all(spec[i, :, F:] == -3.0)
+        if L == 0:
+            continue
+        ref = oracle_mag(xs[i, :L], sc, hop)
+        assert rel_err(got[i, :, :F], ref) <= TOL_FP32, (i, L)
+        assert rel_err(spec[i, :, :F], ref) <= TOL_FP32, (i, L)
+
+
+@pytest.mark.parametrize("hop", [128, 1024])
+def test_all_scales_fused(cw, sig, hop):
+    """High-frequency scales only, at large hops: every scale is cheaper as
+    a direct sum, so the spectral kernel runs its time-domain phase alone
+    (no FFT)."""
+    n = 30000
+    xs = np.stack([sig.machine_clip(77 + i, n) for i in range(2)])
+    sc = sig.scales_for_band(2500, 8000, 12, 16000.0)
+    got, info = run_gpu(cw, xs, sc, hop)
+    assert info["num_fused"] == 12 and info["num_spectral"] == 0, info
+    for i in range(2):
+        ref = oracle_mag(xs[i], sc, hop)
+        assert rel_err(got[i], ref) <= TOL_FP32
+
+
 def test_unsupported_hop_for_spectral(cw):
     with pytest.raises(cw.CwthError) as e:
         cw.Plan([2.0, 5.0], hop=100, max_len=1000, path="spectral")
