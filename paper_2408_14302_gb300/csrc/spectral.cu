@@ -303,6 +303,114 @@ __device__ __forceinline__ void fft_pass_radix(int R, float2* buf, int L, int nb
     }
 }
 
+// The forward FFT's pass sequence unrolled at compile time for each
+// transform length: every pass's radix, stride, butterflies per thread and
+// layouts are constants, and no run-time pass loop holds registers across
+// passes (the run-time loop spills under the 64-register bound of the
+// paired shape; each pass alone does not).  Same plans as fft_radix.
+__host__ __device__ constexpr int ct_npass(int ppt, int e) {
+    return ppt >= 16 ? ((e & 3) == 3 || (e & 3) == 1 ? 1 : 0) + ((e & 3) == 2 || (e & 3) == 1 ? 1 : 0) +
+                           (e - 3 * ((e & 3) == 3 || (e & 3) == 1 ? 1 : 0) -
+                            2 * ((e & 3) == 2 || (e & 3) == 1 ? 1 : 0)) / 4
+                     : (e % 3 == 1 ? 2 : e % 3 == 2 ? 1 : 0) +
+                           (e - 2 * (e % 3 == 1 ? 2 : e % 3 == 2 ? 1 : 0)) / 3;
+}
+__host__ __device__ constexpr int ct_radix(int ppt, int e, int i) {
+    return ppt >= 16 ? (i < ((e & 3) == 3 || (e & 3) == 1 ? 1 : 0)
+                            ? 8
+                            : (i < ((e & 3) == 3 || (e & 3) == 1 ? 1 : 0) +
+                                       ((e & 3) == 2 || (e & 3) == 1 ? 1 : 0)
+                                   ? 4
+                                   : 16))
+                     : (i < (e % 3 == 1 ? 2 : e % 3 == 2 ? 1 : 0) ? 4 : 8);
+}
+
+// PLAN: 16 (radix 16 with a leading 8, 4 or 8, 4) or 8 (radix 8 with a
+// leading 4 or 4, 4); CAP: points a thread may hold (butterflies per thread
+// of a pass <= CAP / R, the caller keeps nbatch * 2^LG <= CAP * THREADS).
+// PRUNE: passes before i0 are skipped and pass i0 reads their result in
+// place (see fft_pass's BC).
+template <bool INV, int PLAN, int CAP, int LG, bool PRUNE, int I = 0, int NS = 1>
+__device__ __forceinline__ void fft_ct(float2* buf, int nbatch, const TwTab& tw, int ts, int i0) {
+    constexpr int NP = ct_npass(PLAN, LG);
+    if constexpr (I < NP) {
+        constexpr int R = ct_radix(PLAN, LG, I);
+        constexpr int L = 1 << LG;
+        constexpr int MAXB = CAP / R > 0 ? CAP / R : 1;
+        constexpr int TS = L / (NS * R);
+        if (!PRUNE || I >= i0) {
+            if (PRUNE && I > 0 && I == i0)
+                fft_pass<R, MAXB, INV, true>(buf, L, nbatch, NS, tw, ts * TS, false, I + 1 < NP);
+            else
+                fft_pass<R, MAXB, INV, false>(buf, L, nbatch, NS, tw, ts * TS, I > 0, I + 1 < NP);
+        }
+        fft_ct<INV, PLAN, CAP, LG, PRUNE, I + 1, NS * R>(buf, nbatch, tw, ts, i0);
+    }
+}
+
+// Leading passes a pruned transform skips: those whose radices multiply to
+// at most L / wmax, never the last (every input is zero from wmax on).
+template <int PLAN>
+__device__ __forceinline__ int fft_skip(int lg, int wmax) {
+    const int np = ct_npass(PLAN, lg);
+    int i = 0, ns = 1;
+    while (i + 1 < np && (int64_t)wmax * ns * ct_radix(PLAN, lg, i) <= (1 << lg))
+        ns *= ct_radix(PLAN, lg, i++);
+    return i;
+}
+
+// One transform of M / 2 = 2^8 .. 2^13 points (the forward FFT), its pass
+// sequence unrolled at compile time for each length.
+template <bool INV, int THREADS>
+__device__ __forceinline__ void fft_one(float2* buf, int L, const TwTab& tw, int ts) {
+    constexpr int PPT = kMaxFftPoints / THREADS;
+    switch (__ffs(L) - 1) {
+        case 8: fft_ct<INV, PPT, PPT, 8, false>(buf, 1, tw, ts, 0); break;
+        case 9: fft_ct<INV, PPT, PPT, 9, false>(buf, 1, tw, ts, 0); break;
+        case 10: fft_ct<INV, PPT, PPT, 10, false>(buf, 1, tw, ts, 0); break;
+        case 11: fft_ct<INV, PPT, PPT, 11, false>(buf, 1, tw, ts, 0); break;
+        case 12: fft_ct<INV, PPT, PPT, 12, false>(buf, 1, tw, ts, 0); break;
+        default: fft_ct<INV, PPT, PPT, 13, false>(buf, 1, tw, ts, 0); break;
+    }
+}
+
+// nbatch transforms of L points with a run-time pass loop (compact: one
+// pass body per radix, each holding CAP / R butterflies per thread).
+template <bool INV, int PLAN, int CAP, bool PRUNE = false>
+__device__ __forceinline__ void fft_many(float2* buf, int L, int nbatch, const TwTab& tw, int ts,
+                                         int wmax = 0) {
+    const int lg = __ffs(L) - 1;
+    const int np = ct_npass(PLAN, lg);
+    int i = PRUNE ? fft_skip<PLAN>(lg, wmax) : 0;
+    int Ns = 1;
+    for (int k = 0; k < i; ++k) Ns *= ct_radix(PLAN, lg, k);
+    const bool bc = PRUNE && i > 0;
+    for (; i < np; ++i) {
+        const int R = ct_radix(PLAN, lg, i);
+        const bool rs = i > 0, ws = i + 1 < np;
+        const bool first_bc = bc && Ns > 1 && i == fft_skip<PLAN>(lg, wmax);
+        if (R == 4) {
+            if (first_bc)
+                fft_pass<4, CAP / 4, INV, true>(buf, L, nbatch, Ns, tw, ts * (L / (Ns * 4)), false, ws);
+            else
+                fft_pass<4, CAP / 4, INV, false>(buf, L, nbatch, Ns, tw, ts * (L / (Ns * 4)), rs, ws);
+        } else if (R == 8) {
+            if (first_bc)
+                fft_pass<8, CAP / 8, INV, true>(buf, L, nbatch, Ns, tw, ts * (L / (Ns * 8)), false, ws);
+            else
+                fft_pass<8, CAP / 8, INV, false>(buf, L, nbatch, Ns, tw, ts * (L / (Ns * 8)), rs, ws);
+        } else if constexpr (PLAN >= 16) {
+            if (first_bc)
+                fft_pass<16, CAP / 16, INV, true>(buf, L, nbatch, Ns, tw, ts * (L / (Ns * 16)), false,
+                                                  ws);
+            else
+                fft_pass<16, CAP / 16, INV, false>(buf, L, nbatch, Ns, tw, ts * (L / (Ns * 16)), rs,
+                                                   ws);
+        }
+        Ns *= R;
+    }
+}
+
 // Batched power-of-two FFT in shared memory, natural order in and out.
 // ts = M / L maps the transform's twiddles onto the table of exp(-2 pi i m/M).
 // PRUNE: every input is zero from index wmax on, so the leading passes
@@ -774,7 +882,7 @@ __device__ __forceinline__ void spectral_body(const SpecLaunch& p) {
     const TwTab tab{T, T + (M >> 7)};
 
     // a2: forward FFT of the M/2 points, twiddles exp(-2 pi i m/(M/2)) = tw[2m].
-    fft_block<false, kPPT>(X, Mh, 1, tab, 2);
+    fft_one<false, THREADS>(X, Mh, tab, 2);
 
     // Real-input split: with Z = FFT(z), E = (Z[q] + conj Z[Mh-q])/2 and
     // O = (Z[q] - conj Z[Mh-q])/(2i) are the spectra of the even and odd
@@ -826,9 +934,9 @@ __device__ __forceinline__ void spectral_body(const SpecLaunch& p) {
         // Few points per thread: the radix-8 plan (radix 8 with a leading 4
         // or 4, 4) keeps more warps busy than radix-16 butterflies would.
         if (!PRUNE && kPPT > 8 && p.inv_r8)
-            fft_block<true, 8>(Z, P, nc, tab, p.hop);
+            fft_many<true, 8, 8>(Z, P, nc, tab, p.hop);
         else
-            fft_block<true, kPPT, PRUNE>(Z, P, nc, tab, p.hop, PRUNE ? p.sc[c0].wsuf : 0);
+            fft_many<true, kPPT, kPPT, PRUNE>(Z, P, nc, tab, p.hop, PRUNE ? p.sc[c0].wsuf : 0);
 
         // Stores.  i < 2^24, so the float quotient is off by at most one
         // and one correction step gives c = i / Fs exactly.
