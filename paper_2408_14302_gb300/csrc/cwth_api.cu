@@ -618,6 +618,21 @@ cwth_status build_spectral(cwth_plan_s* p) {
     }
     for (size_t i = host.size(); i-- > 1;)
         host[i - 1].wsuf = std::max(host[i - 1].wsuf, host[i].wsuf);
+    // Fold pairs: scales 2j and 2j + 1 of the table (whose bands nest when
+    // their ratio is near 1) share a walk over the union of their bands when
+    // both weights stay >= 1e-20 on it (the Gaussian's minimum over the
+    // union is at one of its ends).
+    for (size_t i = 0; i + 1 < host.size(); i += 2) {
+        const int64_t lo = std::min(host[i].q_lo, host[i + 1].q_lo);
+        const int64_t hi = std::max(host[i].q_hi, host[i + 1].q_hi);
+        bool ok = true;
+        for (size_t k = i; k <= i + 1; ++k)
+            for (int64_t q : {lo, hi}) {
+                const double u = (double)q * sp[k] / (double)p->M - p->C;
+                if (-M_PI * M_PI * p->B * u * u < log(1e-20)) ok = false;
+            }
+        host[i].pair = ok ? 1 : 0;
+    }
     cudaError_t e = cudaSuccess;
     if (p->n_fd > 0) {
         double rows = 0;

@@ -49,6 +49,10 @@ struct SpecScale {
     // any chunk of scales starting here fits in wsuf residues once shifted
     // to start at residue 0.
     int32_t wsuf;
+    // 1: this scale and the next one of the table share one fold walk over
+    // the union of their bands (both weights stay above 1e-20 there, so the
+    // weight recurrence cannot lose either to underflow)
+    int32_t pair;
 };
 
 // Short-support scales evaluated inside the spectral CTA as time-domain

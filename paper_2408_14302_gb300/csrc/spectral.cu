@@ -491,87 +491,118 @@ __device__ __forceinline__ float fast_sqrt(float x) {
     return y;
 }
 
-// Sum of X[q] * exp2(kexp * (qf * a_over_m - C)^2) over n bins of one run:
+// Sums of X[q] * exp2(kexp * (qf * a_over_m - C)^2) over n bins of one run,
+// for NS = 1 or 2 scales at once (adjacent scales of the ascending list,
+// whose Morlet bands nest, share one walk and one load of each bin):
 // indices q0, q0 + dq, ... (dq = +-P) and unwrapped bin positions qf,
 // qf + P, ... .  The weight is a sampled Gaussian: with u_j the argument at
 // bin j and D = a P / M its step, g_{j+1} = g_j r_j, r_j = 2^{kexp (2 u_j D
-// + D^2)} and r_{j+1} = r_j Q, Q = 2^{2 kexp D^2}.  Runs of 8 or more bins
-// take g_j this way, re-anchored from the exact argument every 8 bins (at
-// most ~3.5e-6 relative drift at a chunk's end; D <= 0.35 there, so the
-// ratios stay in range); shorter runs and the remainder use one
-// ex2.approx (~2^-22 relative) per bin.  LGP > 0 fixes the stride at
-// compile time (dq = SIGN * 2^LGP), so the eight loads of a chunk address X
-// with immediate offsets; LGP = 0 takes dq as passed.
-template <int LGP, int SIGN>
-__device__ __forceinline__ float2 fold_run(const float2* __restrict__ X, int q0, int dq_rt, int n,
-                                           float qf, float pf, const SpecScale& sc, float cneg,
-                                           float kexp) {
+// + D^2)} and r_{j+1} = r_j Q, Q = 2^{2 kexp D^2}.  The recurrence is
+// anchored at the exact argument (ex2.approx, ~2^-22 relative) every 8
+// bins, including a run's last, partial chunk (at most ~3.5e-6 relative
+// drift at a chunk's end; D <= 0.35 where runs are long, so the ratios stay
+// in range).  LGP > 0 fixes the stride at compile time (dq = SIGN * 2^LGP),
+// so the loads of a chunk address X with immediate offsets; LGP = 0 takes
+// dq as passed.
+template <int LGP, int SIGN, int NS>
+__device__ __forceinline__ void fold_run(const float2* __restrict__ X, int q0, int dq_rt, int n,
+                                         float qf, float pf, const SpecScale* sc, float cneg,
+                                         float kexp, float2* acc) {
     const int dq = LGP ? SIGN * (1 << LGP) : dq_rt;
-    float2 acc = make_float2(0.f, 0.f);
     const float2* xp = X + q0;
-    int j = 0;
-    if (n >= 8) {
-        const float dlt = sc.dlt, q2 = sc.q2;
-        for (; j + 8 <= n; j += 8) {
-            const float u = fmaf(qf, sc.a_over_m, cneg);
-            float g = fast_exp2(kexp * u * u);
-            float r = fast_exp2(kexp * fmaf(2.f * u, dlt, dlt * dlt));
+    if (n <= 2) {
+        // Runs of one or two bins (small hops): an exact weight per bin is
+        // cheaper than anchoring the recurrence.
+        for (int t = 0; t < n; ++t) {
+            const float2 v = xp[t * dq];
+#pragma unroll
+            for (int k = 0; k < NS; ++k) {
+                const float u = fmaf(qf + (float)t * pf, sc[k].a_over_m, cneg);
+                const float g = fast_exp2(kexp * u * u);
+                acc[k].x = fmaf(v.x, g, acc[k].x);
+                acc[k].y = fmaf(v.y, g, acc[k].y);
+            }
+        }
+        return;
+    }
+    for (int j = 0; j < n; j += 8) {
+        float g[NS], r[NS];
+#pragma unroll
+        for (int k = 0; k < NS; ++k) {
+            const float u = fmaf(qf, sc[k].a_over_m, cneg);
+            const float d = sc[k].dlt;
+            g[k] = fast_exp2(kexp * u * u);
+            r[k] = fast_exp2(kexp * fmaf(2.f * u, d, d * d));
+        }
+        if (j + 8 <= n) {
 #pragma unroll
             for (int t = 0; t < 8; ++t) {
                 const float2 v = xp[t * dq];
-                acc.x = fmaf(v.x, g, acc.x);
-                acc.y = fmaf(v.y, g, acc.y);
-                g *= r;
-                r *= q2;
+#pragma unroll
+                for (int k = 0; k < NS; ++k) {
+                    acc[k].x = fmaf(v.x, g[k], acc[k].x);
+                    acc[k].y = fmaf(v.y, g[k], acc[k].y);
+                    g[k] *= r[k];
+                    r[k] *= sc[k].q2;
+                }
             }
-            xp += 8 * dq;
-            qf += 8.f * pf;
+        } else {
+            for (int t = 0; t < n - j; ++t) {
+                const float2 v = xp[t * dq];
+#pragma unroll
+                for (int k = 0; k < NS; ++k) {
+                    acc[k].x = fmaf(v.x, g[k], acc[k].x);
+                    acc[k].y = fmaf(v.y, g[k], acc[k].y);
+                    g[k] *= r[k];
+                    r[k] *= sc[k].q2;
+                }
+            }
         }
+        xp += 8 * dq;
+        qf += 8.f * pf;
     }
-    for (; j < n; ++j) {
-        const float2 v = *xp;
-        xp += dq;
-        const float u = fmaf(qf, sc.a_over_m, cneg);
-        qf += pf;
-        const float g = fast_exp2(kexp * u * u);
-        acc.x = fmaf(v.x, g, acc.x);
-        acc.y = fmaf(v.y, g, acc.y);
-    }
-    return acc;
 }
 
-// Z[r] = gscale * sum over the unwrapped band [q_lo, q_hi] of the bins
-// q_u = r (mod P) of X[q_u mod M] * Psi-weight; bins above M/2 are read as
-// conj(X[M - q]).  The walk is split into runs that stay on one side of M/2,
-// so the inner loop is branch-free.  LGP > 0: P = 2^LGP at compile time.
-template <int LGP>
-__device__ __forceinline__ float2 fold_residue(const float2* __restrict__ X, const SpecScale& sc,
-                                               int r, int M, int Mh, int P_rt, int lgP_rt,
-                                               float cneg, float kexp) {
+// Z_k[r] = gscale_k * sum over the unwrapped band of the bins q_u = r
+// (mod P) of X[q_u mod M] * Psi_k-weight, for the NS scales sc[0..NS-1]
+// walked together over the union of their bands (outside its own band a
+// scale's weights are below the band threshold and add next to nothing);
+// bins above M/2 are read as conj(X[M - q]).  The walk is split into runs
+// that stay on one side of M/2, so the inner loop is branch-free.
+// LGP > 0: P = 2^LGP at compile time.
+template <int LGP, int NS>
+__device__ __forceinline__ void fold_residue(const float2* __restrict__ X, const SpecScale* sc,
+                                             int r, int M, int Mh, int P_rt, int lgP_rt, float cneg,
+                                             float kexp, float2* out) {
     const int P = LGP ? (1 << LGP) : P_rt;
     const int lgP = LGP ? LGP : lgP_rt;
-    int qu = sc.q_lo + ((r - sc.q_lo) & (P - 1));
-    int left = qu <= sc.q_hi ? ((sc.q_hi - qu) >> lgP) + 1 : 0;
+    int q_lo = sc[0].q_lo, q_hi = sc[0].q_hi;
+    if (NS > 1) {
+        q_lo = min(q_lo, sc[NS - 1].q_lo);
+        q_hi = max(q_hi, sc[NS - 1].q_hi);
+    }
+    int qu = q_lo + ((r - q_lo) & (P - 1));
+    int left = qu <= q_hi ? ((q_hi - qu) >> lgP) + 1 : 0;
     const float pf = (float)P;
-    float2 ad = make_float2(0.f, 0.f), am = make_float2(0.f, 0.f);
+    float2 ad[NS], am[NS];
+#pragma unroll
+    for (int k = 0; k < NS; ++k) ad[k] = am[k] = make_float2(0.f, 0.f);
     while (left > 0) {
         const int q = qu & (M - 1);
         int n;
         if (q <= Mh) {
             n = min(left, ((Mh - q) >> lgP) + 1);
-            const float2 t = fold_run<LGP, 1>(X, q, P, n, (float)qu, pf, sc, cneg, kexp);
-            ad.x += t.x;
-            ad.y += t.y;
+            fold_run<LGP, 1, NS>(X, q, P, n, (float)qu, pf, sc, cneg, kexp, ad);
         } else {
             n = min(left, ((M - 1 - q) >> lgP) + 1);
-            const float2 t = fold_run<LGP, -1>(X, M - q, -P, n, (float)qu, pf, sc, cneg, kexp);
-            am.x += t.x;
-            am.y += t.y;
+            fold_run<LGP, -1, NS>(X, M - q, -P, n, (float)qu, pf, sc, cneg, kexp, am);
         }
         qu += n * P;
         left -= n;
     }
-    return make_float2(sc.gscale * (ad.x + am.x), sc.gscale * (ad.y - am.y));
+#pragma unroll
+    for (int k = 0; k < NS; ++k)
+        out[k] = make_float2(sc[k].gscale * (ad[k].x + am[k].x), sc[k].gscale * (ad[k].y - am[k].y));
 }
 
 // Fused time-domain scales.  The window buffer Xw[tau][f] =
@@ -705,9 +736,10 @@ __device__ __forceinline__ void fd_run(const SpecLaunch& p, const FdWork& w, int
     fd_item(p, w.Xw, w.T, w.clip, w.k0, w.F, w.grp + q * w.ngrp, i - q * w.nfb);
 }
 
-// a3 for one chunk of scales: band multiply + hop fold.  The chunk's
-// (scale, residue) pairs are numbered g = c P + r; one item = 32
-// consecutive g (32 residues of one scale, or 32 / P whole scales when
+// a3 for one chunk of scales: band multiply + hop fold.  Scales are taken
+// in adjacent pairs (c, c + 1), whose bands nest, and folded together; the
+// chunk's (pair, residue) items are numbered g = c2 P + r; one item = 32
+// consecutive g (32 residues of one pair, or 32 / P whole pairs when
 // P < 32), one lane each; the loop walks the unwrapped band.  Items are
 // ordered by decreasing band width (scales ascend); they are dealt to warps
 // in a snake order to balance the work.
@@ -717,21 +749,35 @@ __device__ __forceinline__ void fold_items(const SpecLaunch& p, const float2* __
                                            int lgP) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nwarps = blockDim.x >> 5;
-    const int nitems = (nc * P + 31) >> 5;
+    const int npairs = (nc + 1) >> 1;
+    const int nitems = (npairs * P + 31) >> 5;
     const float cneg = -p.center;
     for (int round = 0;; ++round) {
         const int it = round * nwarps + ((round & 1) ? nwarps - 1 - warp : warp);
         if (it >= nitems) break;
         const int g = (it << 5) + lane;
-        const int c = g >> lgP;
+        const int c = (g >> lgP) * 2;
         const int r = g & (P - 1);
         if (c >= nc) continue;
-        const SpecScale sc = p.sc[c0 + c];
-        // SHIFT: stored shifted by the band's first residue (a unit-modulus
-        // phase on the inverse transform, so |W| is unchanged); the band
-        // then occupies residues [0, min(P, q_hi - q_lo + 1)).
-        const int zr = SHIFT ? ((r - sc.q_lo) & (P - 1)) : r;
-        Z[c * P + zr] = fold_residue<LGP>(X, sc, r, M, M >> 1, P, lgP, cneg, p.kexp);
+        SpecScale sc[2];
+        sc[0] = p.sc[c0 + c];
+        float2 z[2];
+        // SHIFT: each band stored shifted by its first residue (a
+        // unit-modulus phase on the inverse transform, so |W| is unchanged);
+        // it then occupies residues [0, min(P, q_hi - q_lo + 1)).
+        if (c + 1 < nc) {
+            sc[1] = p.sc[c0 + c + 1];
+            if (sc[0].pair) {
+                fold_residue<LGP, 2>(X, sc, r, M, M >> 1, P, lgP, cneg, p.kexp, z);
+            } else {
+                fold_residue<LGP, 1>(X, sc, r, M, M >> 1, P, lgP, cneg, p.kexp, z);
+                fold_residue<LGP, 1>(X, sc + 1, r, M, M >> 1, P, lgP, cneg, p.kexp, z + 1);
+            }
+            Z[(c + 1) * P + (SHIFT ? ((r - sc[1].q_lo) & (P - 1)) : r)] = z[1];
+        } else {
+            fold_residue<LGP, 1>(X, sc, r, M, M >> 1, P, lgP, cneg, p.kexp, z);
+        }
+        Z[c * P + (SHIFT ? ((r - sc[0].q_lo) & (P - 1)) : r)] = z[0];
     }
 }
 
@@ -938,26 +984,36 @@ __device__ __forceinline__ void spectral_body(const SpecLaunch& p) {
         else
             fft_many<true, kPPT, kPPT, PRUNE>(Z, P, nc, tab, p.hop, PRUNE ? p.sc[c0].wsuf : 0);
 
-        // Stores.  i < 2^24, so the float quotient is off by at most one
-        // and one correction step gives c = i / Fs exactly.
-        const int Fs = p.seg_frames;
-        const float inv_fs = 1.0f / (float)Fs;
-        for (int i = threadIdx.x; i < nc * Fs; i += blockDim.x) {
-            int c = (int)((float)i * inv_fs);
-            int f = i - c * Fs;
-            if (f < 0) {
-                --c;
-                f += Fs;
-            } else if (f >= Fs) {
-                ++c;
-                f -= Fs;
-            }
-            const int64_t k = k0 + f;
-            if (k < F) {
-                const float2 w = Z[c * P + p.kp0 + f];
-                const int row = p.sc[c0 + c].row;
-                p.out[((int64_t)clip * p.S_total + row) * p.frames_max + k] =
-                    fast_sqrt(fmaf(w.x, w.x, w.y * w.y));
+        // Stores: one warp per scale row, or (fewer rows than warps) warp
+        // items of 32 consecutive frames of one row; the row is read once
+        // per row or item, stores are coalesced and reads conflict-free.
+        {
+            const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+            const int nwarps = blockDim.x >> 5;
+            const int Fs = p.seg_frames;
+            const int fend = (int)(F - k0 < (int64_t)Fs ? F - k0 : (int64_t)Fs);
+            if (nc >= nwarps) {
+                // One warp per row while there are rows for every warp.
+                for (int c = warp; c < nc; c += nwarps) {
+                    float* o = p.out +
+                               ((int64_t)clip * p.S_total + p.sc[c0 + c].row) * p.frames_max + k0;
+                    const float2* z = Z + c * P + p.kp0;
+                    for (int f = lane; f < fend; f += 32) {
+                        const float2 w = z[f];
+                        o[f] = fast_sqrt(fmaf(w.x, w.x, w.y * w.y));
+                    }
+                }
+            } else {
+                const int nch = (fend + 31) >> 5;
+                for (int it = warp; it < nc * nch; it += nwarps) {
+                    const int c = it / nch;
+                    const int f = (it - c * nch) * 32 + lane;
+                    if (f < fend) {
+                        const float2 w = Z[c * P + p.kp0 + f];
+                        p.out[((int64_t)clip * p.S_total + p.sc[c0 + c].row) * p.frames_max + k0 +
+                              f] = fast_sqrt(fmaf(w.x, w.x, w.y * w.y));
+                    }
+                }
             }
         }
         __syncthreads();
