@@ -200,6 +200,16 @@ def algorithmic_flops_per_clip(scales, hop, n=N_SAMPLES):
             + 4.0 * len(scales) * F), M
 
 
+def algorithmic_bytes_per_clip(scales, hop, n=N_SAMPLES):
+    """HBM bytes of the method per clip, the roofline's numerator: the
+    float32 input once (4 n), the float32 scalogram once (4 S F) and one
+    write plus one read of the complex float32 half-spectrum of the
+    unsegmented transform (16 (M/2 + 1), M as in algorithmic_flops_per_clip)."""
+    _, M = algorithmic_flops_per_clip(scales, hop, n)
+    F = -(-n // hop)
+    return 4.0 * n + 4.0 * len(scales) * F + 16.0 * (M // 2 + 1)
+
+
 def kernel_traffic(kernel: str, source: str):
     """DRAM bytes per launch of `kernel` from the committed ncu summary
     (profiles/ncu_traffic.json), or None when the kernel's source changed
@@ -218,9 +228,18 @@ def kernel_traffic(kernel: str, source: str):
     return d["dram_bytes_per_launch"] if d.get("source_sha1") == sha else None
 
 
+def num_sms() -> int:
+    """Streaming multiprocessors of the current device (152 on a GB300)."""
+    try:
+        import torch
+        return int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
+    except Exception:
+        return 152
+
+
 def fp32_peak_tflops(sm_mhz):
-    # 152 SMs x 128 FP32 lanes x 2 flops (FMA) per clock
-    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    # SMs x 128 FP32 lanes x 2 flops (FMA) per clock
+    return num_sms() * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
 # ------------------------------------------------------------------ reference arm
@@ -318,8 +337,10 @@ def cpu_model() -> str:
 DIRECT_CLIPS, DIRECT_N, DIRECT_S = 512, 16000, 128
 
 
-def direct_useful_flops_per_clip(scales, hop, n=DIRECT_N, eps=1e-9):
-    """2 flops per tap per (frame, real/imag column): F * sum_s (2 h_s + 1) * 2 * 2."""
+def direct_useful_flops_per_clip(scales, hop, n=DIRECT_N, eps=1e-16):
+    """2 flops per tap per (frame, real/imag column): F * sum_s (2 h_s + 1) * 2 * 2,
+    with the supports of the float64 definition (taps below 1e-16 of the
+    peak dropped; the kernel itself drops those below 1e-9)."""
     F = -(-n // hop)
     taps = sum(2 * math.ceil(a * math.sqrt(B_MORLET * math.log(1.0 / eps))) + 1 for a in scales)
     return 4.0 * F * taps
@@ -442,7 +463,7 @@ def run_ours(args, rank, world, local_rank):
         hop1 = {"ms_per_step": ms1, "audio_sec_per_s": world * audio_s / (ms1 * 1e-3),
                 "scalogram_gbs": world * o1.numel() * 4 / (ms1 * 1e-3) / 1e9,
                 "seg_len": p1.info()["seg_len"], "num_segments": p1.info()["num_segments"],
-                "bytes_per_launch": int(N_CLIPS * N_SAMPLES * 4 + o1.numel() * 4),
+                "bytes_per_launch": int(algorithmic_bytes_per_clip(scales, 1) * N_CLIPS),
                 "flops_per_launch": algorithmic_flops_per_clip(scales, 1)[0] * N_CLIPS}
         del o1
         p1.close()
@@ -491,7 +512,7 @@ def run_ours(args, rank, world, local_rank):
         peak_alu = cwth.measure_fp32_fma_tflops(stream)
         peak_alu_src = "measured: FP32 FMA microbenchmark (cwth_measure_fp32_fma), best of 3 launches"
     except cwth.CwthError:
-        peak_alu, peak_alu_src = peak_derived, "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"
+        peak_alu, peak_alu_src = peak_derived, "derived: SMs x 128 FP32 lanes x 2 x max SM clock"
     if hop1 is not None:
         # Both roofline fractions at hop 1; the binding one is the larger time at peak.
         t_alu = hop1["flops_per_launch"] / (peak_alu * 1e12)
@@ -503,9 +524,15 @@ def run_ours(args, rank, world, local_rank):
                     "unit": "TFLOP/s", "frac": t_alu / s1},
             "hbm": {"achieved": hop1["bytes_per_launch"] / s1 / 1e9, "peak": pk["hbm_gbs"],
                     "unit": "GB/s", "frac": t_hbm / s1}}
-    achieved = flops_launch / (statistics.mean(step_ms) * 1e-3) / 1e12
-    bytes_launch = N_CLIPS * (N_SAMPLES * 4 + S * plan.frames_max * 4)
-    hbm_achieved = bytes_launch / (statistics.mean(step_ms) * 1e-3) / 1e9
+    t_step = statistics.mean(step_ms) * 1e-3
+    achieved = flops_launch / t_step / 1e12
+    # The binding roofline: the larger of the HBM and ALU times at peak for
+    # the method's algorithmic bytes and flops.
+    bytes_launch = algorithmic_bytes_per_clip(scales, HOP) * N_CLIPS
+    t_hbm_peak = bytes_launch / (pk["hbm_gbs"] * 1e9)
+    t_alu_peak = flops_launch / (peak_alu * 1e12)
+    hbm_achieved = bytes_launch / t_step / 1e9
+    io_bytes = N_CLIPS * (N_SAMPLES * 4 + S * plan.frames_max * 4)
     out_bytes = N_CLIPS * S * plan.frames_max * 4
 
     line = {
@@ -520,16 +547,26 @@ def run_ours(args, rank, world, local_rank):
                    "seg_len": info["seg_len"], "num_segments": info["num_segments"],
                    "num_spectral": info["num_spectral"], "num_direct": info["num_direct"]},
         "scalogram_gbs": world * out_bytes / (ms * 1e-3) / 1e9,
-        "roofline": {"bound": "alu", "kernel": "spectral_segment_kernel",
-                     "achieved": achieved, "peak": peak_alu, "unit": "TFLOP/s",
-                     "frac": achieved / peak_alu,
+        "roofline": {"bound": "hbm" if t_hbm_peak >= t_alu_peak else "alu",
+                     "kernel": "spectral_segment_kernel",
+                     "achieved": hbm_achieved if t_hbm_peak >= t_alu_peak else achieved,
+                     "peak": pk["hbm_gbs"] if t_hbm_peak >= t_alu_peak else peak_alu,
+                     "unit": "GB/s" if t_hbm_peak >= t_alu_peak else "TFLOP/s",
+                     "frac": max(t_hbm_peak, t_alu_peak) / t_step,
                      "traffic": kernel_traffic("spectral_segment_kernel", "spectral.cu"),
-                     "algorithmic_flops_per_launch": flops_launch,
-                     "peak_source": peak_alu_src, "peak_derived": peak_derived,
-                     "hbm_view": {"algorithmic_bytes_per_launch": bytes_launch,
-                                  "achieved_gbs": hbm_achieved, "peak_gbs": pk["hbm_gbs"],
-                                  "frac": hbm_achieved / pk["hbm_gbs"],
-                                  "peak_source": pk_kind}},
+                     "algorithmic_bytes_per_launch": bytes_launch,
+                     "algorithmic_bytes_per_clip": bytes_launch / N_CLIPS,
+                     "peak_source": f"{pk_kind} HBM copy bandwidth (MEASURED_PEAKS.json)",
+                     "time_at_peak_us": {"hbm": t_hbm_peak * 1e6, "alu": t_alu_peak * 1e6},
+                     "alu_view": {"algorithmic_flops_per_launch": flops_launch,
+                                  "achieved_tflops": achieved, "peak_tflops": peak_alu,
+                                  "frac": achieved / peak_alu, "peak_source": peak_alu_src,
+                                  "peak_derived": peak_derived},
+                     "io_view": {"bytes_per_launch": io_bytes,
+                                 "achieved_gbs": io_bytes / t_step / 1e9,
+                                 "frac": io_bytes / t_step / 1e9 / pk["hbm_gbs"],
+                                 "note": "input read once + scalogram written once (the "
+                                         "spectrum stays in shared memory)"}},
         "e2e": {"value": world * audio_s / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": int(hx.numel() * 4),
                 "d2h_bytes_per_step": int(hout.numel() * 4),

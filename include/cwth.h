@@ -249,9 +249,12 @@ cwth_status cwth_sync(cwth_plan_t plan, void *stream);
  * then records CWTH_ERR_TIMEOUT in the plan's device status word, exactly as
  * the tensor-core kernels do when a copy or MMA stage never completes.  The
  * next cwth_sync(plan, stream) returns CWTH_ERR_TIMEOUT and clears the word;
- * the CUDA context stays usable.  Nothing faults or hangs.
- * Errors: CWTH_ERR_BAD_PLAN, CWTH_ERR_INVALID_ARG (budget out of range),
- * CWTH_ERR_CUDA (allocation of the status word or launch failed).
+ * the CUDA context stays usable.  Nothing faults or hangs.  plan == NULL
+ * targets the status word of cwth_execute_direct_noalloc on the current
+ * device instead, which cwth_noalloc_status then reports and clears.
+ * Errors: CWTH_ERR_BAD_PLAN (a destroyed or foreign handle),
+ * CWTH_ERR_INVALID_ARG (budget out of range), CWTH_ERR_CUDA (allocation of
+ * the plan's status word or launch failed).
  */
 cwth_status cwth_selftest_wait_timeout(cwth_plan_t plan, int64_t budget_cycles, void *stream);
 
@@ -274,9 +277,9 @@ cwth_status cwth_plan_scale_paths(cwth_plan_t plan, int32_t *paths);
  *
  * For callers that cannot allocate device memory while they run: code whose
  * device memory is owned by another allocator (a framework's caching pool),
- * real-time or capture-sensitive loops where cudaMalloc/cudaFree would
- * synchronise the device or block, and processes that must not grow their
- * footprint after start-up.  This call needs no plan and allocates nothing:
+ * real-time loops where cudaMalloc/cudaFree would synchronise the device or
+ * block, and processes that must not grow their footprint after start-up.
+ * This call needs no plan and allocates nothing:
  * the tap bank, the per-scale tables, the staged bf16 signal and a status
  * word all live in one array of CWTH_NOALLOC_SCRATCH_BYTES compiled into
  * libcwth.so, which every GPU that loads the library holds until the process
@@ -296,6 +299,12 @@ cwth_status cwth_plan_scale_paths(cwth_plan_t plan, int32_t *paths);
  * overlaps on the GPU - on different streams, or from different threads -
  * race: serialise them, e.g. on one stream.
  *
+ * Device-side failures: the tensor-core kernels wait on their copies and
+ * MMAs with bounded waits; one that runs out records CWTH_ERR_TIMEOUT in a
+ * status word inside the array and its frames are left unwritten.  The word
+ * stays set (later calls then skip their work) until cwth_noalloc_status
+ * reads and clears it, so check it after the calls whose results you use.
+ *
  * Errors: CWTH_ERR_INVALID_ARG for bad arguments and for a request whose
  * scratch would exceed CWTH_NOALLOC_SCRATCH_BYTES (cwth_last_error() states
  * the bytes needed); CWTH_ERR_UNSUPPORTED for a scale needing more than 4096
@@ -306,6 +315,18 @@ cwth_status cwth_execute_direct_noalloc(const cwth_morlet *w, const double *scal
                                         int32_t hop, int32_t precision, const float *d_x,
                                         int64_t ld_x, int64_t max_len, const int64_t *d_lengths,
                                         int32_t batch, float *d_out, void *stream);
+
+/*
+ * Status of cwth_execute_direct_noalloc on the current device (no paper
+ * counterpart): waits for the work enqueued on `stream`, then reads the
+ * status word the allocation-free kernels share and clears it.  Returns
+ * CWTH_ERR_TIMEOUT if one of them gave up a bounded wait since the last
+ * query, CWTH_OK otherwise; CWTH_ERR_CUDA if the stream reported a fault.
+ * Allocates nothing (a synchronous 4-byte copy and, after a timeout, a
+ * 4-byte memset of the array).  Sets the device up like the entry point's
+ * first call if it has not run yet.
+ */
+cwth_status cwth_noalloc_status(void *stream);
 
 #ifdef __cplusplus
 }

@@ -1253,8 +1253,16 @@ cwth_status cwth_sync(cwth_plan_t p, void* stream) {
 }
 
 cwth_status cwth_selftest_wait_timeout(cwth_plan_t p, int64_t budget_cycles, void* stream) {
-    if (!valid_plan(p)) return CWTH_ERR_BAD_PLAN;
     if (budget_cycles < 1 || budget_cycles > kMaxSelftestBudget) return CWTH_ERR_INVALID_ARG;
+    if (!p) {
+        // The allocation-free entry point's status word on the current device.
+        int* word = nullptr;
+        const cwth_status st = cwth::noalloc_status_word(&word);
+        if (st != CWTH_OK) return st;
+        return cuda_status(
+            cwth::direct_wait_selftest(word, (long long)budget_cycles, (cudaStream_t)stream));
+    }
+    if (!valid_plan(p)) return CWTH_ERR_BAD_PLAN;
     DeviceGuard g(p->device);
     if (!g.ok) return CWTH_ERR_CUDA;
     if (!p->d_status) {

@@ -147,6 +147,9 @@ struct DirShape {
 
 // Records the detail string cwth_last_error() returns in the calling thread.
 void set_last_error(const char* msg);
+// Device address of the allocation-free entry point's status word on the
+// current device (noalloc.cu).
+cwth_status noalloc_status_word(int** word);
 
 size_t spectral_smem_bytes(int M, int P, int nconc, size_t fd_bytes = 0);
 // Shared-memory bytes of the fused time-domain scales, held in the fold's

@@ -95,7 +95,36 @@ cwth_status setup(int dev, void** scratch) {
 
 }  // namespace
 
+namespace cwth {
+// Device address of the allocation-free entry point's status word on the
+// current device (the first word of its scratch array), setting the device
+// up on first use.
+cwth_status noalloc_status_word(int** word) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail_cuda(e);
+    void* base = nullptr;
+    const cwth_status st = setup(dev, &base);
+    if (st != CWTH_OK) return st;
+    *word = (int*)base;
+    return CWTH_OK;
+}
+}  // namespace cwth
+
 extern "C" {
+
+cwth_status cwth_noalloc_status(void* stream) {
+    int* word = nullptr;
+    cwth_status st = cwth::noalloc_status_word(&word);
+    if (st != CWTH_OK) return st;
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    int flag = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&flag, word, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && flag != 0) e = cudaMemset(word, 0, sizeof(int));
+    if (e != cudaSuccess) return fail_cuda(e);
+    return flag != 0 ? (cwth_status)flag : CWTH_OK;
+}
+
 
 cwth_status cwth_execute_direct_noalloc(const cwth_morlet* w, const double* scales, int32_t S,
                                         int32_t hop, int32_t precision, const float* d_x,
@@ -118,7 +147,7 @@ cwth_status cwth_execute_direct_noalloc(const cwth_morlet* w, const double* scal
     if ((int64_t)S * ((max_len + hop - 1) / hop) > INT32_MAX)
         return fail(CWTH_ERR_UNSUPPORTED, "one clip's output exceeds 2^31 elements");
 
-    // Per-scale supports, scales sorted by support (stack arrays only).
+    // Per-scale supports (stack arrays only).
     int32_t order[kMaxScales], hs[kMaxScales];
     double sc[kMaxScales];
     for (int32_t s = 0; s < S; ++s) {
@@ -127,10 +156,13 @@ cwth_status cwth_execute_direct_noalloc(const cwth_morlet* w, const double* scal
         if (rup(2 * (int64_t)hs[s] + 1, 64) > kMaxTaps)
             return fail(CWTH_ERR_UNSUPPORTED, "a scale needs more than 4096 taps");
     }
-    for (int32_t i = 1; i < S; ++i) {  // insertion sort, descending support
+    // Insertion sort (stable), descending scale - the planned direct path's
+    // order, so that both put the same scales in each 128-scale group and
+    // give the same bytes; supports then descend too.
+    for (int32_t i = 1; i < S; ++i) {
         const int32_t v = order[i];
         int32_t j = i - 1;
-        while (j >= 0 && hs[order[j]] < hs[v]) {
+        while (j >= 0 && scales[order[j]] < scales[v]) {
             order[j + 1] = order[j];
             --j;
         }
@@ -162,7 +194,7 @@ cwth_status cwth_execute_direct_noalloc(const cwth_morlet* w, const double* scal
         off = (size_t)rup((int64_t)(off + bytes), 256);
         return o;
     };
-    const size_t o_status = take(sizeof(int));
+    const size_t o_status = take(sizeof(int));  // 0: cwth_noalloc_status reads it there
     const size_t o_rows = take(sizeof(int32_t) * S);
     const size_t o_h = take(sizeof(int32_t) * S);
     const size_t o_sc = take(sizeof(double) * S);
@@ -206,10 +238,11 @@ cwth_status cwth_execute_direct_noalloc(const cwth_morlet* w, const double* scal
     __nv_bfloat16* d_xhi = (__nv_bfloat16*)(base + o_sig);
     __nv_bfloat16* d_xlo = d_xhi + sig_elems;
 
-    // The status word and the small tables start fresh on every call; the
-    // banks and the staged signal are rewritten in full by their kernels.
-    e = cudaMemsetAsync(d_status, 0, sizeof(int), strm);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_rows, order, sizeof(int32_t) * S, cudaMemcpyHostToDevice, strm);
+    // The small tables are rewritten on every call, the banks and the staged
+    // signal in full by their kernels.  The status word is not: it keeps a
+    // bounded-wait timeout until cwth_noalloc_status reads and clears it
+    // (the array starts zeroed when the library loads).
+    e = cudaMemcpyAsync(d_rows, order, sizeof(int32_t) * S, cudaMemcpyHostToDevice, strm);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_h, h_sorted, sizeof(int32_t) * S, cudaMemcpyHostToDevice, strm);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_sc, sc, sizeof(double) * S, cudaMemcpyHostToDevice, strm);
     if (e != cudaSuccess) return fail_cuda(e);

@@ -26,7 +26,7 @@ EXPORTS = ("cwth_plan", "cwth_execute", "cwth_execute_host", "cwth_destroy",
            "cwth_plan_scale_paths", "cwth_sync", "cwth_last_error",
            "cwth_execute_direct_noalloc", "cwth_plan_set_host_chunks",
            "cwth_selftest_wait_timeout", "cwth_measure_fp32_fma", "cwth_plan_resampled",
-           "cwth_plan_segment")
+           "cwth_plan_segment", "cwth_noalloc_status")
 
 
 class CwthError(RuntimeError):
@@ -98,6 +98,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                                 ctypes.POINTER(ctypes.c_double), i32, i32, i32,
                                                 vp, i64, i64, vp, i32, vp, vp]
     lib.cwth_execute_direct_noalloc.restype = ctypes.c_int
+    lib.cwth_noalloc_status.argtypes = [vp]
+    lib.cwth_noalloc_status.restype = ctypes.c_int
     return lib
 
 
@@ -139,8 +141,17 @@ def execute_direct_noalloc(scales, hop: int, x, out, lengths=None, precision: st
     sc = np.ascontiguousarray(np.asarray(scales, dtype=np.float64).ravel())
     if x.dim() == 1:
         x = x.unsqueeze(0)
+    if x.dtype != torch.float32 or not x.is_cuda or x.stride(1) != 1:
+        raise ValueError("x must be a float32 CUDA tensor with unit column stride")
     B = x.shape[0]
     max_len = int(x.shape[1]) if max_len is None else int(max_len)
+    if lengths is not None and (lengths.dtype != torch.int64 or not lengths.is_cuda
+                                or lengths.numel() != B or not lengths.is_contiguous()):
+        raise ValueError("lengths must be a contiguous int64 CUDA tensor with one entry per clip")
+    want = (B, int(sc.shape[0]), num_frames(max_len, hop))
+    if (out.dtype != torch.float32 or not out.is_cuda or not out.is_contiguous()
+            or tuple(out.shape) != want):
+        raise ValueError(f"out must be a contiguous float32 CUDA tensor of shape {want}")
     ld = int(x.shape[1]) if B == 1 else int(x.stride(0))
     if stream is None:
         stream = torch.cuda.current_stream(x.device)
@@ -152,6 +163,14 @@ def execute_direct_noalloc(scales, hop: int, x, out, lengths=None, precision: st
         ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(stream.cuda_stream))
     _check(st, "cwth_execute_direct_noalloc")
     return out
+
+
+def noalloc_status(stream=None):
+    """cwth_noalloc_status: wait for ``stream`` and raise CwthError if an
+    allocation-free call gave up a bounded wait since the last check (the
+    status word is cleared by the check)."""
+    s = 0 if stream is None else stream.cuda_stream
+    _check(_lib.cwth_noalloc_status(ctypes.c_void_p(s)), "cwth_noalloc_status")
 
 
 class Plan:

@@ -103,7 +103,9 @@ def test_null_plan_handles(cw):
     assert lib.cwth_execute(None, None, 0, None, 0, None, None) == 6
     assert lib.cwth_execute_host(None, None, 0, None, 0, None, None) == 6
     assert lib.cwth_plan_set_host_chunks(None, 2) == 6
-    assert lib.cwth_selftest_wait_timeout(None, 1000, None) == 6
+    # (a NULL plan there names the allocation-free entry point's status
+    # word, which needs a device; a budget out of range is refused first)
+    assert lib.cwth_selftest_wait_timeout(None, 0, None) == 1
     info = cw.PlanInfo()
     assert lib.cwth_plan_query(None, ctypes.byref(info)) == 6
     assert lib.cwth_plan_scale_paths(None, None) == 6
@@ -117,3 +119,15 @@ def test_product_package_does_not_import_the_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(import|from)\s+oracle\b", text, re.M), f
                 assert "cwth_oracle" not in text, f
+
+
+def test_noalloc_wrapper_checks_arguments_before_the_library(cw):
+    """execute_direct_noalloc refuses host tensors, wrong dtypes and a
+    mis-shaped output before anything reaches the C ABI (no GPU needed)."""
+    torch = pytest.importorskip("torch")
+    x = torch.zeros((2, 1000), dtype=torch.float32)
+    out = torch.zeros((2, 3, 16), dtype=torch.float32)
+    with pytest.raises(ValueError):
+        cw.execute_direct_noalloc([2.0, 4.0, 8.0], 64, x, out)          # host memory
+    with pytest.raises(ValueError):
+        cw.execute_direct_noalloc([2.0, 4.0, 8.0], 64, x.double(), out)  # float64

@@ -1,13 +1,21 @@
 """cwth_execute_direct_noalloc: the direct path for callers that cannot
 allocate device memory while they run (their memory belongs to another
-allocator, or cudaMalloc would stall a real-time or captured loop).  Its
-scratch is a fixed array inside libcwth.so.
+allocator, a real-time loop must not stall on cudaMalloc/cudaFree, or the
+process must not grow after start-up).  Its scratch is a fixed array inside
+libcwth.so.
 
-The test calls the entry point through the C ABI twice in a row, with
-different batches, scale lists and hops (so the second call runs on scratch
-the first one left behind), and checks each result against the planned
-direct path (cwth_plan + cwth_execute) within the tolerances the parity
-tests use.  This file is named to be collected last.
+The tests call the entry point through the C ABI several times in a row,
+with different batches, scale lists and hops (so each call runs on scratch
+the previous one left behind), and check each result
+
+  * byte for byte against the planned direct path (cwth_plan + cwth_execute
+    run the same kernels on identically built tables), including a request
+    of more than 128 scales, which takes two GEMM groups;
+  * against the float64 oracle, within the tolerances the parity tests use;
+
+and that a bounded wait that runs out is reported once by
+cwth_noalloc_status and then cleared.  This file is named to be collected
+last.
 """
 from __future__ import annotations
 
@@ -45,23 +53,28 @@ def _noalloc(cw, xs, scales, hop, precision, lengths):
     lib = cw.lib()
     sc = np.ascontiguousarray(np.asarray(scales, np.float64))
     w = cw.Morlet(1.5, 1.0)
+    stream = torch.cuda.current_stream().cuda_stream
     st = lib.cwth_execute_direct_noalloc(
         ctypes.byref(w), sc.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), S, hop,
         cw.PREC[precision], ctypes.c_void_p(xs.data_ptr()), int(xs.stride(0)), int(xs.shape[1]),
         ctypes.c_void_p(lengths.data_ptr() if lengths is not None else 0), int(xs.shape[0]),
-        ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(stream))
     assert st == 0, (st, lib.cwth_last_error())
-    torch.cuda.synchronize()
+    assert lib.cwth_noalloc_status(ctypes.c_void_p(stream)) == 0
     return out.cpu().numpy()
 
 
-def test_noalloc_matches_planned_direct_path_twice(cw):
+def test_noalloc_matches_planned_direct_path_and_oracle(cw):
+    import oracle
     from paper_2408_14302_gb300 import signals
     cases = [
         # (clips, samples, scales, hop, precision, lengths)
         (3, 16000, signals.scales_for_band(100, 8000, 40, 16000.0), 64, "bf16x2", None),
         (5, 9000, signals.scales_for_band(150, 6000, 24, 16000.0), 128, "bf16",
          [9000, 8999, 1, 0, 4097]),
+        # 200 scales: two GEMM groups (128 + 72), each with its own bank
+        # slot, schedule slot and tensor maps inside the scratch array
+        (2, 12000, signals.scales_for_band(100, 8000, 200, 16000.0), 64, "bf16x2", [12000, 7001]),
     ]
     for clips, n, scales, hop, precision, lengths in cases:
         xs = np.stack([signals.machine_clip(300 + i, n) for i in range(clips)])
@@ -70,15 +83,61 @@ def test_noalloc_matches_planned_direct_path_twice(cw):
         got = _noalloc(cw, xd, scales, hop, precision, ld)
         ref = _planned(cw, xd, scales, hop, precision, ld)
         assert got.shape == ref.shape
+        # Same kernels on identically built tables: identical bytes,
+        # including the untouched frames past each clip.
+        assert np.array_equal(got, ref), (precision, hop, len(scales))
         for i in range(clips):
             L = n if lengths is None else lengths[i]
             F = -(-L // hop)
             assert np.all(got[i, :, F:] == -5.0), "frames past the clip were written"
             if L == 0:
                 continue
-            scale = max(float(np.abs(ref[i, :, :F]).max()), 1e-30)
-            err = float(np.max(np.abs(got[i, :, :F] - ref[i, :, :F]))) / scale
+            want = oracle.cwth_magnitude(xs[i, :L].astype(np.float32).astype(np.float64),
+                                         scales, hop)
+            err = float(np.max(np.abs(got[i, :, :F] - want))) / float(want.max())
             assert err <= TOL[precision], (precision, i, err)
+
+
+def test_noalloc_timeout_is_reported_once_then_cleared(cw):
+    """A bounded wait that runs out (forced by the self-test on the
+    allocation-free status word: a wait of 10^6 cycles on a barrier nothing
+    arrives on) is reported by the next status check, once; afterwards the
+    entry point works again."""
+    from paper_2408_14302_gb300 import signals
+    lib = cw.lib()
+    stream = torch.cuda.current_stream().cuda_stream
+    assert lib.cwth_noalloc_status(ctypes.c_void_p(stream)) == 0
+    assert lib.cwth_selftest_wait_timeout(None, 1_000_000, ctypes.c_void_p(stream)) == 0
+    assert lib.cwth_noalloc_status(ctypes.c_void_p(stream)) == 5  # CWTH_ERR_TIMEOUT
+    assert lib.cwth_noalloc_status(ctypes.c_void_p(stream)) == 0
+    n, hop = 8000, 64
+    xs = np.stack([signals.machine_clip(77 + i, n) for i in range(2)])
+    xd = torch.from_numpy(np.ascontiguousarray(xs, np.float32)).cuda()
+    scales = signals.scales_for_band(200, 8000, 16, 16000.0)
+    got = _noalloc(cw, xd, scales, hop, "bf16x2", None)
+    ref = _planned(cw, xd, scales, hop, "bf16x2", None)
+    assert np.array_equal(got, ref)
+
+
+def test_noalloc_python_wrapper(cw):
+    """The binding's wrapper runs the entry point and checks its own
+    arguments before calling it."""
+    from paper_2408_14302_gb300 import signals
+    n, hop = 6000, 64
+    scales = signals.scales_for_band(300, 8000, 12, 16000.0)
+    xd = torch.from_numpy(signals.machine_batch(2, n)).cuda()
+    out = torch.empty((2, 12, cw.num_frames(n, hop)), device="cuda")
+    cw.execute_direct_noalloc(scales, hop, xd, out, precision="bf16x2")
+    cw.noalloc_status()
+    ref = _planned(cw, xd, scales, hop, "bf16x2", None)
+    assert np.array_equal(out.cpu().numpy(), ref)
+    with pytest.raises(ValueError):
+        cw.execute_direct_noalloc(scales, hop, xd, out[:, :5])           # wrong shape
+    with pytest.raises(ValueError):
+        cw.execute_direct_noalloc(scales, hop, xd.double(), out)         # not float32
+    with pytest.raises(ValueError):
+        cw.execute_direct_noalloc(scales, hop, xd, out,
+                                  lengths=torch.tensor([n, n], dtype=torch.int32, device="cuda"))
 
 
 def test_noalloc_rejects_requests_beyond_its_scratch(cw):
