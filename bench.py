@@ -354,7 +354,7 @@ def run_direct_leg(torch, cwth, dev, flush, stream, steps, peak_bf16):
     x_d = torch.from_numpy(xs).to(dev)
     res = {}
     for hop in (64, 128, 256, 512):
-        for prec in ("bf16", "bf16x2"):
+        for prec in ("bf16", "bf16x2", "bf16x3"):
             p = cwth.Plan(scales, hop=hop, max_len=DIRECT_N, precision=prec, path="direct",
                           sample_rate=FS)
             o = torch.empty((DIRECT_CLIPS, DIRECT_S, p.frames_max), device=dev)
@@ -367,7 +367,7 @@ def run_direct_leg(torch, cwth, dev, flush, stream, steps, peak_bf16):
             p.sync(stream)
             ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
             useful = direct_useful_flops_per_clip(scales, hop) * DIRECT_CLIPS
-            products = 4 if prec == "bf16x2" else 1
+            products = {"bf16x2": 4, "bf16x3": 6}.get(prec, 1)
             ach = useful * products / (ms * 1e-3) / 1e12
             res[f"hop{hop}_{prec}"] = {
                 "ms_per_step": ms,
@@ -478,7 +478,7 @@ def run_ours(args, rank, world, local_rank):
     auto = None
     if not args.no_direct:
         pa = cwth.Plan(scales, hop=HOP, max_len=N_SAMPLES, bandwidth=B_MORLET, center=C_MORLET,
-                       sample_rate=FS, precision="bf16x2", path="auto")
+                       sample_rate=FS, precision="bf16x3", path="auto")
         oa = torch.empty_like(out_d)
         fa = lambda: pa.execute(x_d, out=oa, stream=stream)  # noqa: E731
         for _ in range(3):
@@ -489,7 +489,7 @@ def run_ours(args, rank, world, local_rank):
         pa.sync(stream)
         msa = statistics.mean(a.elapsed_time(b) for a, b in ea)
         ia = pa.info()
-        auto = {"precision": "bf16x2", "path": "auto", "ms_per_step": msa,
+        auto = {"precision": "bf16x3", "path": "auto", "ms_per_step": msa,
                 "audio_sec_per_s": world * audio_s / (msa * 1e-3),
                 "num_direct": ia["num_direct"], "num_spectral": ia["num_spectral"]}
         pa.close()
@@ -574,7 +574,7 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": args.steps * 1,
         "clocks": clocks,
         "hop1": hop1,
-        "auto_bf16x2": auto,
+        "auto_bf16x3": auto,
         "direct": direct,
     }
     plan.close()
@@ -590,7 +590,7 @@ def profile_case(argv):
     test-suite does that)."""
     ap = argparse.ArgumentParser(prog="bench.py --profile-case")
     ap.add_argument("--path", default="spectral", choices=["auto", "spectral", "direct"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "bf16x2"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "bf16x2", "bf16x3"])
     ap.add_argument("--signal", default="machine", choices=["machine", "tones"])
     ap.add_argument("--clips", type=int, default=64)
     ap.add_argument("--seconds", type=float, default=10.0)

@@ -53,11 +53,19 @@ typedef struct {
 typedef struct cwth_plan_s *cwth_plan_t;
 
 /* Arithmetic of the direct (time-domain, tensor-core) path.  The spectral
- * path always computes in float32. */
+ * path always computes in float32.  The split variants write the samples
+ * and the taps as sums of bf16 parts and accumulate part products in
+ * float32: BF16X2 (hi + lo, all four products) holds each tap product to
+ * about 2^-17 relative, so a scalogram value is within about 2^-17 of the
+ * sum of |x g| over its taps (tight where the taps do not cancel);
+ * BF16X3 (hi + mid + lo, the six products of order up to 2^-16) holds each
+ * tap product to about 2^-24, i.e. float32 accuracy even where the taps
+ * cancel. */
 enum {
     CWTH_PREC_FP32 = 0,   /* float32 everywhere                          */
     CWTH_PREC_BF16 = 1,   /* bf16 operands, float32 accumulation         */
-    CWTH_PREC_BF16X2 = 2  /* hi+lo split bf16 operands, fp32 accumulate  */
+    CWTH_PREC_BF16X2 = 2, /* hi+lo split bf16 operands, fp32 accumulate  */
+    CWTH_PREC_BF16X3 = 3  /* hi+mid+lo split bf16, fp32 accumulate      */
 };
 
 /* Which evaluation each scale takes. */
@@ -287,7 +295,8 @@ cwth_status cwth_plan_scale_paths(cwth_plan_t plan, int32_t *paths);
  *
  * Computes the same |W| as cwth_plan(..., CWTH_PATH_DIRECT) + cwth_execute:
  *   w, scales, S (1..1024), hop (a multiple of 8), precision
- *   (CWTH_PREC_BF16 or CWTH_PREC_BF16X2) as in cwth_plan; d_x, ld_x,
+ *   (CWTH_PREC_BF16, CWTH_PREC_BF16X2 or CWTH_PREC_BF16X3) as in
+ *   cwth_plan; d_x, ld_x,
  *   d_lengths, batch, d_out, stream as in cwth_execute, with max_len the
  *   longest clip and d_out laid out [batch][S][cwth_num_frames(max_len, hop)].
  *

@@ -27,7 +27,7 @@ from . import cwth, signals
 
 # Candidate (path, precision) pairs per accuracy class.
 CANDIDATES = {
-    "fp32": [("spectral", "fp32"), ("auto", "bf16x2")],
+    "fp32": [("spectral", "fp32"), ("auto", "bf16x3")],
     "bf16": [("auto", "bf16"), ("spectral", "fp32")],
 }
 

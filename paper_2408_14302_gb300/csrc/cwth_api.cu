@@ -94,6 +94,9 @@ int num_sms(int dev) {
 }
 // Largest padded tap count the direct path accepts.
 constexpr int kMaxDirectTaps = 4096;
+// Largest padded tap count an automatic CWTH_PREC_BF16X3 plan sends to the
+// tensor cores (see direct_eligible).
+constexpr int kSplitAutoTaps = 1024;
 // Longest wait cwth_selftest_wait_timeout accepts: the kernels' own budget
 // (about 2 s of SM clock).
 constexpr int64_t kMaxSelftestBudget = 4000000000LL;
@@ -345,10 +348,14 @@ void free_plan_memory(cwth_plan_s* p) {
     }
     cudaFree(p->d_bank_hi);
     cudaFree(p->d_bank_lo);
+    cudaFree(p->d_bank_lo2);
+    p->d_bank_lo2 = nullptr;
     cudaFree(p->d_bank_f32);
     cudaFree(p->d_status);
     cudaFree(p->d_xhi);
     cudaFree(p->d_xlo);
+    cudaFree(p->d_xlo2);
+    p->d_xlo2 = nullptr;
     p->d_bank_hi = nullptr;
     p->d_bank_lo = nullptr;
     p->d_bank_f32 = nullptr;
@@ -406,6 +413,11 @@ cudaError_t host_pipeline_init(cwth_plan_s* p) {
 
 int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
+// bf16 parts per operand of the tensor-core direct path for a precision.
+int direct_parts(int32_t precision) {
+    return precision == CWTH_PREC_BF16X3 ? 3 : (precision == CWTH_PREC_BF16X2 ? 2 : 1);
+}
+
 // Half support of the direct path's truncated taps, a multiple of 8 so that
 // every group's view of the staged signal starts 16-byte aligned.
 int32_t direct_half_support(double a, double B) {
@@ -415,6 +427,14 @@ int32_t direct_half_support(double a, double B) {
 bool direct_eligible(const cwth_plan_s& p, double a) {
     const int64_t k = round_up(2 * (int64_t)direct_half_support(a, p.B) + 1, 64);
     if (k > kMaxDirectTaps) return false;
+    // Automatic three-part split plans keep the float32 accuracy class on
+    // every input: the tensor cores' float32 accumulation loses low-order
+    // bits along an MMA chain (measured on GB300: a mean relative bias of
+    // -3.5e-6 at 613 taps, -6.5e-6 at 1185, -1.2e-5 at 2297 on white
+    // noise), so scales beyond kSplitAutoTaps padded taps take the float32
+    // spectral path instead.
+    if (p.path == CWTH_PATH_AUTO && p.precision == CWTH_PREC_BF16X3 && k > kSplitAutoTaps)
+        return false;
     if (p.precision != CWTH_PREC_FP32 && p.hop % 8 != 0) return false;
     // The tensor-core epilogue addresses a clip's output with 32-bit offsets.
     if (p.precision != CWTH_PREC_FP32 && (int64_t)p.S * p.frames_max > INT32_MAX) return false;
@@ -477,7 +497,8 @@ cwth_status build_direct(cwth_plan_s* p) {
     std::vector<std::pair<int, int>> ranges;
     for (int i = 0; i < (int)idx.size(); i += 128)
         ranges.push_back({i, std::min<int>((int)idx.size(), i + 128)});
-    const bool split = p->precision == CWTH_PREC_BF16X2;
+    const int nparts = direct_parts(p->precision);
+    const bool split = nparts > 1;
     int64_t bank_elems = 0, f32_elems = 0;
     for (auto& r : ranges) {
         cwth::DirGroup g;
@@ -487,7 +508,7 @@ cwth_status build_direct(cwth_plan_s* p) {
         g.k_pad = (int32_t)round_up(2 * (int64_t)g.h + 1, 64);
         g.bank_off = bank_elems;
         g.f32_off = f32_elems;
-        g.shape = cwth::direct_shape(g.ncols, split, p->hop, g.k_pad);
+        g.shape = cwth::direct_shape(g.ncols, nparts, p->hop, g.k_pad);
         if (g.shape.stages == 0) return CWTH_ERR_UNSUPPORTED;
         bank_elems += (int64_t)g.ncols * g.k_pad;
         f32_elems += (int64_t)g.n_scales * g.k_pad;
@@ -497,11 +518,13 @@ cwth_status build_direct(cwth_plan_s* p) {
     }
     cudaError_t e = cudaMalloc(&p->d_bank_hi, sizeof(__nv_bfloat16) * bank_elems);
     if (e == cudaSuccess) e = cudaMalloc(&p->d_bank_lo, sizeof(__nv_bfloat16) * bank_elems);
+    if (e == cudaSuccess && nparts > 2)
+        e = cudaMalloc(&p->d_bank_lo2, sizeof(__nv_bfloat16) * bank_elems);
     if (e == cudaSuccess) e = cudaMalloc(&p->d_bank_f32, sizeof(float2) * f32_elems);
     if (e == cudaSuccess) e = cudaMalloc(&p->d_status, sizeof(int));
     if (e == cudaSuccess) e = cudaMemsetAsync(p->d_status, 0, sizeof(int), p->setup);
     if (e != cudaSuccess) return cuda_status(e);
-    p->table_bytes += (int64_t)(bank_elems * 4 + f32_elems * 8);
+    p->table_bytes += (int64_t)(bank_elems * 2 * (nparts > 2 ? 3 : 2) + f32_elems * 8);
     for (size_t gi = 0; gi < ranges.size(); ++gi) {
         cwth::DirGroup& g = p->groups[gi];
         std::vector<int32_t> rows, hh;
@@ -520,12 +543,12 @@ cwth_status build_direct(cwth_plan_s* p) {
             e = cudaMemcpyAsync(g.d_h, hh.data(), sizeof(int32_t) * hh.size(), cudaMemcpyHostToDevice, p->setup);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(g.d_scales, sc.data(), sizeof(double) * sc.size(), cudaMemcpyHostToDevice, p->setup);
-        std::vector<int2> sched(g.k_pad / 64), sched2(2 * (g.k_pad / 64));
+        std::vector<int2> sched(g.k_pad / 64), sched2(3 * (g.k_pad / 64));
         g.nsteps = cwth::direct_schedule(
             hh.data(), g.n_scales, g.h, g.k_pad, (g.ncols + 63) / 64,
-            cwth::direct_a_pieces(split, g.shape.unit, g.shape.win_rows > 0), sched.data());
+            cwth::direct_a_pieces(nparts, g.shape.unit, g.shape.win_rows > 0), sched.data());
         if (split) {
-            g.nsteps = cwth::direct_split_schedule(sched.data(), g.nsteps, sched2.data());
+            g.nsteps = cwth::direct_split_schedule(sched.data(), g.nsteps, nparts, sched2.data());
             sched.swap(sched2);
         }
         if (e == cudaSuccess) e = cudaMalloc(&g.d_sched, sizeof(int2) * sched.size());
@@ -534,13 +557,16 @@ cwth_status build_direct(cwth_plan_s* p) {
         if (e == cudaSuccess)
             e = cwth::direct_make_bank(g.d_scales, g.d_h, g.n_scales, g.ncols, g.k_pad, g.h, p->B,
                                        p->C, p->d_bank_hi + g.bank_off, p->d_bank_lo + g.bank_off,
+                                       p->d_bank_lo2 ? p->d_bank_lo2 + g.bank_off : nullptr,
                                        p->d_bank_f32 + g.f32_off, p->setup);
         if (e != cudaSuccess) return cuda_status(e);
         if (p->precision != CWTH_PREC_FP32) {
             if (!encode_bf16_2d(&g.map_b_hi, p->d_bank_hi + g.bank_off, g.k_pad, g.ncols,
                                 (uint64_t)g.k_pad * 2, 64) ||
                 !encode_bf16_2d(&g.map_b_lo, p->d_bank_lo + g.bank_off, g.k_pad, g.ncols,
-                                (uint64_t)g.k_pad * 2, 64)) {
+                                (uint64_t)g.k_pad * 2, 64) ||
+                (nparts > 2 && !encode_bf16_2d(&g.map_b_lo2, p->d_bank_lo2 + g.bank_off, g.k_pad,
+                                               g.ncols, (uint64_t)g.k_pad * 2, 64))) {
                 note_error("cuTensorMapEncodeTiled rejected the tap-bank tensor map");
                 return CWTH_ERR_UNSUPPORTED;
             }
@@ -798,7 +824,7 @@ cwth_status launch_direct(cwth_plan_s* p, const float* d_x, int64_t ld_x, const 
         }
         return CWTH_OK;
     }
-    const bool split = p->precision == CWTH_PREC_BF16X2;
+    const int nparts = direct_parts(p->precision);
     const int64_t hop = p->hop;
     const int64_t rows_per_clip =
         (2 * (int64_t)p->dir_front + p->frames_max * hop + p->dir_taps + hop - 1) / hop;
@@ -809,23 +835,30 @@ cwth_status launch_direct(cwth_plan_s* p, const float* d_x, int64_t ld_x, const 
     if ((size_t)total > p->x_elems) {
         cudaFree(p->d_xhi);
         cudaFree(p->d_xlo);
+        cudaFree(p->d_xlo2);
         p->d_xhi = nullptr;
         p->d_xlo = nullptr;
+        p->d_xlo2 = nullptr;
         p->x_elems = 0;
         p->x_maps_ptr = nullptr;
         cudaError_t e = cudaMalloc(&p->d_xhi, sizeof(__nv_bfloat16) * (size_t)total);
         if (e == cudaSuccess) e = cudaMalloc(&p->d_xlo, sizeof(__nv_bfloat16) * (size_t)total);
+        if (e == cudaSuccess && nparts > 2)
+            e = cudaMalloc(&p->d_xlo2, sizeof(__nv_bfloat16) * (size_t)total);
         if (e != cudaSuccess) return cuda_status(e);
         p->x_elems = (size_t)total;
     }
     if (p->x_maps_ptr != p->d_xhi || p->x_maps_rows != total_rows) {
         p->maps_a_hi.assign(p->groups.size(), CUtensorMap());
         p->maps_a_lo.assign(p->groups.size(), CUtensorMap());
+        p->maps_a_lo2.assign(p->groups.size(), CUtensorMap());
         for (size_t gi = 0; gi < p->groups.size(); ++gi) {
             const cwth::DirGroup& g = p->groups[gi];
             const int64_t off = p->dir_front - g.h;
             if (!encode_bf16_2d(&p->maps_a_hi[gi], p->d_xhi + off, g.k_pad, total_rows, hop * 2, 32) ||
-                !encode_bf16_2d(&p->maps_a_lo[gi], p->d_xlo + off, g.k_pad, total_rows, hop * 2, 32)) {
+                !encode_bf16_2d(&p->maps_a_lo[gi], p->d_xlo + off, g.k_pad, total_rows, hop * 2, 32) ||
+                (nparts > 2 && !encode_bf16_2d(&p->maps_a_lo2[gi], p->d_xlo2 + off, g.k_pad,
+                                               total_rows, hop * 2, 32))) {
                 note_error("cuTensorMapEncodeTiled rejected the frame-matrix tensor map");
                 return CWTH_ERR_UNSUPPORTED;
             }
@@ -834,13 +867,16 @@ cwth_status launch_direct(cwth_plan_s* p, const float* d_x, int64_t ld_x, const 
         p->x_maps_rows = total_rows;
     }
     cudaError_t e = cwth::direct_stage(d_x, ld_x, d_len, p->max_len, batch, p->d_xhi,
-                                       split ? p->d_xlo : nullptr, lpad, p->dir_front, total, st);
+                                       nparts > 1 ? p->d_xlo : nullptr,
+                                       nparts > 2 ? p->d_xlo2 : nullptr, lpad, p->dir_front, total,
+                                       st);
     if (e != cudaSuccess) return cuda_status(e);
     L.rows_per_clip = rows_per_clip;
     L.total_rows = total_rows;
     for (size_t gi = 0; gi < p->groups.size(); ++gi) {
         const cwth::DirGroup& g = p->groups[gi];
-        CUtensorMap maps[4] = {p->maps_a_hi[gi], p->maps_a_lo[gi], g.map_b_hi, g.map_b_lo};
+        CUtensorMap maps[6] = {p->maps_a_hi[gi], p->maps_a_lo[gi], p->maps_a_lo2[gi],
+                               g.map_b_hi,        g.map_b_lo,        g.map_b_lo2};
         L.ncols = g.ncols;
         L.k_pad = g.k_pad;
         L.h_group = g.h;
@@ -856,7 +892,7 @@ cwth_status launch_direct(cwth_plan_s* p, const float* d_x, int64_t ld_x, const 
         L.win_sets = g.shape.win_sets;
         L.acc_sets = g.shape.acc_sets;
         L.tmem_cols = g.shape.tmem_cols;
-        e = cwth::direct_launch_mma(maps, L, split, st);
+        e = cwth::direct_launch_mma(maps, L, nparts, st);
         if (e != cudaSuccess) return cuda_status(e);
     }
     return CWTH_OK;
@@ -983,7 +1019,7 @@ cwth_status plan_create(const cwth_morlet* w, const double* scales, int32_t S, i
     if (!(isfinite(w->bandwidth) && w->bandwidth > 0)) return CWTH_ERR_INVALID_ARG;
     if (!(isfinite(w->center_freq) && w->center_freq > 0)) return CWTH_ERR_INVALID_ARG;
     if (!(isfinite(sample_rate) && sample_rate > 0)) return CWTH_ERR_INVALID_ARG;
-    if (precision < CWTH_PREC_FP32 || precision > CWTH_PREC_BF16X2) return CWTH_ERR_INVALID_ARG;
+    if (precision < CWTH_PREC_FP32 || precision > CWTH_PREC_BF16X3) return CWTH_ERR_INVALID_ARG;
     if (path < CWTH_PATH_AUTO || path > CWTH_PATH_DIRECT) return CWTH_ERR_INVALID_ARG;
     for (int32_t s = 0; s < S; ++s)
         if (!(isfinite(scales[s]) && scales[s] > 0)) return CWTH_ERR_INVALID_ARG;

@@ -108,8 +108,8 @@ struct SpecLaunch {
 // Direct (GEMM) path launch parameters; one launch per scale group.
 constexpr int kMaxDirStages = 6;
 // Schedule steps of one group: at most 4096 taps = 64 tap blocks, each
-// visited once per bank part (two parts in the split variant).
-constexpr int kMaxDirSteps = 128;
+// visited once per bank part (up to three parts in the split variants).
+constexpr int kMaxDirSteps = 192;
 struct DirLaunch {
     float* out;
     int64_t frames_max;
@@ -128,7 +128,7 @@ struct DirLaunch {
     int32_t stages;
     uint32_t tmem_cols;
     int* status;            // device status word (CWTH_ERR_TIMEOUT on a bounded-wait expiry)
-    const int2* sched;      // per K step: {tap block, columns used | bank part << 16}
+    const int2* sched;      // per K step: {tap blocks, columns used | bank part bits}
     int32_t nsteps;
     int32_t a_shift;        // frame-view rows per tap block (64 / hop; per a_phases blocks
                             // when a_phases > 1) when windows serve all blocks, else 0
@@ -165,17 +165,19 @@ cudaError_t spectral_make_twiddles(float2* d_tw, int M, cudaStream_t st);
 cudaError_t spectral_launch(const SpecLaunch& L, int threads, bool prune, int n_seg, int batch,
                             int n_groups, size_t smem, cudaStream_t st);
 
-size_t direct_smem_bytes(int ncols, int stages, bool split, int win_rows, int unit,
+// nparts: bf16 parts of each operand (1 = bf16, 2 = bf16x2, 3 = bf16x3).
+size_t direct_smem_bytes(int ncols, int stages, int nparts, int win_rows, int unit,
                          int win_sets, int phases);
-int direct_max_stages(int ncols, bool split, int win_rows, int unit, int win_sets, int phases);
-DirShape direct_shape(int ncols, bool split, int hop, int k_pad);
+int direct_max_stages(int ncols, int nparts, int win_rows, int unit, int win_sets, int phases);
+DirShape direct_shape(int ncols, int nparts, int hop, int k_pad);
 // Rows of the frame window for hops dividing 64 (0: per-step frame tiles).
 int direct_window_rows(int hop, int k_pad);
 int direct_window_phases(int hop);
 int direct_window_shift(int hop);
-// The split variant's schedule: every step of `in` twice, hi part then lo
-// part (bit 16 of .y); returns 2 n.
-int direct_split_schedule(const int2* in, int n, int2* out);
+// The split variants' schedule: every step of `in` nparts times, bank part
+// j = 0 .. nparts - 1 in bit 16 (j & 1) and bits 19-20 (j >> 1) of .y;
+// returns nparts * n.
+int direct_split_schedule(const int2* in, int n, int nparts, int2* out);
 cudaError_t direct_prepare_device();
 cudaError_t direct_wait_selftest(int* status, long long budget, cudaStream_t st);
 cudaError_t resample_launch(const float* x, int64_t ld_x, const int64_t* lengths, int64_t in_len,
@@ -184,17 +186,19 @@ cudaError_t resample_launch(const float* x, int64_t ld_x, const int64_t* lengths
 cudaError_t direct_prepare_f32(size_t smem);
 cudaError_t direct_make_bank(const double* d_scales, const int32_t* d_h, int n_scales, int ncols,
                              int k_pad, int h_group, double B, double C, __nv_bfloat16* hi,
-                             __nv_bfloat16* lo, float2* f32bank, cudaStream_t st);
+                             __nv_bfloat16* lo, __nv_bfloat16* lo2, float2* f32bank,
+                             cudaStream_t st);
 cudaError_t direct_stage(const float* x, int64_t ld_x, const int64_t* lengths, int64_t max_len,
-                         int batch, __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t lpad,
-                         int64_t h_front, int64_t total, cudaStream_t st);
-cudaError_t direct_launch_mma(const CUtensorMap* maps, const DirLaunch& L, bool split,
+                         int batch, __nv_bfloat16* hi, __nv_bfloat16* lo, __nv_bfloat16* lo2,
+                         int64_t lpad, int64_t h_front, int64_t total, cudaStream_t st);
+// maps: {A part 0, 1, 2, bank part 0, 1, 2}; parts past nparts unused.
+cudaError_t direct_launch_mma(const CUtensorMap* maps, const DirLaunch& L, int nparts,
                               cudaStream_t st);
 // Centre-out K-block schedule of one group (supports in descending order):
 // out[i] = {tap block, columns}; returns the number of steps (<= k_pad / 64).
 int direct_schedule(const int32_t* h_desc, int n, int h_group, int k_pad, int stage_pieces,
                     int a_pieces, int2* out);
-int direct_a_pieces(bool split, int unit, bool windowed);
+int direct_a_pieces(int nparts, int unit, bool windowed);
 cudaError_t direct_launch_f32(const float* x, int64_t ld_x, const float2* bank, const int32_t* d_h,
                               const DirLaunch& L, cudaStream_t st);
 
@@ -212,7 +216,7 @@ struct DirGroup {
     double* d_scales = nullptr;
     int2* d_sched = nullptr;
     int32_t nsteps = 0;
-    CUtensorMap map_b_hi, map_b_lo;
+    CUtensorMap map_b_hi, map_b_lo, map_b_lo2;
 };
 
 }  // namespace cwth
@@ -250,14 +254,16 @@ struct cwth_plan_s {
     std::vector<cwth::DirGroup> groups;
     __nv_bfloat16* d_bank_hi = nullptr;
     __nv_bfloat16* d_bank_lo = nullptr;
+    __nv_bfloat16* d_bank_lo2 = nullptr;
     float2* d_bank_f32 = nullptr;
     int* d_status = nullptr;
     // staged bf16 signal (workspace), grown on demand
     __nv_bfloat16* d_xhi = nullptr;
     __nv_bfloat16* d_xlo = nullptr;
+    __nv_bfloat16* d_xlo2 = nullptr;
     size_t x_elems = 0;
     // A-operand tensor maps per group, valid for (x_maps_ptr, x_maps_rows)
-    std::vector<CUtensorMap> maps_a_hi, maps_a_lo;
+    std::vector<CUtensorMap> maps_a_hi, maps_a_lo, maps_a_lo2;
     const void* x_maps_ptr = nullptr;
     int64_t x_maps_rows = -1;
 

@@ -17,10 +17,15 @@
 //   warp 0      TMA producer (frame windows or A tiles, bank tiles, 128B swizzle)
 //   warp 1      TMEM allocation + elected-lane MMA issue (M=128, N<=256, K=16)
 //   warps 2..9  epilogue: tcgen05.ld, |re + i im|, coalesced stores along k
-// The split variant ("bf16x2") represents x = x_hi + x_lo and g = g_hi + g_lo
-// (each pair within 2^-18 of its value) and accumulates all four products
-// into the same tensor-memory accumulator, so every tap product is within
-// about 2^-17 relative of x * g even when a frame has a single tap.  Every mbarrier wait is bounded; on a timeout the CTA
+// The split variants represent x and g as sums of bf16 parts, x = x_0 + x_1
+// (+ x_2), each part the bf16 rounding of what the earlier ones leave, and
+// accumulate the part products into the same tensor-memory accumulator:
+// "bf16x2" (two parts, within 2^-18 of each value) takes all four products,
+// so every tap product is within about 2^-17 relative of x * g; "bf16x3"
+// (three parts, within 2^-26) takes the six products x_i g_j with
+// i + j <= 2, within about 2^-24 relative (the dropped ones are smaller
+// still), which holds the sum to float32 accuracy even where the tap
+// products cancel.  Every mbarrier wait is bounded; on a timeout the CTA
 // records CWTH_ERR_TIMEOUT in a device status word, drains its own TMA
 // copies (bounded), releases tensor memory and returns.
 #include <cuda_bf16.h>
@@ -56,13 +61,16 @@ __device__ __forceinline__ float sqrt_approx(float v) {
 
 // ------------------------------------------------------------ staging
 // x_pad[b][j] = x[b][j - h_front] for j - h_front in [0, len_b), else 0;
-// hi = bf16(x), lo = bf16(x - hi).  Row b = batch is the zero tail after the
-// last clip.  Each thread writes 8 consecutive bf16 (one 16-byte store per
-// buffer); rows and the tail are multiples of 8 elements long.
+// part 0 = bf16(x), part 1 = bf16(x - part 0), part 2 = bf16(x - part 0 -
+// part 1) (the differences are exact in float32).  Row b = batch is the
+// zero tail after the last clip.  Each thread writes 8 consecutive bf16
+// (one 16-byte store per buffer); rows and the tail are multiples of 8
+// elements long.  Null part buffers are not written.
 __global__ void stage_bf16_kernel(const float* __restrict__ x, int64_t ld_x,
                                   const int64_t* __restrict__ lengths, int64_t max_len, int batch,
                                   __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo,
-                                  int64_t lpad, int64_t h_front, int64_t total) {
+                                  __nv_bfloat16* __restrict__ lo2, int64_t lpad, int64_t h_front,
+                                  int64_t total) {
     const int b = blockIdx.y;
     const int64_t row_len = b < batch ? lpad : total - (int64_t)batch * lpad;
     int64_t len = 0;
@@ -74,7 +82,7 @@ __global__ void stage_bf16_kernel(const float* __restrict__ x, int64_t ld_x,
     const int64_t base = (int64_t)b * lpad;
     for (int64_t j0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 8; j0 < row_len;
          j0 += (int64_t)gridDim.x * blockDim.x * 8) {
-        uint32_t wh[4], wl[4];
+        uint32_t wh[4], wl[4], w2[4];
 #pragma unroll
         for (int e = 0; e < 8; e += 2) {
             float v[2];
@@ -85,23 +93,30 @@ __global__ void stage_bf16_kernel(const float* __restrict__ x, int64_t ld_x,
             }
             const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[0], v[1]);
             const float2 hf = __bfloat1622float2(h2);
-            const __nv_bfloat162 l2 = __floats2bfloat162_rn(v[0] - hf.x, v[1] - hf.y);
+            const float r0 = v[0] - hf.x, r1 = v[1] - hf.y;
+            const __nv_bfloat162 l2 = __floats2bfloat162_rn(r0, r1);
+            const float2 lf = __bfloat1622float2(l2);
+            const __nv_bfloat162 m2 = __floats2bfloat162_rn(r0 - lf.x, r1 - lf.y);
             wh[e >> 1] = *reinterpret_cast<const uint32_t*>(&h2);
             wl[e >> 1] = *reinterpret_cast<const uint32_t*>(&l2);
+            w2[e >> 1] = *reinterpret_cast<const uint32_t*>(&m2);
         }
         *reinterpret_cast<uint4*>(hi + base + j0) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
         if (lo) *reinterpret_cast<uint4*>(lo + base + j0) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
+        if (lo2) *reinterpret_cast<uint4*>(lo2 + base + j0) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
     }
 }
 
 // ------------------------------------------------------------ tap bank (float64)
-// bank[n][tau] for column n of a group: scale j = n / 2 (real part for even n,
+// bank[n][tau] for column n of a group (parts as the staged signal's: hi,
+// lo = bf16 of the remainder, lo2 = bf16 of what is left; lo2 may be
+// null): scale j = n / 2 (real part for even n,
 // imaginary for odd n), tap t = tau - h_group, value a^{-1/2} conj(psi(t/a))
 // for |t| <= h_j, else 0.  Columns past 2 * n_scales are zero.
 __global__ void bank_kernel(const double* __restrict__ scales, const int32_t* __restrict__ h_of,
                             int n_scales, int ncols, int k_pad, int h_group, double B, double C,
                             __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo,
-                            float2* __restrict__ f32bank) {
+                            __nv_bfloat16* __restrict__ lo2, float2* __restrict__ f32bank) {
     const int64_t total = (int64_t)ncols * k_pad;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -122,7 +137,10 @@ __global__ void bank_kernel(const double* __restrict__ scales, const int32_t* __
         }
         const __nv_bfloat16 h = __float2bfloat16_rn((float)v);
         hi[i] = h;
-        lo[i] = __float2bfloat16_rn((float)(v - (double)__bfloat162float(h)));
+        const double r = v - (double)__bfloat162float(h);
+        const __nv_bfloat16 l = __float2bfloat16_rn((float)r);
+        lo[i] = l;
+        if (lo2) lo2[i] = __float2bfloat16_rn((float)(r - (double)__bfloat162float(l)));
         if (f32bank && j < n_scales) {
             // float32 copy for the SIMT kernel: [scale][tau] as (re, im)
             float* f = reinterpret_cast<float*>(f32bank + (int64_t)j * k_pad + tau);
@@ -143,16 +161,19 @@ __global__ void bank_kernel(const double* __restrict__ scales, const int32_t* __
 //
 // Shared-memory layout (1024-byte aligned pieces):
 //   windows: [set][tile][part][phase]   only when p.a_shift > 0 (see below)
-//   stage s: [A tile 0 hi][A tile 0 lo][A tile 1 hi][A tile 1 lo] ... [B]
-//            (A parts only without a window; lo parts only when split)
+//   stage s: [A tile 0 part 0][A tile 0 part 1]..[A tile 1 part 0].. [B]
+//            (A parts only without a window; NP parts per tile)
 // Schedule step j: up to four tap blocks, block b in bits 8b..8b+7 of
 // sched[j].x; sched[j].y = columns used (low 16 bits, a multiple of 16) |
-// bank part (bit 16: 0 = hi, 1 = lo) | blocks - 1 (bits 17-18).  A step of
+// bank part (bit 16: 0 = hi, 1 = lo; bits 19-20: part 2) | blocks - 1
+// (bits 17-18).  A step of
 // several blocks carries all their tiles in one stage, each block as [A
 // tiles (without a window)][bank tile] at the same column count, so the
 // narrow outer blocks of the pyramid share stage turns (4 MMAs per block).
-// The split variant visits every step twice, once per bank part; the plain
-// variant uses the hi part only.
+// The split variants visit every step once per bank part (NP times); the
+// plain variant uses the hi part only.  Bank part j meets the A parts
+// 0 .. NP - 1 (two parts: all four products) or, with three parts, 0 ..
+// 2 - j (the six products x_i g_j with i + j <= 2).
 // When 64 is a multiple of the hop, the frame tile of tap block kb is the
 // tile of block 0 moved down by kb * 64 / H rows of the frame view, so one
 // window of 128 + (blocks - 1) * 64/H rows per tile, loaded once, serves
@@ -161,12 +182,14 @@ __global__ void bank_kernel(const double* __restrict__ scales, const int32_t* __
 // 64 ph .. 64 ph + 63 of frame rows moved down by j: r windows ("phases",
 // loaded at tap offset 64 ph) of 128 + ceil(blocks / r) - 1 rows serve all
 // blocks the same way.
-template <bool SPLIT>
+template <int NP>
 __global__ void __launch_bounds__(kDirThreads, 1)
     direct_mma_kernel(const __grid_constant__ CUtensorMap mA_hi,
                       const __grid_constant__ CUtensorMap mA_lo,
+                      const __grid_constant__ CUtensorMap mA_lo2,
                       const __grid_constant__ CUtensorMap mB_hi,
-                      const __grid_constant__ CUtensorMap mB_lo, const DirLaunch p) {
+                      const __grid_constant__ CUtensorMap mB_lo,
+                      const __grid_constant__ CUtensorMap mB_lo2, const DirLaunch p) {
     extern __shared__ uint8_t dsmem_raw[];
     __shared__ __align__(8) uint64_t full_bar[kMaxDirStages];
     __shared__ __align__(8) uint64_t empty_bar[kMaxDirStages];
@@ -178,7 +201,7 @@ __global__ void __launch_bounds__(kDirThreads, 1)
     __shared__ int2 sched_sh[kMaxDirSteps];
 
     uint8_t* smem = (uint8_t*)(((uintptr_t)dsmem_raw + 1023) & ~(uintptr_t)1023);
-    constexpr int kParts = SPLIT ? 2 : 1;
+    constexpr int kParts = NP;
     const int N = p.ncols;
     const int T = p.unit;
     const int stages = p.stages;
@@ -222,9 +245,13 @@ __global__ void __launch_bounds__(kDirThreads, 1)
         fence_mbar_init();
         prefetch_tensormap(&mA_hi);
         prefetch_tensormap(&mB_hi);
-        if (SPLIT) {
+        if (NP > 1) {
             prefetch_tensormap(&mA_lo);
             prefetch_tensormap(&mB_lo);
+        }
+        if (NP > 2) {
+            prefetch_tensormap(&mA_lo2);
+            prefetch_tensormap(&mB_lo2);
         }
     }
     if (warp == 1) {
@@ -239,6 +266,7 @@ __global__ void __launch_bounds__(kDirThreads, 1)
     auto win_ptr = [&](int set, int tile, int part, int ph) {
         return smem + (((size_t)(set * T + tile) * kParts + part) * phases + ph) * win_span;
     };
+    auto amap = [&](int part) { return part == 0 ? &mA_hi : (part == 1 ? &mA_lo : &mA_lo2); };
     auto aborted = [&]() { return *(volatile int*)&abort_sh != 0; };
     auto fail = [&]() { atomicExch(&abort_sh, 1); };
 
@@ -265,13 +293,10 @@ __global__ void __launch_bounds__(kDirThreads, 1)
                     for (int tt = 0; tt < T; ++tt) {
                         const int m0 = (u * T + tt) * kBM;
                         for (int ph = 0; ph < phases; ++ph)
-                            for (int j = 0; j < p.win_rows / kAPieceRows; ++j) {
-                                tma_load_2d(win_ptr(ws, tt, 0, ph) + j * kPiece, &mA_hi,
-                                            &win_full[ws], ph * kBK, m0 + j * kAPieceRows);
-                                if (SPLIT)
-                                    tma_load_2d(win_ptr(ws, tt, 1, ph) + j * kPiece, &mA_lo,
+                            for (int j = 0; j < p.win_rows / kAPieceRows; ++j)
+                                for (int part = 0; part < kParts; ++part)
+                                    tma_load_2d(win_ptr(ws, tt, part, ph) + j * kPiece, amap(part),
                                                 &win_full[ws], ph * kBK, m0 + j * kAPieceRows);
-                            }
                     }
                 }
                 __syncwarp();
@@ -296,7 +321,9 @@ __global__ void __launch_bounds__(kDirThreads, 1)
                 if (elect_one()) {
                     const int pieces = ((step.y & 0xFFFF) + 63) >> 6;
                     const int nblk = 1 + ((step.y >> 17) & 3);
-                    const CUtensorMap* mb = (SPLIT && ((step.y >> 16) & 1)) ? &mB_lo : &mB_hi;
+                    const int bpart = ((step.y >> 16) & 1) | (((step.y >> 19) & 3) << 1);
+                    const CUtensorMap* mb =
+                        (NP > 1 && bpart == 1) ? &mB_lo : ((NP > 2 && bpart == 2) ? &mB_lo2 : &mB_hi);
                     uint8_t* st = stage0 + (size_t)s * stage_bytes;
                     mbar_arrive_expect_tx(&full_bar[s],
                                           (uint32_t)nblk * (a_step + (uint32_t)pieces * 64 * kBK * 2));
@@ -308,14 +335,11 @@ __global__ void __launch_bounds__(kDirThreads, 1)
                         if (!shift) {
                             for (int tt = 0; tt < T; ++tt) {
                                 const int m0 = (u * T + tt) * kBM;
-                                for (int q = 0; q < kBM / kAPieceRows; ++q) {
-                                    tma_load_2d(sb + (tt * kParts) * a_tile + q * kPiece, &mA_hi,
-                                                &full_bar[s], kxb, m0 + q * kAPieceRows);
-                                    if (SPLIT)
-                                        tma_load_2d(sb + (tt * kParts + 1) * a_tile + q * kPiece,
-                                                    &mA_lo, &full_bar[s], kxb,
+                                for (int q = 0; q < kBM / kAPieceRows; ++q)
+                                    for (int part = 0; part < kParts; ++part)
+                                        tma_load_2d(sb + (tt * kParts + part) * a_tile + q * kPiece,
+                                                    amap(part), &full_bar[s], kxb,
                                                     m0 + q * kAPieceRows);
-                                }
                             }
                         }
                         for (int q = 0; q < pieces; ++q)
@@ -390,6 +414,9 @@ __global__ void __launch_bounds__(kDirThreads, 1)
                         a_step16 + (uint32_t)(((step.y & 0xFFFF) + 63) >> 6) * 512u;
                     const uint32_t kb_all = (uint32_t)step.x;
                     const uint32_t acc0 = j > 0 ? 1u : 0u;
+                    // A parts this bank part meets (see the kernel comment)
+                    const int bpart = ((step.y >> 16) & 1) | (((step.y >> 19) & 3) << 1);
+                    const int na = NP == 3 ? 3 - bpart : NP;
                     if (!mbar_wait(&full_bar[s], sph, kWaitBudget)) {
                         fail();
                         ok = false;
@@ -408,16 +435,19 @@ __global__ void __launch_bounds__(kDirThreads, 1)
                         for (int tt = 0; tt < T; ++tt) {
                             const uint32_t dacc = dacc0 + (uint32_t)tt * acc_cols;
                             const uint32_t ah = a_lo + (uint32_t)(tt * kParts) * pitch16;
-                            const uint32_t al = ah + (uint32_t)(kParts - 1) * pitch16;
 #pragma unroll
                             for (int k = 0; k < kBK / 16; ++k) {
                                 // 16 bf16 = 32 bytes along K -> +2 in the address field
                                 const uint64_t bd = desc_words(bb + 2 * k, kDescSw128Hi);
                                 mma_f16(dacc, desc_words(ah + 2 * k, kDescSw128Hi), bd, idesc,
                                         (acc0 | (uint32_t)b | (uint32_t)k) ? 1u : 0u);
-                                if (SPLIT)
-                                    mma_f16(dacc, desc_words(al + 2 * k, kDescSw128Hi), bd, idesc,
-                                            1u);
+#pragma unroll
+                                for (int ap = 1; ap < NP; ++ap)
+                                    if (ap < na)
+                                        mma_f16(dacc,
+                                                desc_words(ah + (uint32_t)ap * pitch16 + 2 * k,
+                                                           kDescSw128Hi),
+                                                bd, idesc, 1u);
                             }
                         }
                     }
@@ -553,9 +583,9 @@ __global__ void __launch_bounds__(128) direct_f32_kernel(const float* __restrict
 // CTA allocates both tensor-memory accumulators).
 constexpr size_t kDirSmemMin = 120 * 1024;
 
-size_t direct_smem_bytes(int ncols, int stages, bool split, int win_rows, int unit,
+size_t direct_smem_bytes(int ncols, int stages, int nparts, int win_rows, int unit,
                          int win_sets, int phases) {
-    const size_t parts = split ? 2 : 1;
+    const size_t parts = (size_t)nparts;
     const size_t brows = (size_t)(ncols + 63) / 64 * 64;
     const size_t a = win_rows > 0 ? 0 : (size_t)kBM * kBK * 2 * parts * unit;
     const size_t stage = a + brows * kBK * 2;
@@ -589,31 +619,31 @@ int direct_window_rows(int hop, int k_pad) {
     return (rows + kAPieceRows - 1) / kAPieceRows * kAPieceRows;
 }
 
-int direct_split_schedule(const int2* in, int n, int2* out) {
-    for (int i = 0; i < n; ++i) {
-        out[2 * i] = in[i];
-        out[2 * i + 1] = make_int2(in[i].x, in[i].y | (1 << 16));
-    }
-    return 2 * n;
+int direct_split_schedule(const int2* in, int n, int nparts, int2* out) {
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < nparts; ++j)
+            out[nparts * i + j] = make_int2(in[i].x, in[i].y | ((j & 1) << 16) | ((j >> 1) << 19));
+    return nparts * n;
 }
 
 // Dynamic shared memory a direct CTA may request: the 227 KB opt-in limit
 // less room for the kernel's static shared memory (barriers, the per-scale
-// output offsets and the schedule: under 2 KB).
-constexpr size_t kDirSmemLimit = 227 * 1024 - 2048;
+// output offsets and the schedule: under 3 KB).
+constexpr size_t kDirSmemLimit = 227 * 1024 - 3072;
 
 // A stage's A tiles (frames; none with a frame window) in 8 KB pieces.
-int direct_a_pieces(bool split, int unit, bool windowed) {
-    return windowed ? 0 : kBM * (split ? 2 : 1) * unit / 64;
+int direct_a_pieces(int nparts, int unit, bool windowed) {
+    return windowed ? 0 : kBM * nparts * unit / 64;
 }
 
-int direct_max_stages(int ncols, bool split, int win_rows, int unit, int win_sets, int phases) {
+int direct_max_stages(int ncols, int nparts, int win_rows, int unit, int win_sets, int phases) {
     int s = kMaxDirStages;
     while (s > 2 &&
-           direct_smem_bytes(ncols, s, split, win_rows, unit, win_sets, phases) > kDirSmemLimit)
+           direct_smem_bytes(ncols, s, nparts, win_rows, unit, win_sets, phases) > kDirSmemLimit)
         --s;
-    return direct_smem_bytes(ncols, s, split, win_rows, unit, win_sets, phases) <= kDirSmemLimit ? s
-                                                                                                : 0;
+    return direct_smem_bytes(ncols, s, nparts, win_rows, unit, win_sets, phases) <= kDirSmemLimit
+               ? s
+               : 0;
 }
 
 // Launch shape of a group: frame tiles per unit, window and accumulator
@@ -621,7 +651,7 @@ int direct_max_stages(int ncols, bool split, int win_rows, int unit, int win_set
 // sets still fit in tensor memory (N <= 128): measured on GB300, exposing
 // the epilogue (two 256-column tiles filling all 512 columns) costs more
 // than the halved bank traffic saves.
-DirShape direct_shape(int ncols, bool split, int hop, int k_pad) {
+DirShape direct_shape(int ncols, int nparts, int hop, int k_pad) {
     DirShape best{};
     int cpow = 32;
     while (cpow < ncols) cpow <<= 1;
@@ -633,7 +663,7 @@ DirShape direct_shape(int ncols, bool split, int hop, int k_pad) {
             if (wrows == 0 && win > 0 && best.stages > 0) continue;
             const int ph = wrows ? direct_window_phases(hop) : 1;
             for (int wsets = (wrows ? 2 : 1); wsets >= 1; --wsets) {
-                const int st = direct_max_stages(ncols, split, wrows, unit, wsets, ph);
+                const int st = direct_max_stages(ncols, nparts, wrows, unit, wsets, ph);
                 if (st >= (wsets == 2 ? 3 : 2)) {
                     best.unit = unit;
                     best.acc_sets = asets;
@@ -651,38 +681,41 @@ DirShape direct_shape(int ncols, bool split, int hop, int k_pad) {
 }
 
 cudaError_t direct_prepare_device() {
-    cudaError_t e = cudaFuncSetAttribute(direct_mma_kernel<false>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kDirSmemLimit);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(direct_mma_kernel<true>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDirSmemLimit);
+    cudaError_t e = cudaSuccess;
+    for (const void* f : {(const void*)direct_mma_kernel<1>, (const void*)direct_mma_kernel<2>,
+                          (const void*)direct_mma_kernel<3>})
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kDirSmemLimit);
+    return e;
 }
 
 cudaError_t direct_make_bank(const double* d_scales, const int32_t* d_h, int n_scales, int ncols,
                              int k_pad, int h_group, double B, double C, __nv_bfloat16* hi,
-                             __nv_bfloat16* lo, float2* f32bank, cudaStream_t st) {
+                             __nv_bfloat16* lo, __nv_bfloat16* lo2, float2* f32bank,
+                             cudaStream_t st) {
     const int64_t total = (int64_t)ncols * k_pad;
     const int blocks = (int)std::min<int64_t>((total + 255) / 256, 4096);
     bank_kernel<<<blocks, 256, 0, st>>>(d_scales, d_h, n_scales, ncols, k_pad, h_group, B, C, hi,
-                                        lo, f32bank);
+                                        lo, lo2, f32bank);
     return cudaGetLastError();
 }
 
 cudaError_t direct_stage(const float* x, int64_t ld_x, const int64_t* lengths, int64_t max_len,
-                         int batch, __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t lpad,
-                         int64_t h_front, int64_t total, cudaStream_t st) {
+                         int batch, __nv_bfloat16* hi, __nv_bfloat16* lo, __nv_bfloat16* lo2,
+                         int64_t lpad, int64_t h_front, int64_t total, cudaStream_t st) {
     // lpad and the tail are multiples of 8 elements (hop % 8 == 0, supports
     // and tap counts multiples of 8), so every 16-byte store is aligned.
     const int64_t longest = std::max<int64_t>(lpad, total - (int64_t)batch * lpad);
     const unsigned bx = (unsigned)std::min<int64_t>((longest / 8 + 255) / 256, 1024);
     dim3 grid(bx > 0 ? bx : 1, (unsigned)batch + 1);
-    stage_bf16_kernel<<<grid, 256, 0, st>>>(x, ld_x, lengths, max_len, batch, hi, lo, lpad,
+    stage_bf16_kernel<<<grid, 256, 0, st>>>(x, ld_x, lengths, max_len, batch, hi, lo, lo2, lpad,
                                             h_front, total);
     return cudaGetLastError();
 }
 
-cudaError_t direct_launch_mma(const CUtensorMap* maps, const DirLaunch& L, bool split,
+// maps: {A part 0, 1, 2, bank part 0, 1, 2}; parts past nparts are unused.
+cudaError_t direct_launch_mma(const CUtensorMap* maps, const DirLaunch& L, int nparts,
                               cudaStream_t st) {
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -690,14 +723,18 @@ cudaError_t direct_launch_mma(const CUtensorMap* maps, const DirLaunch& L, bool 
     if (e != cudaSuccess) return e;
     const int64_t units = ((L.total_rows + kBM - 1) / kBM + L.unit - 1) / L.unit;
     const int64_t tiles = std::min<int64_t>(units, sms);
-    const size_t smem = direct_smem_bytes(L.ncols, L.stages, split, L.a_shift ? L.win_rows : 0,
+    const size_t smem = direct_smem_bytes(L.ncols, L.stages, nparts, L.a_shift ? L.win_rows : 0,
                                           L.unit, L.win_sets, L.a_phases);
-    if (split)
-        direct_mma_kernel<true><<<(unsigned)tiles, kDirThreads, smem, st>>>(maps[0], maps[1],
-                                                                           maps[2], maps[3], L);
+    const dim3 grid((unsigned)tiles);
+    if (nparts == 3)
+        direct_mma_kernel<3><<<grid, kDirThreads, smem, st>>>(maps[0], maps[1], maps[2], maps[3],
+                                                             maps[4], maps[5], L);
+    else if (nparts == 2)
+        direct_mma_kernel<2><<<grid, kDirThreads, smem, st>>>(maps[0], maps[1], maps[1], maps[3],
+                                                             maps[4], maps[4], L);
     else
-        direct_mma_kernel<false><<<(unsigned)tiles, kDirThreads, smem, st>>>(maps[0], maps[0],
-                                                                            maps[2], maps[2], L);
+        direct_mma_kernel<1><<<grid, kDirThreads, smem, st>>>(maps[0], maps[0], maps[0], maps[3],
+                                                             maps[3], maps[3], L);
     return cudaGetLastError();
 }
 

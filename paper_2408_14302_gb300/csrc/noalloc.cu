@@ -133,8 +133,11 @@ cwth_status cwth_execute_direct_noalloc(const cwth_morlet* w, const double* scal
     if (!w || !scales) return fail(CWTH_ERR_INVALID_ARG, "NULL wavelet or scale list");
     if (S < 1 || S > kMaxScales) return fail(CWTH_ERR_INVALID_ARG, "S must be in [1, 1024]");
     if (hop < 8 || hop % 8 != 0) return fail(CWTH_ERR_INVALID_ARG, "hop must be a positive multiple of 8");
-    if (precision != CWTH_PREC_BF16 && precision != CWTH_PREC_BF16X2)
-        return fail(CWTH_ERR_INVALID_ARG, "precision must be CWTH_PREC_BF16 or CWTH_PREC_BF16X2");
+    if (precision != CWTH_PREC_BF16 && precision != CWTH_PREC_BF16X2 &&
+        precision != CWTH_PREC_BF16X3)
+        return fail(CWTH_ERR_INVALID_ARG,
+                    "precision must be CWTH_PREC_BF16, CWTH_PREC_BF16X2 or CWTH_PREC_BF16X3");
+    const int nparts = precision == CWTH_PREC_BF16X3 ? 3 : (precision == CWTH_PREC_BF16X2 ? 2 : 1);
     if (!(isfinite(w->bandwidth) && w->bandwidth > 0 && isfinite(w->center_freq) &&
           w->center_freq > 0))
         return fail(CWTH_ERR_INVALID_ARG, "bandwidth and centre frequency must be positive");
@@ -198,7 +201,7 @@ cwth_status cwth_execute_direct_noalloc(const cwth_morlet* w, const double* scal
     const size_t o_rows = take(sizeof(int32_t) * S);
     const size_t o_h = take(sizeof(int32_t) * S);
     const size_t o_sc = take(sizeof(double) * S);
-    const size_t o_sched = take(sizeof(int2) * 2 * (kMaxTaps / 64) * ((kMaxScales + kScalesPerGroup - 1) / kScalesPerGroup));
+    const size_t o_sched = take(sizeof(int2) * 3 * (kMaxTaps / 64) * ((kMaxScales + kScalesPerGroup - 1) / kScalesPerGroup));
     size_t o_bank[(kMaxScales + kScalesPerGroup - 1) / kScalesPerGroup];
     int32_t ncols[(kMaxScales + kScalesPerGroup - 1) / kScalesPerGroup];
     int32_t kpad[(kMaxScales + kScalesPerGroup - 1) / kScalesPerGroup];
@@ -207,11 +210,11 @@ cwth_status cwth_execute_direct_noalloc(const cwth_morlet* w, const double* scal
         const int n = std::min(S, first + kScalesPerGroup) - first;
         ncols[g] = (int32_t)rup(2 * n, 16);
         kpad[g] = (int32_t)rup(2 * (int64_t)h_sorted[first] + 1, 64);
-        o_bank[g] = take((size_t)ncols[g] * kpad[g] * 2 * sizeof(__nv_bfloat16));
+        o_bank[g] = take((size_t)ncols[g] * kpad[g] * (nparts > 2 ? 3 : 2) * sizeof(__nv_bfloat16));
     }
     if (total_rows > (int64_t(1) << 31) - 256)
         return fail(CWTH_ERR_INVALID_ARG, "batch too large for one launch");
-    const size_t o_sig = take((size_t)sig_elems * 2 * sizeof(__nv_bfloat16));
+    const size_t o_sig = take((size_t)sig_elems * (nparts > 2 ? 3 : 2) * sizeof(__nv_bfloat16));
     if (off > kNoAllocScratchBytes) {
         char buf[256];
         snprintf(buf, sizeof(buf),
@@ -237,6 +240,7 @@ cwth_status cwth_execute_direct_noalloc(const cwth_morlet* w, const double* scal
     double* d_sc = (double*)(base + o_sc);
     __nv_bfloat16* d_xhi = (__nv_bfloat16*)(base + o_sig);
     __nv_bfloat16* d_xlo = d_xhi + sig_elems;
+    __nv_bfloat16* d_xlo2 = d_xlo + sig_elems;
 
     // The small tables are rewritten on every call, the banks and the staged
     // signal in full by their kernels.  The status word is not: it keeps a
@@ -248,21 +252,21 @@ cwth_status cwth_execute_direct_noalloc(const cwth_morlet* w, const double* scal
     if (e != cudaSuccess) return fail_cuda(e);
 
     // Centre-out K schedules of all groups, one slot of kMaxTaps/64 steps each.
-    const bool split = precision == CWTH_PREC_BF16X2;
-    int2 sched[(kMaxScales + kScalesPerGroup - 1) / kScalesPerGroup][2 * (kMaxTaps / 64)];
+    const bool split = nparts > 1;
+    int2 sched[(kMaxScales + kScalesPerGroup - 1) / kScalesPerGroup][3 * (kMaxTaps / 64)];
     int32_t nsteps[(kMaxScales + kScalesPerGroup - 1) / kScalesPerGroup];
     int2* d_sched = (int2*)(base + o_sched);
     for (int g = 0; g < n_groups; ++g) {
         const int first = g * kScalesPerGroup;
         const int n = std::min(S, first + kScalesPerGroup) - first;
         int2 one[kMaxTaps / 64];
-        const cwth::DirShape sh = cwth::direct_shape(ncols[g], split, hop, kpad[g]);
+        const cwth::DirShape sh = cwth::direct_shape(ncols[g], nparts, hop, kpad[g]);
         nsteps[g] = cwth::direct_schedule(h_sorted + first, n, h_sorted[first], kpad[g],
                                           (ncols[g] + 63) / 64,
-                                          cwth::direct_a_pieces(split, sh.unit, sh.win_rows > 0),
+                                          cwth::direct_a_pieces(nparts, sh.unit, sh.win_rows > 0),
                                           one);
         if (split)
-            nsteps[g] = cwth::direct_split_schedule(one, nsteps[g], sched[g]);
+            nsteps[g] = cwth::direct_split_schedule(one, nsteps[g], nparts, sched[g]);
         else
             for (int i = 0; i < nsteps[g]; ++i) sched[g][i] = one[i];
     }
@@ -275,11 +279,13 @@ cwth_status cwth_execute_direct_noalloc(const cwth_morlet* w, const double* scal
         __nv_bfloat16* bhi = (__nv_bfloat16*)(base + o_bank[g]);
         __nv_bfloat16* blo = bhi + (size_t)ncols[g] * kpad[g];
         e = cwth::direct_make_bank(d_sc + first, d_h + first, n, ncols[g], kpad[g],
-                                   h_sorted[first], w->bandwidth, w->center_freq, bhi,
-                                   blo, nullptr, strm);
+                                   h_sorted[first], w->bandwidth, w->center_freq, bhi, blo,
+                                   nparts > 2 ? blo + (size_t)ncols[g] * kpad[g] : nullptr,
+                                   nullptr, strm);
         if (e != cudaSuccess) return fail_cuda(e);
     }
     e = cwth::direct_stage(d_x, ld_x, d_lengths, max_len, batch, d_xhi, split ? d_xlo : nullptr,
+                           nparts > 2 ? d_xlo2 : nullptr,
                            lpad, front, sig_elems, strm);
     if (e != cudaSuccess) return fail_cuda(e);
 
@@ -301,19 +307,23 @@ cwth_status cwth_execute_direct_noalloc(const cwth_morlet* w, const double* scal
         const int32_t hg = h_sorted[first];
         __nv_bfloat16* bhi = (__nv_bfloat16*)(base + o_bank[g]);
         __nv_bfloat16* blo = bhi + (size_t)ncols[g] * kpad[g];
-        CUtensorMap maps[4];
+        CUtensorMap maps[6];
+        __nv_bfloat16* blo2 = blo + (size_t)ncols[g] * kpad[g];
         const int64_t aoff = front - hg;
         if (!encode(&maps[0], d_xhi + aoff, kpad[g], total_rows, (uint64_t)hop * 2, 32) ||
             !encode(&maps[1], d_xlo + aoff, kpad[g], total_rows, (uint64_t)hop * 2, 32) ||
-            !encode(&maps[2], bhi, kpad[g], ncols[g], (uint64_t)kpad[g] * 2, 64) ||
-            !encode(&maps[3], blo, kpad[g], ncols[g], (uint64_t)kpad[g] * 2, 64))
+            (nparts > 2 &&
+             !encode(&maps[2], d_xlo2 + aoff, kpad[g], total_rows, (uint64_t)hop * 2, 32)) ||
+            !encode(&maps[3], bhi, kpad[g], ncols[g], (uint64_t)kpad[g] * 2, 64) ||
+            !encode(&maps[4], blo, kpad[g], ncols[g], (uint64_t)kpad[g] * 2, 64) ||
+            (nparts > 2 && !encode(&maps[5], blo2, kpad[g], ncols[g], (uint64_t)kpad[g] * 2, 64)))
             return fail(CWTH_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled rejected a tensor map");
         L.ncols = ncols[g];
         L.k_pad = kpad[g];
         L.h_group = hg;
         L.n_scales = n;
         L.rows = d_rows + first;
-        const cwth::DirShape sh = cwth::direct_shape(ncols[g], split, hop, kpad[g]);
+        const cwth::DirShape sh = cwth::direct_shape(ncols[g], nparts, hop, kpad[g]);
         L.stages = sh.stages;
         L.win_rows = sh.win_rows;
         L.a_shift = sh.win_rows ? cwth::direct_window_shift(hop) : 0;
@@ -321,11 +331,11 @@ cwth_status cwth_execute_direct_noalloc(const cwth_morlet* w, const double* scal
         L.unit = sh.unit;
         L.win_sets = sh.win_sets;
         L.acc_sets = sh.acc_sets;
-        L.sched = d_sched + (size_t)g * 2 * (kMaxTaps / 64);
+        L.sched = d_sched + (size_t)g * 3 * (kMaxTaps / 64);
         L.nsteps = nsteps[g];
         L.tmem_cols = sh.tmem_cols;
         if (L.stages == 0) return fail(CWTH_ERR_UNSUPPORTED, "tile does not fit in shared memory");
-        e = cwth::direct_launch_mma(maps, L, split, strm);
+        e = cwth::direct_launch_mma(maps, L, nparts, strm);
         if (e != cudaSuccess) return fail_cuda(e);
     }
     return CWTH_OK;

@@ -374,40 +374,52 @@ __device__ __forceinline__ void fft_one(float2* buf, int L, const TwTab& tw, int
     }
 }
 
-// nbatch transforms of L points with a run-time pass loop (compact: one
-// pass body per radix, each holding CAP / R butterflies per thread).
+// One pass of fft_many: radix R at sub-transform length Ns, pass index i of
+// np; with PRUNE the passes before i0 are skipped and pass i0 reads their
+// result in place (fft_pass's BC).
+template <int R, int CAP, bool INV, bool PRUNE>
+__device__ __forceinline__ void fft_many_pass(float2* buf, int L, int nbatch, int Ns,
+                                              const TwTab& tw, int ts, int i, int np, int i0) {
+    if (PRUNE && i < i0) return;
+    if (PRUNE && i > 0 && i == i0)
+        fft_pass<R, CAP / R, INV, true>(buf, L, nbatch, Ns, tw, ts * (L / (Ns * R)), false,
+                                        i + 1 < np);
+    else
+        fft_pass<R, CAP / R, INV, false>(buf, L, nbatch, Ns, tw, ts * (L / (Ns * R)), i > 0,
+                                         i + 1 < np);
+}
+
+// nbatch transforms of L points (the plan's radices, as fft_radix): the
+// leading radix-8 / radix-4 passes in line, then a loop whose body is the
+// plan's main radix alone (a loop over every radix holds too many registers
+// for the 64-register bound of the paired shape).
 template <bool INV, int PLAN, int CAP, bool PRUNE = false>
 __device__ __forceinline__ void fft_many(float2* buf, int L, int nbatch, const TwTab& tw, int ts,
                                          int wmax = 0) {
-    const int lg = __ffs(L) - 1;
-    const int np = ct_npass(PLAN, lg);
-    int i = PRUNE ? fft_skip<PLAN>(lg, wmax) : 0;
-    int Ns = 1;
-    for (int k = 0; k < i; ++k) Ns *= ct_radix(PLAN, lg, k);
-    const bool bc = PRUNE && i > 0;
-    for (; i < np; ++i) {
-        const int R = ct_radix(PLAN, lg, i);
-        const bool rs = i > 0, ws = i + 1 < np;
-        const bool first_bc = bc && Ns > 1 && i == fft_skip<PLAN>(lg, wmax);
-        if (R == 4) {
-            if (first_bc)
-                fft_pass<4, CAP / 4, INV, true>(buf, L, nbatch, Ns, tw, ts * (L / (Ns * 4)), false, ws);
-            else
-                fft_pass<4, CAP / 4, INV, false>(buf, L, nbatch, Ns, tw, ts * (L / (Ns * 4)), rs, ws);
-        } else if (R == 8) {
-            if (first_bc)
-                fft_pass<8, CAP / 8, INV, true>(buf, L, nbatch, Ns, tw, ts * (L / (Ns * 8)), false, ws);
-            else
-                fft_pass<8, CAP / 8, INV, false>(buf, L, nbatch, Ns, tw, ts * (L / (Ns * 8)), rs, ws);
-        } else if constexpr (PLAN >= 16) {
-            if (first_bc)
-                fft_pass<16, CAP / 16, INV, true>(buf, L, nbatch, Ns, tw, ts * (L / (Ns * 16)), false,
-                                                  ws);
-            else
-                fft_pass<16, CAP / 16, INV, false>(buf, L, nbatch, Ns, tw, ts * (L / (Ns * 16)), rs,
-                                                   ws);
+    const int e = __ffs(L) - 1;
+    const int np = ct_npass(PLAN, e);
+    const int i0 = PRUNE ? fft_skip<PLAN>(e, wmax) : 0;
+    int i = 0, Ns = 1;
+    if constexpr (PLAN >= 16) {
+        const int m = e & 3;
+        if (m == 3 || m == 1) {
+            fft_many_pass<8, CAP, INV, PRUNE>(buf, L, nbatch, Ns, tw, ts, i, np, i0);
+            Ns *= 8;
+            ++i;
         }
-        Ns *= R;
+        if (m == 2 || m == 1) {
+            fft_many_pass<4, CAP, INV, PRUNE>(buf, L, nbatch, Ns, tw, ts, i, np, i0);
+            Ns *= 4;
+            ++i;
+        }
+        for (; i < np; ++i, Ns *= 16)
+            fft_many_pass<16, CAP, INV, PRUNE>(buf, L, nbatch, Ns, tw, ts, i, np, i0);
+    } else {
+        const int n4 = (e % 3 == 1) ? 2 : (e % 3 == 2) ? 1 : 0;
+        for (; i < n4; ++i, Ns *= 4)
+            fft_many_pass<4, CAP, INV, PRUNE>(buf, L, nbatch, Ns, tw, ts, i, np, i0);
+        for (; i < np; ++i, Ns *= 8)
+            fft_many_pass<8, CAP, INV, PRUNE>(buf, L, nbatch, Ns, tw, ts, i, np, i0);
     }
 }
 

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libcwth.so")
 CWTH_OK = 0
 STATUS = {0: "CWTH_OK", 1: "CWTH_ERR_INVALID_ARG", 2: "CWTH_ERR_OOM", 3: "CWTH_ERR_CUDA",
           4: "CWTH_ERR_UNSUPPORTED", 5: "CWTH_ERR_TIMEOUT", 6: "CWTH_ERR_BAD_PLAN"}
-PREC = {"fp32": 0, "bf16": 1, "bf16x2": 2}
+PREC = {"fp32": 0, "bf16": 1, "bf16x2": 2, "bf16x3": 3}
 PATH = {"auto": 0, "spectral": 1, "direct": 2}
 
 # Every symbol include/cwth.h declares.

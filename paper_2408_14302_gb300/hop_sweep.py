@@ -75,7 +75,7 @@ def main(argv=None):
     for hop in (int(h) for h in a.hops.split(",")):
         forms = [("spectral", "fp32")]
         if hop % 8 == 0:
-            forms.append(("auto", "bf16x2"))
+            forms.append(("auto", "bf16x3"))
         for path, precision in forms:
             try:
                 plan = cwth.Plan(sc, hop=hop, max_len=n, sample_rate=a.fs, precision=precision,

@@ -104,7 +104,7 @@ class GpuExecutor:
     """Runs batches through libcwth.so.  form: "batched" uses the automatic
     path at `precision`; "per_clip" is the plain float32 spectral path."""
 
-    def __init__(self, slots: int = 4, precision: str = "bf16x2", path: str = "auto",
+    def __init__(self, slots: int = 4, precision: str = "bf16x3", path: str = "auto",
                  f_lo: float = 50.0, f_hi: float = 8000.0, device: str = "cuda"):
         import torch
         from . import cwth
@@ -329,13 +329,13 @@ def main(argv=None):
     ap.add_argument("--budget-gb", type=float, default=40.0)
     ap.add_argument("--max-batch", type=int, default=16)
     ap.add_argument("--slots", type=int, default=4)
-    ap.add_argument("--forms", default="batched_spectral_fp32,batched_auto_bf16x2,"
+    ap.add_argument("--forms", default="batched_spectral_fp32,batched_auto_bf16x3,"
                     "per_clip_fp32_spectral")
     a = ap.parse_args(argv)
     import torch
     pool = [signals.machine_clip(5000 + i, 60 * 16000, 16000.0) for i in range(8)]
     forms = {"batched_spectral_fp32": dict(precision="fp32", path="spectral", batched=True),
-             "batched_auto_bf16x2": dict(precision="bf16x2", path="auto", batched=True),
+             "batched_auto_bf16x3": dict(precision="bf16x3", path="auto", batched=True),
              "per_clip_fp32_spectral": dict(precision="fp32", path="spectral", batched=False)}
     forms = {k: forms[k] for k in a.forms.split(",")}
     for name, f in forms.items():

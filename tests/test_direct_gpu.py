@@ -1,7 +1,9 @@
 """GPU parity of the direct (time-domain GEMM) path against the float64 oracle.
 
 Tolerances, max |err| / max|W| per clip: bf16 operands 2e-2, split hi+lo bf16
-1e-5, float32 (SIMT) 1e-5.  Workload: the tones generator, 1 s at 16 kHz,
+1e-5 (where the tap products do not cancel: its bound is about 2^-17 of
+the sum of |x g|), split hi+mid+lo bf16 1e-5 on every input, float32 (SIMT)
+1e-5.  Workload: the tones generator, 1 s at 16 kHz,
 128 scales 100-8000 Hz, hops 64/128/256/512 (the precision study), plus
 ragged batches and small hops that exercise overlapping frame views.
 """
@@ -13,7 +15,7 @@ import pytest
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {"bf16": 2e-2, "bf16x2": 1e-5, "fp32": 1e-5}
+TOL = {"bf16": 2e-2, "bf16x2": 1e-5, "bf16x3": 1e-5, "fp32": 1e-5}
 
 
 @pytest.fixture(scope="module")
@@ -45,7 +47,7 @@ def run(cw, xs, scales, hop, precision, path="direct", lengths=None, fill=np.nan
         return out.cpu().numpy().astype(np.float64), plan.info(), plan.scale_paths()
 
 
-@pytest.mark.parametrize("precision", ["bf16", "bf16x2", "fp32"])
+@pytest.mark.parametrize("precision", ["bf16", "bf16x2", "bf16x3", "fp32"])
 @pytest.mark.parametrize("hop", [64, 128, 256, 512])
 def test_precision_study_128_scales(cw, sig, hop, precision):
     x = sig.tones_clip(seed=0, n=16000).astype(np.float32)
@@ -57,7 +59,7 @@ def test_precision_study_128_scales(cw, sig, hop, precision):
     assert err <= TOL[precision], (hop, precision, err)
 
 
-@pytest.mark.parametrize("precision", ["bf16", "bf16x2"])
+@pytest.mark.parametrize("precision", ["bf16", "bf16x2", "bf16x3"])
 @pytest.mark.parametrize("hop", [8, 16, 40])
 def test_small_hops_overlapping_frames(cw, sig, hop, precision):
     x = sig.machine_clip(seed=3, n=6001)
@@ -67,7 +69,7 @@ def test_small_hops_overlapping_frames(cw, sig, hop, precision):
     assert np.max(np.abs(got[0] - ref)) / ref.max() <= TOL[precision]
 
 
-@pytest.mark.parametrize("precision", ["bf16x2", "fp32"])
+@pytest.mark.parametrize("precision", ["bf16x2", "bf16x3", "fp32"])
 def test_ragged_batch_and_untouched_tail(cw, sig, precision):
     hop, n = 64, 12000
     lengths = [12000, 11999, 1, 0, 500, 64, 65, 7000, 3333]
@@ -103,6 +105,68 @@ def test_direct_large_batch_sampled(cw, sig):
     assert np.isfinite(got).all()
     for i in (0, 255, 511):
         ref = oracle_mag(xs[i], sc, hop)
+        assert np.max(np.abs(got[i] - ref)) / ref.max() <= 1e-5
+
+
+def tap_mass(x, scales, hop):
+    """Largest sum of |x[kH + t] g_s[t]| over the frames and scales (float64,
+    the same taps as the oracle): the quantity a split's per-product error
+    is relative to."""
+    x = np.abs(np.asarray(x, np.float64))
+    best = 0.0
+    for a in scales:
+        h = int(np.ceil(a * np.sqrt(1.5 * np.log(1e16))))
+        t = np.arange(-h, h + 1) / a
+        g = np.exp(-t * t / 1.5) / np.sqrt(a * np.pi * 1.5)
+        m = np.convolve(x, g, mode="full")[h:h + len(x)]
+        best = max(best, float(m[::hop].max()))
+    return best
+
+
+def test_cancelling_short_clip_split_precisions(cw):
+    """A short white-noise clip with long wavelets: each scalogram value is a
+    sum of up to ~3600 tap products of random sign, so the tap-product mass
+    is several times max|W|.
+
+    * The automatic three-part split plan (tensor cores for supports up to
+      1024 padded taps, float32 spectral beyond) holds 1e-5 of max|W|.
+    * Forced onto the tensor cores, the three-part split holds 1e-5 on
+      every row up to 1024 taps; longer rows carry the float32
+      accumulation's bias (about 1e-5 relative at 2300 taps), bounded
+      here by 3e-5.
+    * The two-part split holds its own bound, 2^-16 of the tap-product
+      mass."""
+    rng = np.random.default_rng(12)
+    x = rng.standard_normal(8000).astype(np.float32)
+    sc = np.geomspace(2.0, 320.0, 24)
+    ref = oracle_mag(x, sc, 64)
+    mass = tap_mass(x, sc, 64)
+    assert mass > 5 * ref.max()   # 2^-17 of the mass is then above 1e-5 of max|W|
+    got, info, paths = run(cw, x, sc, 64, "bf16x3", path="auto")
+    assert info["num_direct"] > 0 and info["num_spectral"] > 0, info
+    assert np.max(np.abs(got[0] - ref)) / ref.max() <= 1e-5
+    got3, info3, _ = run(cw, x, sc, 64, "bf16x3")
+    short = np.array([2 * int(np.ceil(a * np.sqrt(1.5 * np.log(1e9)))) + 1 <= 1024 for a in sc])
+    err3 = np.max(np.abs(got3[0] - ref), axis=1) / ref.max()
+    assert np.all(err3[short] <= 1e-5) and np.all(err3 <= 3e-5), err3
+    got2, _, _ = run(cw, x, sc, 64, "bf16x2")
+    assert np.max(np.abs(got2[0] - ref)) <= 2.0 ** -16 * mass
+
+
+def test_bf16x3_auto_and_large_batch(cw, sig):
+    """The three-part split through the automatic path (scales beyond 4096
+    taps go spectral) and on the 512-clip throughput batch, rows sampled."""
+    x = sig.machine_clip(seed=4, n=40000)
+    sc = np.array([2.0, 5.0, 30.0, 200.0, 500.0, 1200.0])
+    got, info, paths = run(cw, x, sc, 64, "bf16x3", path="auto")
+    assert info["num_direct"] >= 3 and info["num_spectral"] >= 1
+    ref = oracle_mag(x, sc, 64)
+    assert np.max(np.abs(got[0] - ref)) / ref.max() <= 1e-5
+    xs = np.stack([sig.tones_clip(seed=s, n=16000) for s in range(512)]).astype(np.float32)
+    sc = sig.scales_for_band(100, 8000, 128, 16000.0)
+    got, _, _ = run(cw, xs, sc, 64, "bf16x3")
+    for i in (0, 511):
+        ref = oracle_mag(xs[i], sc, 64)
         assert np.max(np.abs(got[i] - ref)) / ref.max() <= 1e-5
 
 

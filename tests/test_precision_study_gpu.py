@@ -14,8 +14,8 @@ import pytest
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-VARIANTS = [("direct", "bf16", 2e-2), ("direct", "bf16x2", 1e-5), ("direct", "fp32", 1e-5),
-            ("spectral", "fp32", 1e-5)]
+VARIANTS = [("direct", "bf16", 2e-2), ("direct", "bf16x2", 1e-5), ("direct", "bf16x3", 1e-5),
+            ("direct", "fp32", 1e-5), ("spectral", "fp32", 1e-5)]
 
 
 def test_precision_study():

@@ -1,9 +1,8 @@
 """The continuous-batching server on the GPU: every request's scalogram is
 the same in the mix as alone (within 1e-5 of max|W|) and matches the float64
-oracle.  The float32 form is held to 1e-5 of max|W|; split bf16 to 1e-5 of
-max(max|W|, M), M the largest tap-product mass sum_t |x[kH+t] g[t]| over the
-clip's frames, because its error is bounded by about 2^-17 of that mass (the
-two bounds coincide unless a short clip makes the sum cancel heavily)."""
+oracle within 1e-5 of max|W|, for the float32 form and the three-part split
+bf16 form (whose per-product error, about 2^-24, holds on clips whose tap
+products cancel)."""
 from __future__ import annotations
 
 import numpy as np
@@ -13,20 +12,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-def tap_mass(x, scales, hop, bandwidth=1.5):
-    """max over scales and frames of sum_t |x[kH + t]| |g_s[t]| (float64)."""
-    x = np.abs(np.asarray(x, np.float64))
-    best = 0.0
-    for a in scales:
-        h = int(np.ceil(a * np.sqrt(bandwidth * np.log(1e16))))
-        t = np.arange(-h, h + 1)
-        g = np.exp(-(t / a) ** 2 / bandwidth) / np.sqrt(a * np.pi * bandwidth)
-        m = np.convolve(x, g, mode="full")[h: h + len(x)]   # centred at each sample
-        best = max(best, float(m[::hop].max()))
-    return best
-
-
-@pytest.mark.parametrize("precision,path", [("bf16x2", "auto"), ("fp32", "spectral")])
+@pytest.mark.parametrize("precision,path", [("bf16x3", "auto"), ("fp32", "spectral")])
 def test_mix_equals_alone_and_oracle(precision, path):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -49,7 +35,4 @@ def test_mix_equals_alone_and_oracle(precision, path):
         assert got.shape == alone.shape
         assert np.max(np.abs(got - alone)) <= 1e-5 * np.max(alone), q.rid
         ref = oracle.cwth_magnitude(q.x.astype(np.float64), sc, q.hop)
-        norm = np.max(ref)
-        if precision == "bf16x2":
-            norm = max(norm, tap_mass(q.x, sc, q.hop))
-        assert np.max(np.abs(got - ref)) <= 1e-5 * norm, q.rid
+        assert np.max(np.abs(got - ref)) <= 1e-5 * np.max(ref), q.rid

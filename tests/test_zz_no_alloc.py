@@ -27,7 +27,7 @@ import pytest
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {"bf16": 2e-2, "bf16x2": 1e-5}
+TOL = {"bf16": 2e-2, "bf16x2": 1e-5, "bf16x3": 1e-5}
 
 
 @pytest.fixture(scope="module")
@@ -72,6 +72,7 @@ def test_noalloc_matches_planned_direct_path_and_oracle(cw):
         (3, 16000, signals.scales_for_band(100, 8000, 40, 16000.0), 64, "bf16x2", None),
         (5, 9000, signals.scales_for_band(150, 6000, 24, 16000.0), 128, "bf16",
          [9000, 8999, 1, 0, 4097]),
+        (2, 10000, signals.scales_for_band(100, 8000, 32, 16000.0), 256, "bf16x3", [10000, 5003]),
         # 200 scales: two GEMM groups (128 + 72), each with its own bank
         # slot, schedule slot and tensor maps inside the scratch array
         (2, 12000, signals.scales_for_band(100, 8000, 200, 16000.0), 64, "bf16x2", [12000, 7001]),
