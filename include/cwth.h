@@ -281,6 +281,55 @@ cwth_status cwth_measure_fp32_fma(double *tflops, void *stream);
 cwth_status cwth_plan_scale_paths(cwth_plan_t plan, int32_t *paths);
 
 /*
+ * Uneven batches in one launch (paper Sec. II.B applied to clips of mixed
+ * lengths, sample rates, scale counts and hops: one plan per group of
+ * clips that share rate, scales and hop).
+ *
+ * cwth_batch_create binds n groups, each a plan with its device batch,
+ * exactly as cwth_execute takes them:
+ *   plans[i]      a plan whose every scale takes the float32 spectral path
+ *                 (with the short-support scales it sums in the time domain:
+ *                 CWTH_PREC_FP32 with CWTH_PATH_AUTO or CWTH_PATH_SPECTRAL),
+ *                 without pruned inverse FFTs (cwth_plan_query reports
+ *                 spectral_pruned = 0; pruning is taken at hops 1 and 2)
+ *                 and not re-sampled;
+ *   d_x[i], ld_x[i], d_lengths[i] (may be NULL), batch[i], d_out[i]
+ *                 as cwth_execute's arguments for that plan (device memory);
+ *   h_lengths     NULL, or n host pointers (each NULL or batch[i] lengths,
+ *                 the same as d_lengths[i]): only the segments a clip needs
+ *                 become work items.
+ * It builds a device work list of (group, clip, segment) items, ordered by
+ * the plans' cost models, largest first, and allocates it (the only
+ * allocation; cwth_batch_destroy frees it).  cwth_batch_execute then runs
+ * every group with ONE kernel launch on `stream` (one block per item, the
+ * hardware's block scheduler dealing them to the SMs as they free up); it
+ * allocates nothing and can be repeated, also from a captured CUDA graph.
+ * The result is the same as cwth_execute of each group within the float32
+ * tolerance (the groups' plans fold their scales in one pass).  The bound
+ * buffers and plans must outlive the batch; a batch may be executed on one
+ * stream at a time.
+ *
+ * Errors: CWTH_ERR_INVALID_ARG (NULL arrays, n outside 1..96, a batch
+ * outside 0..65535, ld_x below the plan's max_len, plans on different
+ * devices), CWTH_ERR_BAD_PLAN, CWTH_ERR_UNSUPPORTED (a plan with
+ * tensor-core or SIMT direct scales, pruned inverse FFTs, re-sampling, or
+ * the one-CTA-per-SM shape), CWTH_ERR_OOM / CWTH_ERR_CUDA.
+ */
+typedef struct cwth_batch_s *cwth_batch_t;
+cwth_status cwth_batch_create(int32_t n, const cwth_plan_t *plans, const float *const *d_x,
+                              const int64_t *ld_x, const int64_t *const *d_lengths,
+                              const int64_t *const *h_lengths, const int32_t *batch,
+                              float *const *d_out, cwth_batch_t *out);
+/* One launch over the batch's work list, asynchronous on `stream`.
+ * Errors: CWTH_ERR_BAD_PLAN (not a live batch), CWTH_ERR_CUDA. */
+cwth_status cwth_batch_execute(cwth_batch_t batch, void *stream);
+/* Work items of the batch (blocks per launch), or -1 for a bad handle. */
+int64_t cwth_batch_items(cwth_batch_t batch);
+/* Release the batch's work list; NULL is accepted.  Not while a launch of
+ * it may still be running. */
+cwth_status cwth_batch_destroy(cwth_batch_t batch);
+
+/*
  * Allocation-free direct-path scalograms.
  *
  * For callers that cannot allocate device memory while they run: code whose

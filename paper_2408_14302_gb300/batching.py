@@ -1,16 +1,23 @@
 """Uneven-length batches: many clips with different lengths, sample rates,
-scale counts and hops in one CUDA-graph launch.
+scale counts and hops in one launch.
 
 Clips are grouped by (sample rate, scale count, hop); each group is one plan
-whose clips are packed into one padded device batch with a lengths vector,
-so a group runs as one `cwth_execute` (every kernel already honours per-clip
-lengths).  All groups' executes are captured into one CUDA graph, so a whole
-batch is a single host-side launch.  An autotuner times the candidate
-evaluations of each group once (the float32 spectral path at the plan's own
-FFT segment length and at half and twice it, and the automatic path at
-split-bf16 precision, all within 1e-5 of max|W|) and remembers the fastest
-in a JSON cache keyed by GPU, sample rate, scale count, hop and length
-bucket.
+whose clips are packed into one padded device batch with a lengths vector.
+Two modes:
+
+* "worklist" (the default for the float32 accuracy class): every group's
+  plan is a float32 plan of the spectral kernel (with its short-support
+  scales summed in the time domain), and all groups are bound into one
+  cwth_batch: a device work list of (group, clip, segment) items, longest
+  first, run by ONE kernel launch (one block per item).  The autotuner picks
+  each group's FFT segment length (the cost model's, half or twice it).
+* "graph": each group runs as its own `cwth_execute` (any path and
+  precision, e.g. the tensor-core split-bf16 path) and all groups' executes
+  are captured in one CUDA graph.  Its autotuner also tries the automatic
+  path at three-part split-bf16 precision (within 1e-5 of max|W|).
+
+Choices persist in a JSON cache keyed by GPU, sample rate, scale count,
+hop, length bucket, accuracy class and mode.
 
 Python orchestration only: the transform runs in libcwth.so.
 """
@@ -30,6 +37,8 @@ CANDIDATES = {
     "fp32": [("spectral", "fp32"), ("auto", "bf16x3")],
     "bf16": [("auto", "bf16"), ("spectral", "fp32")],
 }
+# Candidates of the work-list mode: float32 plans of the spectral kernel.
+WORKLIST_CANDIDATES = [("auto", "fp32")]
 
 
 def default_cache_path() -> str:
@@ -86,13 +95,17 @@ class BatchRunner:
 
     def __init__(self, clips, fs, n_scales, hops, f_lo: float = 50.0, f_hi: float = 8000.0,
                  bandwidth: float = 1.5, center: float = 1.0, accuracy: str = "fp32",
-                 tune: bool = True, cache: TuneCache | None = None, device: str = "cuda"):
+                 tune: bool = True, cache: TuneCache | None = None, device: str = "cuda",
+                 mode: str | None = None):
         import torch
         self.torch = torch
         self.device = torch.device(device)
         self.n = len(clips)
         self.bandwidth, self.center = bandwidth, center
         self.accuracy = accuracy
+        self.mode = mode or ("worklist" if accuracy == "fp32" else "graph")
+        if self.mode not in ("worklist", "graph"):
+            raise ValueError("mode must be 'worklist' or 'graph'")
         self.cache = cache if cache is not None else (TuneCache() if tune else None)
         self.groups = []
         by_key = {}
@@ -118,6 +131,10 @@ class BatchRunner:
             self.groups.append(g)
         self.graph = None
         self.stream = torch.cuda.Stream(self.device)
+        self.batch = None
+        if self.mode == "worklist":
+            self.batch = cwth.Batch([(g["plan"], g["x"], g["len_d"], g["out"], g["lens"])
+                                     for g in self.groups])
 
     # ------------------------------------------------------------ planning
     def _plan(self, g, path, precision, seg_len=0):
@@ -131,13 +148,15 @@ class BatchRunner:
         candidate; the spectral path also tries half and twice the segment
         length its cost model picks."""
         gfs, S, hop = g["key"]
-        key = f"{gpu}|{gfs:g}|{S}|{hop}|{length_bucket(g['max_len'])}|{self.accuracy}"
+        key = (f"{gpu}|{gfs:g}|{S}|{hop}|{length_bucket(g['max_len'])}|{self.accuracy}"
+               f"|{self.mode}")
         if self.cache is not None:
             hit = self.cache.get(key)
             if hit:
                 return hit["path"], hit["precision"], int(hit.get("seg_len", 0))
         best = None
-        for path, prec in CANDIDATES[self.accuracy]:
+        cands = WORKLIST_CANDIDATES if self.mode == "worklist" else CANDIDATES[self.accuracy]
+        for path, prec in cands:
             segs = [0]
             while segs:
                 seg = segs.pop(0)
@@ -146,7 +165,11 @@ class BatchRunner:
                 except cwth.CwthError:
                     continue
                 info = plan.info()
-                if seg == 0 and path == "spectral" and info["seg_len"] > 0:
+                if self.mode == "worklist" and info["spectral_pruned"]:
+                    plan.close()
+                    continue
+                if seg == 0 and path in ("spectral", "auto") and prec == "fp32" and \
+                        info["seg_len"] > 0:
                     segs = [m for m in (info["seg_len"] // 2, info["seg_len"] * 2)
                             if 512 <= m <= 32768]
                 ms = self._time(plan, g)
@@ -176,7 +199,11 @@ class BatchRunner:
 
     # ------------------------------------------------------------ running
     def run(self):
-        """All groups, eagerly, on the current stream."""
+        """All groups, eagerly, on the current stream: one kernel launch in
+        the work-list mode, one execute per group in the graph mode."""
+        if self.batch is not None:
+            self.batch.execute()
+            return
         for g in self.groups:
             g["plan"].execute(g["x"], lengths=g["len_d"], out=g["out"])
 
@@ -213,6 +240,9 @@ class BatchRunner:
         return float(sum(int(g["lens"].sum()) / g["key"][0] for g in self.groups))
 
     def close(self):
+        if self.batch is not None:
+            self.batch.close()
+            self.batch = None
         for g in self.groups:
             g["plan"].close()
 
@@ -245,12 +275,14 @@ def main(argv=None):
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--accuracy", default="fp32", choices=["fp32", "bf16"])
     ap.add_argument("--cache", default=None)
+    ap.add_argument("--mode", default=None, choices=["worklist", "graph"])
     a = ap.parse_args(argv)
     import torch
     t0 = time.time()
     clips, fs, ns, hs = uneven_workload(a.clips)
     t1 = time.time()
-    runner = BatchRunner(clips, fs, ns, hs, accuracy=a.accuracy, cache=TuneCache(a.cache))
+    runner = BatchRunner(clips, fs, ns, hs, accuracy=a.accuracy, cache=TuneCache(a.cache),
+                         mode=a.mode)
     t2 = time.time()
     runner.capture()
     runner.replay()
@@ -266,7 +298,9 @@ def main(argv=None):
     ms = e0.elapsed_time(e1) / a.reps
     audio = runner.audio_seconds()
     print(json.dumps({"workload": f"uneven_{a.clips}clips_1-30s_16k48k_S64-128_H128-512",
-                      "groups": len(runner.groups), "audio_seconds": audio,
+                      "mode": runner.mode, "groups": len(runner.groups),
+                      "work_items": runner.batch.items if runner.batch is not None else None,
+                      "audio_seconds": audio,
                       "ms_per_graph_launch": ms, "audio_sec_per_s": audio / (ms * 1e-3),
                       "choices": {str(g["key"]): g["choice"] for g in runner.groups},
                       "generate_s": t1 - t0, "plan_tune_s": t2 - t1}))

@@ -624,6 +624,7 @@ cwth_status build_spectral(cwth_plan_s* p) {
     p->kp0 = ch.kp0;
     p->seg_frames = ch.seg_frames;
     p->n_seg = ch.n_seg;
+    p->seg_cost = ch.n_seg > 0 ? ch.cost / ch.n_seg : 0.0;
 
     std::vector<SpecScale> host(sp.size());
     for (size_t i = 0; i < sp.size(); ++i) {
@@ -736,16 +737,16 @@ cwth_status build_spectral(cwth_plan_s* p) {
     return cuda_status(e);
 }
 
-cwth_status launch_spectral(cwth_plan_s* p, const float* d_x, int64_t ld_x,
-                            const int64_t* d_len, int32_t batch, float* d_out, cudaStream_t st,
-                            bool fill_gpu) {
-    if ((p->n_sp == 0 && p->n_fd == 0) || batch == 0) return CWTH_OK;
-    // Scale groups: enough CTAs for two waves, each group at least 8 scales
-    // (every group repeats its segment's forward FFT).  A launch that shares
-    // the GPU with other chunks of the same batch keeps one group.  The
-    // fused time-domain tap groups are dealt round-robin over the scale
-    // groups.
-    const int64_t base = (int64_t)p->n_seg * batch;
+// The spectral kernel's launch record of a plan for one batch: scale
+// groups (enough CTAs for two waves, each group at least 8 scales, since
+// every group repeats its segment's forward FFT; one group when fill_gpu is
+// false, i.e. when the launch shares the GPU with other work of the same
+// batch), the fused tap groups dealt round-robin over them, the CTA shape
+// and the dynamic shared memory.
+void spectral_record(const cwth_plan_s* p, const float* d_x, int64_t ld_x, const int64_t* d_len,
+                     int32_t batch, float* d_out, bool fill_gpu, SpecLaunch* out, int* threads_out,
+                     int* n_groups_out, size_t* smem_out) {
+    const int64_t base = std::max<int64_t>(1, (int64_t)p->n_seg * batch);
     const int64_t want = (2 * (int64_t)num_sms(p->device) + base - 1) / base;
     const int fdg = (int)p->fd_groups.size();
     int n_groups = 1, gs = 0;
@@ -753,16 +754,21 @@ cwth_status launch_spectral(cwth_plan_s* p, const float* d_x, int64_t ld_x,
         n_groups = !fill_gpu ? 1 : (int)std::min<int64_t>(want, std::max(1, p->n_sp / 8));
         n_groups = std::max(1, n_groups);
         gs = (p->n_sp + n_groups - 1) / n_groups;
+        // Groups and passes of an even number of scales: the fold walks
+        // table pairs (2j, 2j + 1), so every launch shape pairs the same
+        // scales and gives the same bytes.
+        gs += gs & 1;
         n_groups = (p->n_sp + gs - 1) / gs;
     } else {
         n_groups = !fill_gpu ? 1 : (int)std::max<int64_t>(1, std::min<int64_t>(want, fdg));
     }
     const size_t fdb = fd_bytes(p);
     const int threads = spectral_threads(p->M, p->P, fdb);
-    const int nconc = spectral_nconc(p->M, p->P, std::max(1, gs), threads, fdb);
-    if (batch > 65535 || p->n_seg > 0x7fffffff) return CWTH_ERR_UNSUPPORTED;
+    int nconc = spectral_nconc(p->M, p->P, std::max(1, gs), threads, fdb);
+    if (nconc > 1) nconc &= ~1;
 
     SpecLaunch L;
+    memset(&L, 0, sizeof(L));
     L.x = d_x;
     L.ld_x = ld_x;
     L.lengths = d_len;
@@ -794,7 +800,21 @@ cwth_status launch_spectral(cwth_plan_s* p, const float* d_x, int64_t ld_x,
     L.fd_taps = p->d_fd_taps;
     L.fd_grp = p->d_fd_grp;
     L.inv_r8 = p->inv_r8 ? 1 : 0;
-    const size_t smem = cwth::spectral_smem_bytes(p->M, p->P, nconc, fdb);
+    *out = L;
+    *threads_out = threads;
+    *n_groups_out = n_groups;
+    *smem_out = cwth::spectral_smem_bytes(p->M, p->P, nconc, fdb);
+}
+
+cwth_status launch_spectral(cwth_plan_s* p, const float* d_x, int64_t ld_x,
+                            const int64_t* d_len, int32_t batch, float* d_out, cudaStream_t st,
+                            bool fill_gpu) {
+    if ((p->n_sp == 0 && p->n_fd == 0) || batch == 0) return CWTH_OK;
+    if (batch > 65535 || p->n_seg > 0x7fffffff) return CWTH_ERR_UNSUPPORTED;
+    SpecLaunch L;
+    int threads = 0, n_groups = 1;
+    size_t smem = 0;
+    spectral_record(p, d_x, ld_x, d_len, batch, d_out, fill_gpu, &L, &threads, &n_groups, &smem);
     return cuda_status(
         cwth::spectral_launch(L, threads, p->spec_prune, p->n_seg, batch, n_groups, smem, st));
 }
@@ -1263,8 +1283,11 @@ cwth_status cwth_plan_query(cwth_plan_t p, cwth_plan_info* info) {
     info->resample = p->resample;
     if (p->n_sp > 0 || p->n_fd > 0) {
         info->spectral_threads = spectral_threads(p->M, p->P, fd_bytes(p));
-        info->spectral_pass_scales =
-            p->n_sp > 0 ? spectral_nconc(p->M, p->P, p->n_sp, info->spectral_threads, fd_bytes(p)) : 0;
+        int nc = p->n_sp > 0 ? spectral_nconc(p->M, p->P, p->n_sp, info->spectral_threads,
+                                              fd_bytes(p))
+                             : 0;
+        if (nc > 1) nc &= ~1;  // passes hold whole fold pairs (see spectral_record)
+        info->spectral_pass_scales = nc;
         info->spectral_pruned = p->spec_prune ? 1 : 0;
     }
     return CWTH_OK;
@@ -1315,6 +1338,134 @@ cwth_status cwth_plan_scale_paths(cwth_plan_t p, int32_t* paths) {
     if (!paths) return CWTH_ERR_INVALID_ARG;
     for (int s = 0; s < p->S; ++s)
         paths[s] = p->scale_path[s] == kPathFused ? CWTH_PATH_DIRECT : p->scale_path[s];
+    return CWTH_OK;
+}
+
+cwth_status cwth_batch_create(int32_t n, const cwth_plan_t* plans, const float* const* d_x,
+                              const int64_t* ld_x, const int64_t* const* d_lengths,
+                              const int64_t* const* h_lengths, const int32_t* batch,
+                              float* const* d_out, cwth_batch_t* out) {
+    if (out) *out = nullptr;
+    if (!out || !plans || !d_x || !ld_x || !batch || !d_out) return CWTH_ERR_INVALID_ARG;
+    if (n < 1 || n > cwth::kMaxBatchGroups) return CWTH_ERR_INVALID_ARG;
+    int dev = -1;
+    for (int32_t i = 0; i < n; ++i) {
+        const cwth_plan_s* p = plans[i];
+        if (!valid_plan(p)) return CWTH_ERR_BAD_PLAN;
+        if (batch[i] < 0 || batch[i] > 65535) return CWTH_ERR_INVALID_ARG;
+        if (batch[i] > 0 && (!d_x[i] || !d_out[i] || ld_x[i] < input_len(p)))
+            return CWTH_ERR_INVALID_ARG;
+        if (dev >= 0 && p->device != dev) return CWTH_ERR_INVALID_ARG;
+        dev = p->device;
+        // One launch of the paired spectral kernel serves plans whose every
+        // scale is spectral or fused, without pruned inverse FFTs or
+        // re-sampling.
+        if (p->n_dir > 0 || p->resample > 1 || p->spec_prune) {
+            note_error("batched plans must be float32 spectral/fused plans without pruning or "
+                       "re-sampling");
+            return CWTH_ERR_UNSUPPORTED;
+        }
+        if ((p->n_sp > 0 || p->n_fd > 0) &&
+            spectral_threads(p->M, p->P, fd_bytes(p)) != cwth::kSpecThreadsPair) {
+            note_error("a batched plan needs the one-CTA-per-SM shape");
+            return CWTH_ERR_UNSUPPORTED;
+        }
+    }
+    cwth_batch_s* b = new (std::nothrow) cwth_batch_s();
+    if (!b) return CWTH_ERR_OOM;
+    b->wl = new (std::nothrow) cwth::SpecWorkList();
+    if (!b->wl) {
+        delete b;
+        return CWTH_ERR_OOM;
+    }
+    b->device = dev;
+    memset(b->wl, 0, sizeof(cwth::SpecWorkList));
+    // Items of every group: each clip's segments up to its length, each
+    // segment's scale groups.  Ordered by the cost model's work per segment,
+    // largest first (stable within a group).
+    std::vector<std::pair<double, int4>> items;
+    try {
+        for (int32_t i = 0; i < n; ++i) {
+            cwth_plan_s* p = plans[i];
+            if (batch[i] == 0 || (p->n_sp == 0 && p->n_fd == 0)) continue;
+            SpecLaunch L;
+            int threads = 0, ngrp = 1;
+            size_t smem = 0;
+            spectral_record(p, d_x[i], ld_x[i], d_lengths ? d_lengths[i] : nullptr, batch[i],
+                            d_out[i], false, &L, &threads, &ngrp, &smem);
+            b->wl->g[i] = L;
+            b->smem = std::max(b->smem, smem);
+            for (int32_t c = 0; c < batch[i]; ++c) {
+                int64_t len = p->max_len;
+                if (h_lengths && h_lengths[i])
+                    len = std::min<int64_t>(std::max<int64_t>(h_lengths[i][c], 0), p->max_len);
+                const int64_t F = cwth_num_frames(len, p->hop);
+                const int64_t nseg = (F + p->seg_frames - 1) / p->seg_frames;
+                for (int64_t sgm = 0; sgm < nseg; ++sgm)
+                    for (int g = 0; g < ngrp; ++g)
+                        items.push_back({p->seg_cost / ngrp,
+                                         make_int4(i, (int)sgm, (int)c, g | (ngrp << 16))});
+            }
+        }
+    } catch (...) {
+        delete b->wl;
+        delete b;
+        return CWTH_ERR_OOM;
+    }
+    std::stable_sort(items.begin(), items.end(),
+                     [](const std::pair<double, int4>& x, const std::pair<double, int4>& y) {
+                         return x.first > y.first;
+                     });
+    if (items.size() > 0x7fffffff) {
+        delete b->wl;
+        delete b;
+        return CWTH_ERR_UNSUPPORTED;
+    }
+    b->n_items = (int64_t)items.size();
+    b->wl->n_items = (int32_t)items.size();
+    b->wl->n_groups = n;
+    DeviceGuard gd(dev);
+    cudaError_t e = gd.ok ? cudaSuccess : cudaErrorInvalidDevice;
+    if (e == cudaSuccess && !items.empty()) {
+        std::vector<int4> h(items.size());
+        for (size_t k = 0; k < items.size(); ++k) h[k] = items[k].second;
+        e = cudaMalloc(&b->d_items, sizeof(int4) * h.size());
+        if (e == cudaSuccess)
+            e = cudaMemcpy(b->d_items, h.data(), sizeof(int4) * h.size(), cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = cwth::spectral_prepare_device();
+    if (e != cudaSuccess) {
+        cudaFree(b->d_items);
+        delete b->wl;
+        delete b;
+        return cuda_status(e);
+    }
+    b->wl->items = b->d_items;
+    b->magic = cwth::kPlanMagic ^ 0x5A5A5A5Au;
+    *out = b;
+    return CWTH_OK;
+}
+
+cwth_status cwth_batch_execute(cwth_batch_t b, void* stream) {
+    if (!b || b->magic != (cwth::kPlanMagic ^ 0x5A5A5A5Au)) return CWTH_ERR_BAD_PLAN;
+    DeviceGuard g(b->device);
+    if (!g.ok) return CWTH_ERR_CUDA;
+    return cuda_status(cwth::spectral_worklist_launch(*b->wl, b->smem, (cudaStream_t)stream));
+}
+
+int64_t cwth_batch_items(cwth_batch_t b) {
+    if (!b || b->magic != (cwth::kPlanMagic ^ 0x5A5A5A5Au)) return -1;
+    return b->n_items;
+}
+
+cwth_status cwth_batch_destroy(cwth_batch_t b) {
+    if (!b) return CWTH_OK;
+    if (b->magic != (cwth::kPlanMagic ^ 0x5A5A5A5Au)) return CWTH_ERR_BAD_PLAN;
+    DeviceGuard g(b->device);
+    b->magic = 0;
+    cudaFree(b->d_items);
+    delete b->wl;
+    delete b;
     return CWTH_OK;
 }
 

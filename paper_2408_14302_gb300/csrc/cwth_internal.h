@@ -105,6 +105,16 @@ struct SpecLaunch {
     int32_t inv_r8;
 };
 
+// Plan records of a persistent batch launch, passed by value (the launch
+// parameters hold up to 32 KB).
+constexpr int kMaxBatchGroups = 96;
+struct SpecWorkList {
+    const int4* items;   // device, {group, segment, clip, scale group | groups << 16}
+    int32_t n_items;
+    int32_t n_groups;
+    SpecLaunch g[kMaxBatchGroups];
+};
+
 // Direct (GEMM) path launch parameters; one launch per scale group.
 constexpr int kMaxDirStages = 6;
 // Schedule steps of one group: at most 4096 taps = 64 tap blocks, each
@@ -164,6 +174,10 @@ cudaError_t spectral_prepare_device();
 cudaError_t spectral_make_twiddles(float2* d_tw, int M, cudaStream_t st);
 cudaError_t spectral_launch(const SpecLaunch& L, int threads, bool prune, int n_seg, int batch,
                             int n_groups, size_t smem, cudaStream_t st);
+// One launch of the paired shape over a work list: block i runs item i,
+// {group, segment, clip, scale group | scale groups << 16}, of the plan
+// records g[] (passed by value).
+cudaError_t spectral_worklist_launch(const SpecWorkList& wl, size_t smem, cudaStream_t st);
 
 // nparts: bf16 parts of each operand (1 = bf16, 2 = bf16x2, 3 = bf16x3).
 size_t direct_smem_bytes(int ncols, int stages, int nparts, int win_rows, int unit,
@@ -236,6 +250,7 @@ struct cwth_plan_s {
     int32_t M = 0, P = 0, halo = 0, kp0 = 0, seg_frames = 0, n_seg = 0;
     bool spec_prune = false;  // narrow bands let inverse FFTs skip passes
     bool inv_r8 = false;      // inverse FFTs on the radix-8 plan
+    double seg_cost = 0;      // cost model's lane operations per segment
     int32_t seg_force = 0;    // segment length fixed by cwth_plan_segment (0: cost model)
     float2* d_tw = nullptr;
     cwth::SpecScale* d_sp = nullptr;
@@ -290,3 +305,15 @@ struct cwth_plan_s {
     cudaStream_t h2d = nullptr, d2h = nullptr, cs2 = nullptr;
     cudaEvent_t ev_start = nullptr, ev_in = nullptr, ev_comp = nullptr, ev_out = nullptr;
 };
+
+// A bound uneven batch (cwth_batch_create): the plan records of its groups
+// and a device work list, run as one launch of the spectral kernel.
+struct cwth_batch_s {
+    uint32_t magic = 0;
+    int device = 0;
+    int64_t n_items = 0;
+    size_t smem = 0;
+    int4* d_items = nullptr;
+    cwth::SpecWorkList* wl = nullptr;  // host copy, passed by value at launch
+};
+

@@ -796,11 +796,11 @@ __device__ __forceinline__ void fold_items(const SpecLaunch& p, const float2* __
 // Clip length (clamped to [0, max_len]), frame count and first frame of the
 // CTA's segment.  reload: read the length again with a load the compiler
 // may not merge with an earlier one.
-__device__ __forceinline__ void cta_pos(const SpecLaunch& p, bool reload, int64_t* len, int64_t* F,
-                                        int64_t* k0) {
+__device__ __forceinline__ void cta_pos(const SpecLaunch& p, bool reload, int seg, int clip,
+                                        int64_t* len, int64_t* F, int64_t* k0) {
     int64_t n = p.max_len;
     if (p.lengths) {
-        const int64_t* a = p.lengths + blockIdx.y;
+        const int64_t* a = p.lengths + clip;
         if (reload)
             asm volatile("ld.global.nc.s64 %0, [%1];" : "=l"(n) : "l"(a));
         else
@@ -809,29 +809,30 @@ __device__ __forceinline__ void cta_pos(const SpecLaunch& p, bool reload, int64_
     n = n < 0 ? 0 : (n > p.max_len ? p.max_len : n);
     *len = n;
     *F = (n + p.hop - 1) / p.hop;
-    *k0 = (int64_t)blockIdx.x * p.seg_frames;
+    *k0 = (int64_t)seg * p.seg_frames;
 }
 
 template <int THREADS, bool PRUNE>
-__device__ __forceinline__ void spectral_body(const SpecLaunch& p);
+__device__ __forceinline__ void spectral_body(const SpecLaunch& p, int seg, int clip, int grp);
 
+// One work item: segment `seg` of clip `clip`, scale group `grp` of `ngrp`
+// (the spectral scales of the group and the fused tap groups grp, grp +
+// ngrp, ...).  Every thread of the CTA calls it with the same arguments.
 // PRUNE: inverse FFTs skip the passes that a chunk's narrow bands leave
 // trivial (plans whose narrowest folded band fits a small fraction of P).
 template <int THREADS, bool PRUNE>
-__global__ void __launch_bounds__(THREADS, THREADS >= 1024 ? 1 : 2)
-    spectral_segment_kernel(const SpecLaunch p) {
-    constexpr int kPPT = kMaxFftPoints / THREADS;  // FFT points per thread
+__device__ __forceinline__ void spectral_item(const SpecLaunch& p, int seg, int clip, int grp,
+                                              int ngrp) {
     extern __shared__ float2 smem[];
-    const int M = p.M, Mh = M >> 1, P = p.P;
+    const int M = p.M, Mh = M >> 1;
     const int ntw = (M >> 7) + 128;
     float2* T = smem;                 // two-level twiddle table, ntw entries
     float2* X = smem + ntw;           // Mh + 1 used
     float2* Z = smem + ntw + Mh + 2;  // nconc * P used
     const TwTab tab{T, T + (M >> 7)};
 
-    const int clip = blockIdx.y, grp = blockIdx.z;
     int64_t len, F, k0;
-    cta_pos(p, false, &len, &F, &k0);
+    cta_pos(p, false, seg, clip, &len, &F, &k0);
     const bool has_sp = grp * p.group_size < p.n_sp;
     const bool has_fd = grp < p.fd_groups;
     if (k0 >= F || !(has_sp || has_fd)) return;
@@ -896,11 +897,8 @@ __global__ void __launch_bounds__(THREADS, THREADS >= 1024 ? 1 : 2)
     }
     __syncthreads();
 
-    // Short-support scales: their frame windows leave X for a buffer of
-    // their own (after the fold's) before the forward FFT overwrites X; the
-    // FFT's first pass writes only after a barrier that follows this copy.
-    // Their sums run as items of the first fold phase (or here, alone, when
-    // the CTA has no spectral scales).
+    // Short-support scales: summed here, before the forward FFT overwrites
+    // the staged samples.
     if (has_fd) {
         // Fused time-domain scales: taps and frame windows in the fold's
         // buffer (unused until the fold), items dealt to whichever warp is
@@ -911,7 +909,7 @@ __global__ void __launch_bounds__(THREADS, THREADS >= 1024 ? 1 : 2)
         if (threadIdx.x == 0) s_ctr = 0;
         fd_copy_windows(p, reinterpret_cast<const float*>(X), Xw, Tfd);
         __syncthreads();
-        const FdWork fw = fd_work(p, Xw, Tfd, clip, k0, F, grp, gridDim.z);
+        const FdWork fw = fd_work(p, Xw, Tfd, clip, k0, F, grp, ngrp);
         const int lane = threadIdx.x & 31;
         for (;;) {
             int it = 0;
@@ -923,14 +921,36 @@ __global__ void __launch_bounds__(THREADS, THREADS >= 1024 ? 1 : 2)
         __syncthreads();
     }
     if (!has_sp) return;
-    spectral_body<THREADS, PRUNE>(p);
+    spectral_body<THREADS, PRUNE>(p, seg, clip, grp);
+}
+
+// One CTA per (segment, clip, scale group) of one plan.
+template <int THREADS, bool PRUNE>
+__global__ void __launch_bounds__(THREADS, THREADS >= 1024 ? 1 : 2)
+    spectral_segment_kernel(const SpecLaunch p) {
+    spectral_item<THREADS, PRUNE>(p, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.z);
+}
+
+// One launch over a device work list spanning several plans (the groups
+// of an uneven batch): block i runs item i, {group, segment, clip, scale
+// group | scale groups << 16}, with its plan's record read from the launch
+// parameters as in the one-plan kernel.  Items come longest first, so the
+// hardware's block scheduler, which starts blocks in order as SMs free up,
+// deals them longest-first to whichever SM is free.  (A loop over items
+// inside one block keeps the item's state in registers across iterations
+// and spills; one item per block does not.)
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS, THREADS >= 1024 ? 1 : 2)
+    spectral_worklist_kernel(const __grid_constant__ SpecWorkList wl) {
+    const int4 w = __ldg(wl.items + blockIdx.x);
+    spectral_item<THREADS, false>(wl.g[w.x], w.y, w.z, w.w & 0xffff, w.w >> 16);
 }
 
 // Everything from the forward FFT on.  Its per-CTA values are derived again
 // from the launch parameters (the clip length reloaded), so that none of
 // them occupies a register through the FFT passes.
 template <int THREADS, bool PRUNE>
-__device__ __forceinline__ void spectral_body(const SpecLaunch& p) {
+__device__ __forceinline__ void spectral_body(const SpecLaunch& p, int seg, int clip, int grp) {
     constexpr int kPPT = kMaxFftPoints / THREADS;  // FFT points per thread
     extern __shared__ float2 smem[];
     const int M = p.M, Mh = M >> 1;
@@ -962,9 +982,8 @@ __device__ __forceinline__ void spectral_body(const SpecLaunch& p) {
 
     const int P = p.P;
     float2* Z = smem + ntw + Mh + 2;
-    const int clip = blockIdx.y, grp = blockIdx.z;
     int64_t len, F, k0;
-    cta_pos(p, true, &len, &F, &k0);
+    cta_pos(p, true, seg, clip, &len, &F, &k0);
     const int sp_begin = grp * p.group_size;
     const int sp_end = min(p.n_sp, sp_begin + p.group_size);
     const int lgP = __ffs(P) - 1;
@@ -1100,7 +1119,8 @@ int spectral_twiddle_entries(int M) { return (M >> 7) + 128; }
 
 cudaError_t spectral_prepare_device() {
     cudaError_t e = cudaSuccess;
-    for (const void* f : {(const void*)spectral_segment_kernel<kSpecThreadsPair, false>,
+    for (const void* f : {(const void*)spectral_worklist_kernel<kSpecThreadsPair>,
+                          (const void*)spectral_segment_kernel<kSpecThreadsPair, false>,
                           (const void*)spectral_segment_kernel<kSpecThreadsPair, true>,
                           (const void*)spectral_segment_kernel<kSpecThreadsSolo, false>,
                           (const void*)spectral_segment_kernel<kSpecThreadsSolo, true>})
@@ -1108,6 +1128,12 @@ cudaError_t spectral_prepare_device() {
             e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      227 * 1024 - 1024);
     return e;
+}
+
+cudaError_t spectral_worklist_launch(const SpecWorkList& wl, size_t smem, cudaStream_t st) {
+    if (wl.n_items <= 0) return cudaSuccess;
+    spectral_worklist_kernel<kSpecThreadsPair><<<wl.n_items, kSpecThreadsPair, smem, st>>>(wl);
+    return cudaGetLastError();
 }
 
 cudaError_t spectral_make_twiddles(float2* d_tw, int M, cudaStream_t st) {

@@ -26,7 +26,8 @@ EXPORTS = ("cwth_plan", "cwth_execute", "cwth_execute_host", "cwth_destroy",
            "cwth_plan_scale_paths", "cwth_sync", "cwth_last_error",
            "cwth_execute_direct_noalloc", "cwth_plan_set_host_chunks",
            "cwth_selftest_wait_timeout", "cwth_measure_fp32_fma", "cwth_plan_resampled",
-           "cwth_plan_segment", "cwth_noalloc_status")
+           "cwth_plan_segment", "cwth_noalloc_status", "cwth_batch_create",
+           "cwth_batch_execute", "cwth_batch_items", "cwth_batch_destroy")
 
 
 class CwthError(RuntimeError):
@@ -100,6 +101,16 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.cwth_execute_direct_noalloc.restype = ctypes.c_int
     lib.cwth_noalloc_status.argtypes = [vp]
     lib.cwth_noalloc_status.restype = ctypes.c_int
+    pp = ctypes.POINTER(vp)
+    lib.cwth_batch_create.argtypes = [i32, pp, pp, ctypes.POINTER(i64), pp, pp,
+                                      ctypes.POINTER(i32), pp, ctypes.POINTER(vp)]
+    lib.cwth_batch_create.restype = ctypes.c_int
+    lib.cwth_batch_execute.argtypes = [vp, vp]
+    lib.cwth_batch_execute.restype = ctypes.c_int
+    lib.cwth_batch_items.argtypes = [vp]
+    lib.cwth_batch_items.restype = i64
+    lib.cwth_batch_destroy.argtypes = [vp]
+    lib.cwth_batch_destroy.restype = ctypes.c_int
     return lib
 
 
@@ -292,3 +303,70 @@ class Plan:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Batch:
+    """A cwth_batch_t: groups of (plan, device batch) run by one kernel launch.
+
+    groups: list of (plan, x, lengths, out, host_lengths) with x a float32
+    CUDA tensor [B, ld], lengths an int64 CUDA tensor [B] or None, out the
+    float32 CUDA output [B, S, frames_max] and host_lengths a numpy int64
+    array (or None).  The tensors must outlive the batch."""
+
+    def __init__(self, groups):
+        n = len(groups)
+        vp = ctypes.c_void_p
+        self._keep = []
+        plans = (vp * n)(*[g[0].handle.value for g in groups])
+        xs = (vp * n)(*[g[1].data_ptr() for g in groups])
+        lds = (ctypes.c_int64 * n)(*[int(g[1].shape[1]) if g[1].shape[0] == 1
+                                     else int(g[1].stride(0)) for g in groups])
+        dl = (vp * n)(*[(g[2].data_ptr() if g[2] is not None else None) for g in groups])
+        hl = []
+        for g in groups:
+            if g[4] is None:
+                hl.append(None)
+            else:
+                a = np.ascontiguousarray(np.asarray(g[4], np.int64))
+                self._keep.append(a)
+                hl.append(a.ctypes.data)
+        hla = (vp * n)(*hl)
+        bs = (ctypes.c_int32 * n)(*[int(g[1].shape[0]) for g in groups])
+        outs = (vp * n)(*[g[3].data_ptr() for g in groups])
+        for g in groups:
+            x, ln, out = g[1], g[2], g[3]
+            if x.dtype.__str__() != "torch.float32" or not x.is_cuda or x.stride(1) != 1:
+                raise ValueError("x must be a float32 CUDA tensor with unit column stride")
+            if ln is not None and (str(ln.dtype) != "torch.int64" or not ln.is_cuda):
+                raise ValueError("lengths must be an int64 CUDA tensor")
+            if (str(out.dtype) != "torch.float32" or not out.is_cuda or not out.is_contiguous()
+                    or tuple(out.shape) != (x.shape[0], g[0].S, g[0].frames_max)):
+                raise ValueError("out must be a contiguous float32 CUDA tensor [B, S, frames_max]")
+        self._h = vp()
+        _check(_lib.cwth_batch_create(n, plans, xs, lds, dl, hla, bs, outs, ctypes.byref(self._h)),
+               "cwth_batch_create")
+        self.groups = groups
+
+    @property
+    def items(self) -> int:
+        return int(_lib.cwth_batch_items(self._h))
+
+    def execute(self, stream=None):
+        """One kernel launch over every group, on ``stream`` (asynchronous)."""
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        _check(_lib.cwth_batch_execute(self._h, ctypes.c_void_p(stream.cuda_stream)),
+               "cwth_batch_execute")
+
+    def close(self):
+        if self._h:
+            _check(_lib.cwth_batch_destroy(self._h), "cwth_batch_destroy")
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
