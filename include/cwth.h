@@ -136,9 +136,18 @@ cwth_status cwth_plan_segment(const cwth_morlet *w, const double *scales, int32_
  *             written.  d_out must not overlap d_x.
  *   stream    cudaStream_t as void*, NULL for the legacy default stream.
  *
+ * Workspace: plans with direct-path scales at a bf16 precision stage the
+ * batch as bf16 parts, and resample-first plans re-sample it, in device
+ * buffers the plan owns and keeps at the largest batch seen.  A call with a
+ * larger batch than any before frees and re-allocates them (cudaFree /
+ * cudaMalloc, which wait for the device to go idle); calls with smaller or
+ * equal batches allocate nothing.  cwth_plan_reserve sizes them up front.
+ * Float32 plans whose scales all take the spectral path never allocate here.
+ *
  * Errors: CWTH_ERR_BAD_PLAN, CWTH_ERR_INVALID_ARG (NULL buffer with
- * batch > 0, ld_x < max_len, batch < 0), CWTH_ERR_CUDA (launch failure).
- * Kernel faults surface later, at the caller's next synchronisation.
+ * batch > 0, ld_x < max_len, batch < 0), CWTH_ERR_OOM (a workspace could
+ * not grow), CWTH_ERR_CUDA (launch failure).  Kernel faults surface later,
+ * at the caller's next synchronisation.
  */
 cwth_status cwth_execute(cwth_plan_t plan, const float *d_x, int64_t ld_x,
                          const int64_t *d_lengths, int32_t batch, float *d_out,
@@ -194,6 +203,27 @@ cwth_status cwth_execute_host(cwth_plan_t plan, const float *h_x, int64_t ld_x,
  * Errors: CWTH_ERR_BAD_PLAN, CWTH_ERR_INVALID_ARG (n < 0).
  */
 cwth_status cwth_plan_set_host_chunks(cwth_plan_t plan, int32_t n);
+
+/*
+ * Sizes a plan's growable device workspaces for batches of up to `batch`
+ * clips, so that later cwth_execute calls with batch' <= batch allocate
+ * nothing (and, with host != 0, cwth_execute_host calls with batch' <= batch
+ * and row stride ld_x as well: it also creates the host pipeline's streams
+ * and events).  Which workspaces exist depends on the plan (see
+ * cwth_execute); a plan without any returns CWTH_OK at once.  Synchronous:
+ * growing frees the old buffers (cudaFree waits for the device) and
+ * allocates new ones.  No paper counterpart: it only moves allocation out
+ * of the calls that transform.
+ *   batch  clips, >= 0 (0 is a no-op).
+ *   ld_x   row stride in elements of the host input (ignored when host is
+ *          0), >= max_len (for a resample-first plan, the longest clip
+ *          before re-sampling).
+ *   host   nonzero to size cwth_execute_host's staging too.
+ * Errors: CWTH_ERR_BAD_PLAN, CWTH_ERR_INVALID_ARG (batch < 0, host != 0 and
+ * ld_x too small), CWTH_ERR_UNSUPPORTED (the staged direct-path signal would
+ * exceed 2^31 rows), CWTH_ERR_OOM, CWTH_ERR_CUDA.
+ */
+cwth_status cwth_plan_reserve(cwth_plan_t plan, int32_t batch, int64_t ld_x, int32_t host);
 
 /* Release a plan's device tables and staging.  NULL is accepted.  The caller
  * must not destroy a plan while work it enqueued may still be running. */

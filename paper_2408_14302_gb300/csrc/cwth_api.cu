@@ -819,6 +819,46 @@ cwth_status launch_spectral(cwth_plan_s* p, const float* d_x, int64_t ld_x,
         cwth::spectral_launch(L, threads, p->spec_prune, p->n_seg, batch, n_groups, smem, st));
 }
 
+// Rows of one clip in the direct path's staged signal (the clip with its
+// zero margins, in whole hops) and the staged elements of a batch.
+struct DirStageShape {
+    int64_t rows_per_clip, lpad, total_rows, total;
+};
+
+DirStageShape dir_stage_shape(const cwth_plan_s* p, int32_t batch) {
+    DirStageShape d;
+    const int64_t hop = p->hop;
+    d.rows_per_clip = (2 * (int64_t)p->dir_front + p->frames_max * hop + p->dir_taps + hop - 1) / hop;
+    d.lpad = d.rows_per_clip * hop;
+    d.total_rows = (int64_t)batch * d.rows_per_clip;
+    d.total = (int64_t)batch * d.lpad + p->dir_front + p->dir_taps + 64;
+    return d;
+}
+
+// Grows the staged bf16 signal to `total` elements per part.  Growing frees
+// the old buffers first (cudaFree waits for the device to finish the work
+// that may still read them).
+cwth_status dir_stage_grow(cwth_plan_s* p, int64_t total) {
+    const int nparts = direct_parts(p->precision);
+    if ((size_t)total > p->x_elems) {
+        cudaFree(p->d_xhi);
+        cudaFree(p->d_xlo);
+        cudaFree(p->d_xlo2);
+        p->d_xhi = nullptr;
+        p->d_xlo = nullptr;
+        p->d_xlo2 = nullptr;
+        p->x_elems = 0;
+        p->x_maps_ptr = nullptr;
+        cudaError_t e = cudaMalloc(&p->d_xhi, sizeof(__nv_bfloat16) * (size_t)total);
+        if (e == cudaSuccess) e = cudaMalloc(&p->d_xlo, sizeof(__nv_bfloat16) * (size_t)total);
+        if (e == cudaSuccess && nparts > 2)
+            e = cudaMalloc(&p->d_xlo2, sizeof(__nv_bfloat16) * (size_t)total);
+        if (e != cudaSuccess) return cuda_status(e);
+        p->x_elems = (size_t)total;
+    }
+    return CWTH_OK;
+}
+
 cwth_status launch_direct(cwth_plan_s* p, const float* d_x, int64_t ld_x, const int64_t* d_len,
                           int32_t batch, float* d_out, cudaStream_t st) {
     if (p->n_dir == 0 || batch == 0) return CWTH_OK;
@@ -846,27 +886,15 @@ cwth_status launch_direct(cwth_plan_s* p, const float* d_x, int64_t ld_x, const 
     }
     const int nparts = direct_parts(p->precision);
     const int64_t hop = p->hop;
-    const int64_t rows_per_clip =
-        (2 * (int64_t)p->dir_front + p->frames_max * hop + p->dir_taps + hop - 1) / hop;
-    const int64_t lpad = rows_per_clip * hop;
-    const int64_t total_rows = (int64_t)batch * rows_per_clip;
-    const int64_t total = (int64_t)batch * lpad + p->dir_front + p->dir_taps + 64;
+    const DirStageShape sh = dir_stage_shape(p, batch);
+    const int64_t rows_per_clip = sh.rows_per_clip;
+    const int64_t lpad = sh.lpad;
+    const int64_t total_rows = sh.total_rows;
+    const int64_t total = sh.total;
     if (total_rows > (int64_t(1) << 31) - 256) return CWTH_ERR_UNSUPPORTED;
-    if ((size_t)total > p->x_elems) {
-        cudaFree(p->d_xhi);
-        cudaFree(p->d_xlo);
-        cudaFree(p->d_xlo2);
-        p->d_xhi = nullptr;
-        p->d_xlo = nullptr;
-        p->d_xlo2 = nullptr;
-        p->x_elems = 0;
-        p->x_maps_ptr = nullptr;
-        cudaError_t e = cudaMalloc(&p->d_xhi, sizeof(__nv_bfloat16) * (size_t)total);
-        if (e == cudaSuccess) e = cudaMalloc(&p->d_xlo, sizeof(__nv_bfloat16) * (size_t)total);
-        if (e == cudaSuccess && nparts > 2)
-            e = cudaMalloc(&p->d_xlo2, sizeof(__nv_bfloat16) * (size_t)total);
-        if (e != cudaSuccess) return cuda_status(e);
-        p->x_elems = (size_t)total;
+    {
+        cwth_status gs = dir_stage_grow(p, total);
+        if (gs != CWTH_OK) return gs;
     }
     if (p->x_maps_ptr != p->d_xhi || p->x_maps_rows != total_rows) {
         p->maps_a_hi.assign(p->groups.size(), CUtensorMap());
@@ -1242,6 +1270,33 @@ cwth_status cwth_execute_host(cwth_plan_t p, const float* h_x, int64_t ld_x,
     if (s != CWTH_OK) return s;
     if (ej != cudaSuccess) return cuda_status(ej);
     return cuda_status(es);
+}
+
+cwth_status cwth_plan_reserve(cwth_plan_t p, int32_t batch, int64_t ld_x, int32_t host) {
+    if (!valid_plan(p)) return CWTH_ERR_BAD_PLAN;
+    if (batch < 0 || (host && ld_x < input_len(p))) return CWTH_ERR_INVALID_ARG;
+    if (batch == 0) return CWTH_OK;
+    DeviceGuard g(p->device);
+    if (!g.ok) return CWTH_ERR_CUDA;
+    cwth_status s = CWTH_OK;
+    if (p->n_dir > 0 && p->precision != CWTH_PREC_FP32) {
+        const DirStageShape sh = dir_stage_shape(p, batch);
+        if (sh.total_rows > (int64_t(1) << 31) - 256) return CWTH_ERR_UNSUPPORTED;
+        s = dir_stage_grow(p, sh.total);
+    }
+    if (s == CWTH_OK && p->resample > 1) {
+        s = grow(&p->d_res, &p->res_elems, (size_t)batch * (size_t)p->max_len);
+        if (s == CWTH_OK) s = grow(&p->d_res_len, &p->res_len_elems, (size_t)batch);
+    }
+    if (s == CWTH_OK && host) {
+        s = grow(&p->d_stage_x, &p->stage_x_elems, (size_t)batch * (size_t)ld_x);
+        if (s == CWTH_OK)
+            s = grow(&p->d_stage_out, &p->stage_out_elems,
+                     (size_t)batch * (size_t)p->S * (size_t)p->frames_max);
+        if (s == CWTH_OK) s = grow(&p->d_stage_len, &p->stage_len_elems, (size_t)batch);
+        if (s == CWTH_OK) s = cuda_status(host_pipeline_init(p));
+    }
+    return s;
 }
 
 cwth_status cwth_plan_set_host_chunks(cwth_plan_t p, int32_t chunks) {

@@ -27,7 +27,8 @@ EXPORTS = ("cwth_plan", "cwth_execute", "cwth_execute_host", "cwth_destroy",
            "cwth_execute_direct_noalloc", "cwth_plan_set_host_chunks",
            "cwth_selftest_wait_timeout", "cwth_measure_fp32_fma", "cwth_plan_resampled",
            "cwth_plan_segment", "cwth_noalloc_status", "cwth_batch_create",
-           "cwth_batch_execute", "cwth_batch_items", "cwth_batch_destroy")
+           "cwth_batch_execute", "cwth_batch_items", "cwth_batch_destroy",
+           "cwth_plan_reserve")
 
 
 class CwthError(RuntimeError):
@@ -77,6 +78,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.cwth_execute_host.restype = ctypes.c_int
     lib.cwth_plan_set_host_chunks.argtypes = [vp, i32]
     lib.cwth_plan_set_host_chunks.restype = ctypes.c_int
+    lib.cwth_plan_reserve.argtypes = [vp, i32, i64, i32]
+    lib.cwth_plan_reserve.restype = ctypes.c_int
     lib.cwth_selftest_wait_timeout.argtypes = [vp, i64, vp]
     lib.cwth_selftest_wait_timeout.restype = ctypes.c_int
     lib.cwth_measure_fp32_fma.argtypes = [ctypes.POINTER(ctypes.c_double), vp]
@@ -280,6 +283,13 @@ class Plan:
     def set_host_chunks(self, n: int):
         """Chunks of execute_host (0 = automatic); see cwth_plan_set_host_chunks."""
         _check(_lib.cwth_plan_set_host_chunks(self._h, int(n)), "cwth_plan_set_host_chunks")
+
+    def reserve(self, batch: int, ld_x: int = 0, host: bool = False):
+        """Sizes the plan's growable workspaces for `batch` clips so later
+        executes of at most that many clips allocate nothing; see
+        cwth_plan_reserve."""
+        _check(_lib.cwth_plan_reserve(self._h, int(batch), int(ld_x), 1 if host else 0),
+               "cwth_plan_reserve")
 
     def sync(self, stream=None):
         """Wait for this plan's work on ``stream`` and raise on device-side

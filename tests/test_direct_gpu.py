@@ -175,3 +175,43 @@ def test_direct_unsupported_cases(cw):
         cw.Plan([2.0], hop=12, max_len=1000, precision="bf16", path="direct")   # hop % 8
     with pytest.raises(cw.CwthError):
         cw.Plan([900.0], hop=64, max_len=1000, precision="bf16", path="direct")  # > 4096 taps
+
+
+def test_reserve_moves_workspace_growth_out_of_execute(cw, sig):
+    """cwth_plan_reserve sizes the staged bf16 signal (and the host
+    pipeline's staging) up front: after it, executes of up to that many
+    clips leave the device's free memory unchanged, and give the same bytes
+    as a plan that grew its workspace inside execute."""
+    n, hop, B = 32000, 64, 48
+    sc = sig.scales_for_band(100, 8000, 48, 16000.0)
+    xh = np.ascontiguousarray(sig.machine_batch(B, n))
+    xs = torch.from_numpy(xh).cuda()
+
+    def one(reserve):
+        with cw.Plan(sc, hop=hop, max_len=n, precision="bf16x2", path="direct") as plan:
+            out = torch.empty((B, len(sc), plan.frames_max), device="cuda")
+            # One clip first, so every kernel is loaded before memory is read.
+            plan.execute(xs[:1], out=out[:1])
+            plan.sync()
+            if reserve:
+                plan.reserve(B, ld_x=n, host=True)
+            torch.cuda.synchronize()
+            free0 = torch.cuda.mem_get_info()[0]
+            for b in (16, B, 32):
+                plan.execute(xs[:b], out=out[:b])
+            plan.sync()
+            free1 = torch.cuda.mem_get_info()[0]
+            if reserve:
+                h_out = np.empty((B, len(sc), plan.frames_max), np.float32)
+                plan.execute_host(xh, h_out)
+                assert torch.cuda.mem_get_info()[0] == free1
+                assert np.array_equal(h_out, out.cpu().numpy())
+            return out.cpu().numpy(), free0 - free1
+
+    got, grew = one(True)
+    ref, grew_plain = one(False)
+    assert grew == 0, grew
+    # Control: without the reservation the same calls allocate (48 clips of
+    # 32000 samples staged as two bf16 parts are about 6 MB).
+    assert grew_plain > 0
+    assert np.array_equal(got, ref)
