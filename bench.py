@@ -553,7 +553,7 @@ def run_ours(args, rank, world, local_rank):
                      "peak": pk["hbm_gbs"] if t_hbm_peak >= t_alu_peak else peak_alu,
                      "unit": "GB/s" if t_hbm_peak >= t_alu_peak else "TFLOP/s",
                      "frac": max(t_hbm_peak, t_alu_peak) / t_step,
-                     "traffic": kernel_traffic("spectral_segment_kernel", "spectral.cu"),
+                     "traffic": kernel_traffic("spectral_segment_kernel", "spectral_kernel.cuh"),
                      "algorithmic_bytes_per_launch": bytes_launch,
                      "algorithmic_bytes_per_clip": bytes_launch / N_CLIPS,
                      "peak_source": f"{pk_kind} HBM copy bandwidth (MEASURED_PEAKS.json)",

@@ -94,8 +94,10 @@ enum {
  * with them.  Errors: CWTH_ERR_INVALID_ARG for a NULL pointer, S/hop/max_len
  * < 1, a scale that is not finite and positive, B/C/fs not finite and
  * positive, or an unknown flag; CWTH_ERR_UNSUPPORTED when the forced path
- * cannot serve the request (the spectral path needs a power-of-two hop; the
- * direct path needs hop % 8 == 0 for bf16 operands and at most 4096 taps);
+ * cannot serve the request (the spectral path needs hop = 2^e d with d a
+ * product of 3, 5 and 7 no larger than 27, e.g. 3, 96 or 100, and
+ * hop <= 2048; the direct path needs hop % 8 == 0 for bf16 operands and at
+ * most 4096 taps);
  * CWTH_ERR_OOM / CWTH_ERR_CUDA otherwise.  On error *out is set to NULL.
  */
 cwth_status cwth_plan(const cwth_morlet *w, const double *scales, int32_t S, int32_t hop,
@@ -108,14 +110,17 @@ cwth_status cwth_plan(const cwth_morlet *w, const double *scales, int32_t S, int
  * any other segment length within the float32 tolerance: every valid
  * segment gives the linear correlation of Eq. 1 at its frames).
  *
- *   seg_len   0: automatic (exactly cwth_plan); else a power of two M in
- *             [512, 32768] with M / hop >= 8.
+ *   seg_len   0: automatic (exactly cwth_plan); else M in [512, 32768] of
+ *             the form 2^k d, d a product of 3, 5 and 7 no larger than 27
+ *             (a power of two for power-of-two hops).  The spectral path
+ *             uses M = 2 d N2 with d the odd part of the hop, N2 a power of
+ *             two in [256, 8192 / d] and M / hop >= 8.
  *
  * Errors: those of cwth_plan; CWTH_ERR_INVALID_ARG for a seg_len that is
- * negative or not a power of two in range; CWTH_ERR_UNSUPPORTED when the
- * plan has spectral-path scales and M cannot serve them (M / hop < 8, the
- * wavelet support leaves no valid frame, or the segment's shared-memory
- * footprint exceeds a CTA's).
+ * negative, out of range or of another form; CWTH_ERR_UNSUPPORTED when the
+ * plan has spectral-path scales and M cannot serve them (its odd part is
+ * not the hop's, M / hop < 8, the wavelet support leaves no valid frame, or
+ * the segment's shared-memory footprint exceeds a CTA's).
  */
 cwth_status cwth_plan_segment(const cwth_morlet *w, const double *scales, int32_t S,
                               int32_t hop, double sample_rate, int64_t max_len,

@@ -102,6 +102,26 @@ constexpr int kSplitAutoTaps = 1024;
 constexpr int64_t kMaxSelftestBudget = 4000000000LL;
 
 bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+
+// Odd factors the spectral kernel's forward FFT takes beside a power of
+// two: products of 3, 5 and 7 up to 27 (the odd-radix passes run over d
+// columns of at least 256 points within 8192).
+bool spectral_odd_ok(int64_t d) {
+    if (d < 1 || d > 27) return false;
+    for (int r : {3, 5, 7})
+        while (d % r == 0) d /= r;
+    return d == 1;
+}
+
+// Odd part of v > 0.
+int64_t odd_part(int64_t v) {
+    while (v > 0 && (v & 1) == 0) v >>= 1;
+    return v;
+}
+
+// Hops the spectral path serves: 2^e d with d as above.  Segments are
+// M = 2 d N2 samples (N2 a power of two), so P = M / H is a power of two.
+bool spectral_hop_ok(int64_t hop) { return hop > 0 && spectral_odd_ok(odd_part(hop)); }
 int ilog2(int64_t v) {
     int e = 0;
     while ((int64_t(1) << e) < v) ++e;
@@ -233,10 +253,12 @@ std::vector<cwth::FdGroup> fd_make_groups(const std::vector<int32_t>& h_desc, in
     return g;
 }
 
-// Segment length for the spectral kernel: the power of two M (P = M/H >= 8,
-// shared memory within bounds) minimising a lane-operation cost model of
-// staging + FFT + fold + inverse FFTs + stores + the fused time-domain
-// phase per clip.  fd_h: half supports of the fused scales, descending.
+// Segment length for the spectral kernel: M = 2 d N2, d the odd part of
+// the hop and N2 a power of two (so M is a power of two for power-of-two
+// hops; P = M/H >= 8, shared memory within bounds), minimising a
+// lane-operation cost model of staging + FFT + fold + inverse FFTs + stores
+// + the fused time-domain phase per clip.  fd_h: half supports of the fused
+// scales, descending.
 bool choose_segment(const cwth_plan_s& p, const std::vector<double>& sp_scales,
                     const std::vector<int32_t>& fd_h, SegChoice* out) {
     double a_max = 0;
@@ -251,8 +273,11 @@ bool choose_segment(const cwth_plan_s& p, const std::vector<double>& sp_scales,
     const int64_t kp0 = halo / hop;
     const bool sp = !sp_scales.empty();
     bool found = false;
-    for (int lg = 9; lg <= 15; ++lg) {
-        const int64_t M = int64_t(1) << lg;
+    const int64_t d = odd_part(hop);
+    for (int lg = 8; lg <= 13; ++lg) {
+        const int64_t n2 = int64_t(1) << lg;
+        if (d * n2 > cwth::kMaxFftPoints) continue;
+        const int64_t M = 2 * d * n2;
         if (p.seg_force > 0 && M != p.seg_force) continue;
         if (M < 8 * (int64_t)hop) continue;
         const int64_t P = M / hop;
@@ -272,7 +297,16 @@ bool choose_segment(const cwth_plan_s& p, const std::vector<double>& sp_scales,
             band_limits(a, p.B, p.C, (int)M, &lo, &hi);
             fold += 12.0 * (double)(hi - lo + 1) + 4.0 * (double)P;
         }
-        const double fft = sp ? 2.5 * (double)(M / 2) * (lg - 1) + 8.0 * (double)M : 2.0 * (double)M;
+        // Odd-radix passes: a direct length-R DFT per butterfly, about R + 3
+        // lane operations per point and pass.
+        double odd = 0;
+        for (int64_t r = d; r > 1;) {
+            const int R = r % 7 == 0 ? 7 : (r % 5 == 0 ? 5 : 3);
+            odd += (R + 3.0) * (double)(M / 2);
+            r /= R;
+        }
+        const double fft =
+            sp ? 2.5 * (double)(M / 2) * lg + odd + 8.0 * (double)M : 2.0 * (double)M;
         const double ifft = 2.5 * (double)P * ilog2(P) * (double)sp_scales.size();
         const double store = 2.0 * (double)Fseg * (double)sp_scales.size();
         const int nconc = spectral_nconc((int)M, (int)P, std::max<int>(1, (int)sp_scales.size()),
@@ -615,7 +649,7 @@ cwth_status build_spectral(cwth_plan_s* p) {
     for (int32_t s : fd_idx) fd_h.push_back(fd_half_support(p->scales[s], p->B));
     p->n_fd = (int32_t)fd_idx.size();
     if (p->n_sp == 0 && p->n_fd == 0) return CWTH_OK;
-    if (!is_pow2(p->hop)) return CWTH_ERR_UNSUPPORTED;
+    if (!spectral_hop_ok(p->hop)) return CWTH_ERR_UNSUPPORTED;
     SegChoice ch;
     if (!choose_segment(*p, sp, fd_h, &ch)) return CWTH_ERR_UNSUPPORTED;
     p->M = ch.M;
@@ -625,6 +659,8 @@ cwth_status build_spectral(cwth_plan_s* p) {
     p->seg_frames = ch.seg_frames;
     p->n_seg = ch.n_seg;
     p->seg_cost = ch.n_seg > 0 ? ch.cost / ch.n_seg : 0.0;
+    p->fft_d = (int32_t)odd_part(p->M);
+    p->fft_n2 = p->M / 2 / p->fft_d;
 
     std::vector<SpecScale> host(sp.size());
     for (size_t i = 0; i < sp.size(); ++i) {
@@ -789,7 +825,7 @@ void spectral_record(const cwth_plan_s* p, const float* d_x, int64_t ld_x, const
     L.kexp = (float)(-M_PI * M_PI * p->B / M_LN2);
     L.tw = p->d_tw;
     L.sc = p->d_sp;
-    L.vec4 = (ld_x % 4 == 0 && ((uintptr_t)d_x & 15) == 0 && p->halo % 4 == 0 &&
+    L.vec4 = (p->fft_d == 1 && ld_x % 4 == 0 && ((uintptr_t)d_x & 15) == 0 && p->halo % 4 == 0 &&
               ((int64_t)p->seg_frames * p->hop) % 4 == 0)
                  ? 1
                  : 0;
@@ -800,6 +836,8 @@ void spectral_record(const cwth_plan_s* p, const float* d_x, int64_t ld_x, const
     L.fd_taps = p->d_fd_taps;
     L.fd_grp = p->d_fd_grp;
     L.inv_r8 = p->inv_r8 ? 1 : 0;
+    L.fft_d = p->fft_d;
+    L.fft_n2 = p->fft_n2;
     *out = L;
     *threads_out = threads;
     *n_groups_out = n_groups;
@@ -1052,7 +1090,8 @@ cwth_status cwth_plan_segment(const cwth_morlet* w, const double* scales, int32_
                               int32_t precision, int32_t path, int32_t seg_len,
                               cwth_plan_t* out) {
     if (out) *out = nullptr;
-    if (seg_len < 0 || (seg_len > 0 && (seg_len < 512 || seg_len > 32768 || !is_pow2(seg_len))))
+    if (seg_len < 0 || (seg_len > 0 && (seg_len < 512 || seg_len > 32768 ||
+                                         !spectral_odd_ok(odd_part(seg_len)))))
         return CWTH_ERR_INVALID_ARG;
     return plan_create(w, scales, S, hop, sample_rate, max_len, precision, path, seg_len, out);
 }
@@ -1093,7 +1132,7 @@ cwth_status plan_create(const cwth_morlet* w, const double* scales, int32_t S, i
         p->frames_max = cwth_num_frames(max_len, hop);
         p->scales.assign(scales, scales + S);
         p->scale_path.assign(S, CWTH_PATH_SPECTRAL);
-        const bool spectral_ok = is_pow2(hop);
+        const bool spectral_ok = spectral_hop_ok(hop);
         for (int32_t s = 0; s < S && st == CWTH_OK; ++s) {
             const bool direct_ok = direct_eligible(*p, scales[s]);
             int32_t choice;
@@ -1114,7 +1153,8 @@ cwth_status plan_create(const cwth_morlet* w, const double* scales, int32_t S, i
         // moves the short-support scales, whose hop fold would cost more
         // than their direct sums, into the spectral kernel's time-domain
         // phase.
-        if (st == CWTH_OK && path == CWTH_PATH_AUTO && precision == CWTH_PREC_FP32 && spectral_ok) {
+        if (st == CWTH_OK && path == CWTH_PATH_AUTO && precision == CWTH_PREC_FP32 && spectral_ok &&
+            is_pow2(hop)) {
             std::vector<int32_t> asc(S);
             for (int32_t s = 0; s < S; ++s) asc[s] = s;
             std::stable_sort(asc.begin(), asc.end(),

@@ -103,6 +103,11 @@ struct SpecLaunch {
     // 1: the inverse FFTs of the 512-thread shape use the radix-8 plan (one
     // radix-8 butterfly per thread: nc * P <= 4096), else radix 16
     int32_t inv_r8;
+    // forward FFT of M/2 = fft_d * fft_n2 points: fft_d (the odd part of the
+    // hop, 1 for power-of-two hops) column FFTs of fft_n2 = 2^k points, the
+    // staged samples permuted into columns, then radix-3/5/7 passes
+    int32_t fft_d;
+    int32_t fft_n2;
 };
 
 // Plan records of a persistent batch launch, passed by value (the launch
@@ -174,6 +179,10 @@ cudaError_t spectral_prepare_device();
 cudaError_t spectral_make_twiddles(float2* d_tw, int M, cudaStream_t st);
 cudaError_t spectral_launch(const SpecLaunch& L, int threads, bool prune, int n_seg, int batch,
                             int n_groups, size_t smem, cudaStream_t st);
+// The 1024-thread instantiations (compiled in their own translation unit).
+cudaError_t spectral_prepare_solo();
+cudaError_t spectral_launch_solo(const SpecLaunch& L, bool prune, dim3 grid, size_t smem,
+                                 cudaStream_t st);
 // One launch of the paired shape over a work list: block i runs item i,
 // {group, segment, clip, scale group | scale groups << 16}, of the plan
 // records g[] (passed by value).
@@ -250,6 +259,7 @@ struct cwth_plan_s {
     int32_t M = 0, P = 0, halo = 0, kp0 = 0, seg_frames = 0, n_seg = 0;
     bool spec_prune = false;  // narrow bands let inverse FFTs skip passes
     bool inv_r8 = false;      // inverse FFTs on the radix-8 plan
+    int32_t fft_d = 1, fft_n2 = 0;  // forward FFT: fft_d column FFTs of fft_n2 points
     double seg_cost = 0;      // cost model's lane operations per segment
     int32_t seg_force = 0;    // segment length fixed by cwth_plan_segment (0: cost model)
     float2* d_tw = nullptr;

@@ -91,7 +91,9 @@ def test_plan_segment_rejects_bad_segment_lengths(cw):
     h = ctypes.c_void_p()
     w = cw.Morlet(1.5, 1.0)
     sc = (ctypes.c_double * 1)(2.0)
-    for seg in (-1, 256, 3000, 65536):
+    # 3000 = 2^3 * 375, 11264 = 2^10 * 11, 16896 = 2^9 * 33: odd parts the
+    # forward FFT does not take
+    for seg in (-1, 256, 3000, 11264, 16896, 65536):
         assert lib.cwth_plan_segment(ctypes.byref(w), sc, 1, 64, 16000.0, 100, 0, 0, seg,
                                      ctypes.byref(h)) == 1, seg
         assert not h.value

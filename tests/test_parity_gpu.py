@@ -309,7 +309,77 @@ def test_all_scales_fused(cw, sig, hop):
         assert rel_err(got[i], ref) <= TOL_FP32
 
 
-def test_unsupported_hop_for_spectral(cw):
+def test_1024_thread_shape_hop2_long_segments(cw, sig):
+    """Hop 2 with 16384-sample segments: one scale's 8192-point inverse FFT
+    does not fit beside the spectrum in the two-CTA shape's shared memory,
+    so the plan takes one 1024-thread CTA per SM.  Ragged clips over three
+    segments against the oracle."""
+    n, hop = 40000, 2
+    xs = np.stack([sig.machine_clip(501 + i, n) for i in range(2)])
+    lengths = [n, 23457]
+    sc = sig.scales_for_band(200, 8000, 24, 16000.0)
+    with cw.Plan(sc, hop=hop, max_len=n, path="spectral", seg_len=16384) as plan:
+        info = plan.info()
+        assert info["spectral_threads"] == 1024 and info["num_segments"] >= 3, info
+        out = torch.full((2, len(sc), plan.frames_max), -3.0, device="cuda")
+        plan.execute(torch.from_numpy(np.ascontiguousarray(xs, np.float32)).cuda(),
+                     lengths=torch.tensor(lengths, dtype=torch.int64, device="cuda"), out=out)
+        plan.sync()
+        got = out.cpu().numpy().astype(np.float64)
+    for i, L in enumerate(lengths):
+        F = -(-L // hop)
+        ref = oracle_mag(xs[i, :L], sc, hop)
+        assert rel_err(got[i, :, :F], ref) <= TOL_FP32, i
+        assert np.all(got[i, :, F:] == -3.0)
+
+
+@pytest.mark.parametrize("hop", [3, 5, 7, 12, 54, 96, 100, 336, 1600])
+def test_non_power_of_two_hops(cw, sig, hop):
+    """Hops with an odd factor d (3, 5, 7, 3 * 2^2, 27 * 2, 3 * 2^5, 25 * 2^2,
+    21 * 2^4, 25 * 2^6): segments of M = 2 d N2 samples, d column FFTs of
+    N2 points plus radix-3/5/7 passes, and the fold at P = M / H.  Forced
+    spectral and automatic float32 plans, ragged clips, against the oracle."""
+    n = 20000
+    xs = np.stack([sig.machine_clip(900 + i, n) for i in range(2)])
+    lengths = [n, 13001]
+    sc = sig.scales_for_band(50, 8000, 24, 16000.0)
+    refs = [oracle_mag(xs[i, :L], sc, hop) for i, L in enumerate(lengths)]
+    for path in ("spectral", "auto"):
+        got, info = run_gpu(cw, xs, sc, hop, lengths=lengths, path=path, fill=-2.0)
+        assert info["num_spectral"] == 24 and info["seg_len"] % hop == 0, info
+        d = hop
+        while d % 2 == 0:
+            d //= 2
+        assert (info["seg_len"] // 2) % d == 0 and info["fold_len"] & (info["fold_len"] - 1) == 0
+        for i, L in enumerate(lengths):
+            F = -(-L // hop)
+            assert rel_err(got[i, :, :F], refs[i]) <= TOL_FP32, (path, i)
+            assert np.all(got[i, :, F:] == -2.0)
+
+
+def test_non_power_of_two_hop_forced_segments(cw, sig):
+    """Hop 96 (d = 3): every segment length of the form 2 * 3 * 2^k the
+    plan accepts gives the oracle's scalogram; one whose odd part is not the
+    hop's is refused."""
+    n, hop = 30000, 96
+    x = sig.machine_clip(41, n)
+    sc = sig.scales_for_band(50, 8000, 16, 16000.0)
+    ref = oracle_mag(x, sc, hop)
+    xd = torch.from_numpy(np.asarray(x, np.float32)[None]).cuda()
+    for seg in (6144, 12288):
+        with cw.Plan(sc, hop=hop, max_len=n, path="spectral", seg_len=seg) as plan:
+            assert plan.info()["seg_len"] == seg
+            got = plan.execute(xd).cpu().numpy()[0].astype(np.float64)
+        assert rel_err(got, ref) <= TOL_FP32, seg
     with pytest.raises(cw.CwthError) as e:
-        cw.Plan([2.0, 5.0], hop=100, max_len=1000, path="spectral")
+        cw.Plan(sc, hop=hop, max_len=n, path="spectral", seg_len=5 * 2048)
     assert e.value.status == 4
+
+
+def test_unsupported_hop_for_spectral(cw):
+    """Hop 11 (odd part 11) and hop 2^3 * 45 (odd part 45 > 27) stay with
+    the direct path; a forced spectral plan is refused."""
+    for hop in (11, 360):
+        with pytest.raises(cw.CwthError) as e:
+            cw.Plan([2.0, 5.0], hop=hop, max_len=1000, path="spectral")
+        assert e.value.status == 4
