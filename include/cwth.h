@@ -274,6 +274,8 @@ typedef struct {
                                   that narrow Morlet bands leave trivial       */
     int32_t num_fused;         /* of num_direct: short-support scales summed in
                                   the time domain inside the spectral kernel   */
+    int64_t workspace_bytes;   /* device bytes the plan's growable workspaces
+                                  hold now (see cwth_execute, cwth_plan_reserve) */
 } cwth_plan_info;
 
 /* Fill *info.  Errors: CWTH_ERR_BAD_PLAN, CWTH_ERR_INVALID_ARG (NULL info). */
@@ -420,6 +422,124 @@ cwth_status cwth_execute_direct_noalloc(const cwth_morlet *w, const double *scal
  * first call if it has not run yet.
  */
 cwth_status cwth_noalloc_status(void *stream);
+
+/* ------------------------------------------------------------------------
+ * Continuous-batching server (no paper counterpart: the paper transforms
+ * one clip at a time).  Requests, each one clip with its own length, sample
+ * rate, scale count and hop, are queued by cwth_server_submit; every
+ * cwth_server_poll completes finished batches and launches waiting requests
+ * while a stream slot is free and the device-memory budget allows, grouping
+ * requests of the same (sample rate, scale count, hop, power-of-two length
+ * bucket) into batches of up to max_batch clips.  Plans are cached with
+ * their device tables; their bytes count against the budget and the cache
+ * evicts the least recently used idle plan when it would exceed
+ * plan_cache_bytes.  Each request's samples are uploaded straight from the
+ * caller's memory and its scalogram downloaded straight into the caller's
+ * buffer (page-locked host memory makes both asynchronous DMA transfers).
+ * Not thread-safe: one thread drives a server.
+ */
+typedef struct cwth_server_s *cwth_server_t;
+
+typedef struct {
+    double budget_bytes;      /* device bytes the server may hold: staging
+                                 of the batches in flight + cached plans   */
+    double plan_cache_bytes;  /* bound on the cached plans' device bytes   */
+    int32_t max_batch;        /* clips per batch, 1 .. 4096                */
+    int32_t slots;            /* batches in flight (one stream each), 1..64 */
+    int32_t precision;        /* CWTH_PREC_* of every plan                 */
+    int32_t path;             /* CWTH_PATH_* of every plan                 */
+    double f_lo, f_hi;        /* scale band in Hz: S centre frequencies
+                                 f_hi (f_lo/f_hi)^(s/(S-1)), s = 0..S-1, with
+                                 f_hi capped at fs/2; a_s = C fs / f_s     */
+    cwth_morlet wavelet;
+    int32_t dry_run;          /* nonzero: no device work at all; plans are
+                                 costed by cwth_server_plan_bytes and every
+                                 launched batch completes at the next poll
+                                 (tests of the admission logic)            */
+} cwth_server_config;
+
+typedef struct {
+    int64_t rid;              /* caller's id, returned in the completion   */
+    const float *x;           /* host, n float32 samples; must stay valid
+                                 until the request completes               */
+    int64_t n;                /* samples, >= 1                             */
+    double fs;                /* sample rate in Hz, > 0                    */
+    int32_t n_scales;         /* S >= 1                                    */
+    int32_t hop;              /* H >= 1                                    */
+    float *out;               /* host, [S][ceil(n / H)] float32 |W|, written
+                                 before the completion is reported         */
+} cwth_request;
+
+typedef struct {
+    int64_t rid;
+    int32_t status;           /* CWTH_OK, or the error that failed it      */
+    int32_t batch_size;       /* clips in the batch that carried it        */
+    double t_done;            /* seconds on the server's clock (since
+                                 cwth_server_create) when the poll saw it  */
+} cwth_completion;
+
+typedef struct {
+    double bytes_in_use;      /* in-flight staging + cached plans          */
+    double peak_bytes;
+    double plan_bytes;        /* cached plans' device bytes                */
+    int32_t plans;            /* cached plans                              */
+    int32_t evictions;        /* plans evicted (LRU)                       */
+    int64_t launched_batches;
+    int64_t completed;
+    int64_t rejected;         /* requests that can never fit the budget    */
+    int32_t pending;          /* queued, not yet launched                  */
+    int32_t in_flight;        /* batches on the GPU                        */
+} cwth_server_stats;
+
+/*
+ * Creates a server on the current device (streams, events; staging grows on
+ * demand).  Errors: CWTH_ERR_INVALID_ARG for a NULL pointer or a field out
+ * of range; CWTH_ERR_CUDA.
+ */
+cwth_status cwth_server_create(const cwth_server_config *cfg, cwth_server_t *out);
+
+/*
+ * Queues n requests (host work only).  Errors: CWTH_ERR_INVALID_ARG for a
+ * NULL server or request array, or a request with a NULL buffer or a field
+ * out of range (nothing is queued then).
+ */
+cwth_status cwth_server_submit(cwth_server_t s, const cwth_request *reqs, int32_t n);
+
+/*
+ * Completes the batches the GPU has finished (their requests' outputs are
+ * in place), then admits and launches waiting requests.  Writes up to
+ * max_done completions (further ones are kept for the next poll) and
+ * returns how many it wrote, or a negative cwth_status.  Requests that
+ * could never fit the budget complete with CWTH_ERR_OOM; a plan the path
+ * cannot build completes its requests with that plan's error.
+ */
+int32_t cwth_server_poll(cwth_server_t s, cwth_completion *done, int32_t max_done);
+
+cwth_status cwth_server_stats_query(cwth_server_t s, cwth_server_stats *st);
+
+/*
+ * Device bytes a plan of the server holds for (fs, S, hop, bucket length):
+ * its tables and workspaces (as cwth_plan_query reports table_bytes), the
+ * figure the budget charges for it.  In dry-run mode an estimate from the
+ * scale count and segment sizes.
+ */
+double cwth_server_plan_bytes(cwth_server_t s, double fs, int32_t n_scales, int32_t hop,
+                              int64_t bucket);
+
+/*
+ * Open-loop replay: submits request i at arrival_s[i] seconds after the
+ * call starts (host clock) and polls until every request has completed;
+ * latency_s[i] = completion time - arrival time, batch_sizes[i] the size of
+ * the batch that carried it, status[i] its completion status (any of the
+ * three may be NULL).  Requests must be sorted by arrival and have distinct
+ * rids.  Returns the wall time in seconds through *wall_s (may be NULL).
+ */
+cwth_status cwth_server_replay(cwth_server_t s, const cwth_request *reqs,
+                               const double *arrival_s, int32_t n, double *latency_s,
+                               int32_t *batch_sizes, int32_t *status, double *wall_s);
+
+/* Waits for the batches in flight, then frees plans, staging and streams. */
+cwth_status cwth_server_destroy(cwth_server_t s);
 
 #ifdef __cplusplus
 }

@@ -9,8 +9,11 @@ Two modes:
   plan is a float32 plan of the spectral kernel (with its short-support
   scales summed in the time domain), and all groups are bound into one
   cwth_batch: a device work list of (group, clip, segment) items, longest
-  first, run by ONE kernel launch (one block per item).  The autotuner picks
-  each group's FFT segment length (the cost model's, half or twice it).
+  first, run by ONE kernel launch (one block per item).  Groups whose plans
+  the work list cannot take (small hops, whose plans prune their inverse
+  FFTs, or 1024-thread segments) run as their own executes beside it.  The
+  autotuner picks each group's FFT segment length (the cost model's, half
+  or twice it).
 * "graph": each group runs as its own `cwth_execute` (any path and
   precision, e.g. the tensor-core split-bf16 path) and all groups' executes
   are captured in one CUDA graph.  Its autotuner also tries the automatic
@@ -85,6 +88,15 @@ def group_key(fs: float, n_scales: int, hop: int):
     return (float(fs), int(n_scales), int(hop))
 
 
+def _worklist_ok(plan) -> bool:
+    """Whether cwth_batch_create takes the plan: spectral-path scales only
+    (folded or fused), two CTAs per SM, no pruned inverse FFTs, no
+    re-sampling."""
+    i = plan.info()
+    return (i["num_direct"] == i["num_fused"] and not i["spectral_pruned"]
+            and i["spectral_threads"] in (0, 512) and i["resample"] == 1)
+
+
 class BatchRunner:
     """Plans, packs and runs a list of uneven clips.
 
@@ -132,9 +144,16 @@ class BatchRunner:
         self.graph = None
         self.stream = torch.cuda.Stream(self.device)
         self.batch = None
+        self.solo = list(self.groups)
         if self.mode == "worklist":
-            self.batch = cwth.Batch([(g["plan"], g["x"], g["len_d"], g["out"], g["lens"])
-                                     for g in self.groups])
+            # Groups whose plans the work list takes run in its one launch;
+            # the others (pruned inverse FFTs, 1024-thread segments, direct
+            # scales) keep their own executes beside it.
+            wl = [g for g in self.groups if _worklist_ok(g["plan"])]
+            self.solo = [g for g in self.groups if not _worklist_ok(g["plan"])]
+            if wl:
+                self.batch = cwth.Batch([(g["plan"], g["x"], g["len_d"], g["out"], g["lens"])
+                                         for g in wl])
 
     # ------------------------------------------------------------ planning
     def _plan(self, g, path, precision, seg_len=0):
@@ -165,9 +184,6 @@ class BatchRunner:
                 except cwth.CwthError:
                     continue
                 info = plan.info()
-                if self.mode == "worklist" and info["spectral_pruned"]:
-                    plan.close()
-                    continue
                 if seg == 0 and path in ("spectral", "auto") and prec == "fp32" and \
                         info["seg_len"] > 0:
                     segs = [m for m in (info["seg_len"] // 2, info["seg_len"] * 2)
@@ -200,11 +216,11 @@ class BatchRunner:
     # ------------------------------------------------------------ running
     def run(self):
         """All groups, eagerly, on the current stream: one kernel launch in
-        the work-list mode, one execute per group in the graph mode."""
+        the work-list mode (plus an execute per group the work list cannot
+        take), one execute per group in the graph mode."""
         if self.batch is not None:
             self.batch.execute()
-            return
-        for g in self.groups:
+        for g in self.solo:
             g["plan"].execute(g["x"], lengths=g["len_d"], out=g["out"])
 
     def capture(self):

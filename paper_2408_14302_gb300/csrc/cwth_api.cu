@@ -172,11 +172,10 @@ std::vector<int> spectral_fft_radices(int L, int threads) {
 }
 
 // Whether the pruned kernel (inverse FFTs skip the leading passes a narrow
-// band leaves trivial) is worth its extra register pressure: only when the
-// skipped passes would be at least a tenth of all inverse-FFT passes.
-// Measured on GB300, 64 x 10 s clips, 64 scales: hop 1 (22 % of passes
-// skipped) 12.23 -> 11.43 ms and hop 2 (15 %) 6.02 -> 5.44 ms with pruning;
-// hop 4 (6 %) 2.38 -> 2.62 ms, so it stays off there.
+// band leaves trivial, and the fold fills only the residues those FFTs
+// read) is used: whenever some pass can be skipped.  Measured on GB300,
+// 64 x 10 s clips, 64 scales: hop 4 2.86 -> 1.92 ms, hop 8 1.41 -> 1.19 ms,
+// hop 16 0.79 -> 0.71 ms against the plain kernel.
 bool spectral_prune_pays(const std::vector<SpecScale>& sc, int P, int threads) {
     const std::vector<int> rad = spectral_fft_radices(P, threads);
     int64_t skipped = 0;
@@ -185,7 +184,7 @@ bool spectral_prune_pays(const std::vector<SpecScale>& sc, int P, int threads) {
         int64_t ns = 1;
         for (size_t i = 0; i + 1 < rad.size() && w * ns * rad[i] <= P; ++i, ++skipped) ns *= rad[i];
     }
-    return 10 * skipped >= (int64_t)sc.size() * (int64_t)rad.size();
+    return skipped > 0;
 }
 
 // Whether the paired kernel's inverse FFTs take the radix-8 plan instead
@@ -1385,6 +1384,13 @@ cwth_status cwth_plan_query(cwth_plan_t p, cwth_plan_info* info) {
         info->spectral_pass_scales = nc;
         info->spectral_pruned = p->spec_prune ? 1 : 0;
     }
+    const int64_t xparts = p->x_elems ? (p->d_xlo2 ? 3 : 2) : 0;
+    info->workspace_bytes = (int64_t)(p->x_elems * xparts * sizeof(__nv_bfloat16) +
+                                      p->res_elems * sizeof(float) +
+                                      p->res_len_elems * sizeof(int64_t) +
+                                      p->stage_x_elems * sizeof(float) +
+                                      p->stage_out_elems * sizeof(float) +
+                                      p->stage_len_elems * sizeof(int64_t));
     return CWTH_OK;
 }
 
@@ -1462,7 +1468,7 @@ cwth_status cwth_batch_create(int32_t n, const cwth_plan_t* plans, const float* 
         }
         if ((p->n_sp > 0 || p->n_fd > 0) &&
             spectral_threads(p->M, p->P, fd_bytes(p)) != cwth::kSpecThreadsPair) {
-            note_error("a batched plan needs the one-CTA-per-SM shape");
+            note_error("a batched plan needs the two-CTAs-per-SM (512-thread) shape");
             return CWTH_ERR_UNSUPPORTED;
         }
     }

@@ -363,6 +363,20 @@ __device__ __forceinline__ int fft_skip(int lg, int wmax) {
     return i;
 }
 
+// log2 of the product of the radices fft_skip skips: the pruned transform
+// reads only the first L >> fft_skip_lg entries of each input.
+template <int PLAN>
+__device__ __forceinline__ int fft_skip_lg(int lg, int wmax) {
+    const int np = ct_npass(PLAN, lg);
+    int i = 0, ns = 1, l = 0;
+    while (i + 1 < np && (int64_t)wmax * ns * ct_radix(PLAN, lg, i) <= (1 << lg)) {
+        const int r = ct_radix(PLAN, lg, i++);
+        ns *= r;
+        l += r == 16 ? 4 : (r == 8 ? 3 : (r == 4 ? 2 : 1));
+    }
+    return l;
+}
+
 // The forward FFT's power-of-two part: nbatch transforms of L = 2^8 ..
 // 2^13 points back to back (nbatch * L <= kMaxFftPoints), the pass
 // sequence unrolled at compile time for each length.
@@ -864,15 +878,65 @@ __device__ __forceinline__ void fd_run(const SpecLaunch& p, const FdWork& w, int
 // P < 32), one lane each; the loop walks the unwrapped band.  Items are
 // ordered by decreasing band width (scales ascend); they are dealt to warps
 // in a snake order to balance the work.
+//
+// SHIFT (the pruned kernel): each band is stored shifted to residue 0 and
+// the inverse FFT reads only the first 2^lgneed residues of each scale
+// (the rest of a skipped pass's input is zero), so only those are folded,
+// one scale per lane: item g = c 2^lgneed + r' folds residue r' + q_lo.
 template <int LGP, bool SHIFT, bool MODM = false>
 __device__ __forceinline__ void fold_items(const SpecLaunch& p, const float2* __restrict__ X,
                                            float2* __restrict__ Z, int c0, int nc, int M, int P,
-                                           int lgP) {
+                                           int lgP, int lgneed = 0) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nwarps = blockDim.x >> 5;
+    const float cneg = -p.center;
+    if constexpr (SHIFT) {
+        const int nitems = ((nc << lgneed) + 31) >> 5;
+        for (int round = 0;; ++round) {
+            const int it = round * nwarps + ((round & 1) ? nwarps - 1 - warp : warp);
+            if (it >= nitems) break;
+            const int g = (it << 5) + lane;
+            const int c = g >> lgneed;
+            if (c >= nc) continue;
+            const int rs = g & ((1 << lgneed) - 1);
+            const SpecScale sc = p.sc[c0 + c];
+            if (sc.q_hi - sc.q_lo + 1 > 2 * P) {
+                // Bands of several bins per residue: the recurrence walk.
+                float2 z;
+                fold_residue<LGP, 1, MODM>(X, &sc, (rs + sc.q_lo) & (P - 1), M, M >> 1, P, lgP,
+                                           cneg, p.kexp, &z);
+                Z[c * P + rs] = z;
+                continue;
+            }
+            // One or two bins per residue: a plain walk with an exact weight
+            // per bin.
+            float2 acc = make_float2(0.f, 0.f);
+            for (int qu = sc.q_lo + rs; qu <= sc.q_hi; qu += P) {
+                int q;
+                if (MODM) {
+                    q = qu % M;
+                    q += q < 0 ? M : 0;
+                } else {
+                    q = qu & (M - 1);
+                }
+                float2 v;
+                if (q <= (M >> 1)) {
+                    v = X[q];
+                } else {
+                    v = X[M - q];
+                    v.y = -v.y;
+                }
+                const float u = fmaf((float)qu, sc.a_over_m, cneg);
+                const float g = fast_exp2(p.kexp * u * u);
+                acc.x = fmaf(v.x, g, acc.x);
+                acc.y = fmaf(v.y, g, acc.y);
+            }
+            Z[c * P + rs] = make_float2(sc.gscale * acc.x, sc.gscale * acc.y);
+        }
+        return;
+    }
     const int npairs = (nc + 1) >> 1;
     const int nitems = (npairs * P + 31) >> 5;
-    const float cneg = -p.center;
     for (int round = 0;; ++round) {
         const int it = round * nwarps + ((round & 1) ? nwarps - 1 - warp : warp);
         if (it >= nitems) break;
@@ -883,9 +947,6 @@ __device__ __forceinline__ void fold_items(const SpecLaunch& p, const float2* __
         SpecScale sc[2];
         sc[0] = p.sc[c0 + c];
         float2 z[2];
-        // SHIFT: each band stored shifted by its first residue (a
-        // unit-modulus phase on the inverse transform, so |W| is unchanged);
-        // it then occupies residues [0, min(P, q_hi - q_lo + 1)).
         if (c + 1 < nc) {
             sc[1] = p.sc[c0 + c + 1];
             if (sc[0].pair) {
@@ -894,11 +955,11 @@ __device__ __forceinline__ void fold_items(const SpecLaunch& p, const float2* __
                 fold_residue<LGP, 1, MODM>(X, sc, r, M, M >> 1, P, lgP, cneg, p.kexp, z);
                 fold_residue<LGP, 1, MODM>(X, sc + 1, r, M, M >> 1, P, lgP, cneg, p.kexp, z + 1);
             }
-            Z[(c + 1) * P + (SHIFT ? ((r - sc[1].q_lo) & (P - 1)) : r)] = z[1];
+            Z[(c + 1) * P + r] = z[1];
         } else {
             fold_residue<LGP, 1, MODM>(X, sc, r, M, M >> 1, P, lgP, cneg, p.kexp, z);
         }
-        Z[c * P + (SHIFT ? ((r - sc[0].q_lo) & (P - 1)) : r)] = z[0];
+        Z[c * P + r] = z[0];
     }
 }
 
@@ -1105,28 +1166,38 @@ __device__ __forceinline__ void spectral_body(const SpecLaunch& p, int seg, int 
 
     const int P = p.P;
     float2* Z = smem + ntw + Mh + 2;
-    int64_t len, F, k0;
-    cta_pos(p, true, seg, clip, &len, &F, &k0);
-    const int sp_begin = grp * p.group_size;
-    const int sp_end = min(p.n_sp, sp_begin + p.group_size);
+    // The CTA's position lives in shared memory through the chunk loop and
+    // is read back (volatile) where it is needed, so that nothing but the
+    // chunk index holds a register through the inverse FFT's passes.
+    __shared__ int s_pos[3];
+    if (threadIdx.x == 0) {
+        s_pos[0] = seg;
+        s_pos[1] = clip;
+        s_pos[2] = grp;
+    }
+    __syncthreads();
+    const volatile int* vpos = s_pos;
     const int lgP = __ffs(P) - 1;
-    for (int c0 = sp_begin; c0 < sp_end; c0 += p.nconc) {
+    for (int c0 = vpos[2] * p.group_size;; c0 += p.nconc) {
+        const int sp_end = min(p.n_sp, vpos[2] * p.group_size + p.group_size);
+        if (c0 >= sp_end) break;
         const int nc = min(p.nconc, sp_end - c0);
 
         // a3: the band walks of 8 or more bins per residue occur for P up to
         // M/16; those periods get a compile-time stride.  A segment length
         // with an odd factor takes the run-time stride and reduces bins
         // modulo M by division.
-        if (p.fft_d > 1) fold_items<0, PRUNE, true>(p, X, Z, c0, nc, M, P, lgP);
+        const int lgneed = PRUNE ? lgP - fft_skip_lg<kPPT>(lgP, p.sc[c0].wsuf) : lgP;
+        if (p.fft_d > 1) fold_items<0, PRUNE, true>(p, X, Z, c0, nc, M, P, lgP, lgneed);
         else switch (lgP) {
-            case 4: fold_items<4, PRUNE>(p, X, Z, c0, nc, M, P, lgP); break;
-            case 5: fold_items<5, PRUNE>(p, X, Z, c0, nc, M, P, lgP); break;
-            case 6: fold_items<6, PRUNE>(p, X, Z, c0, nc, M, P, lgP); break;
-            case 7: fold_items<7, PRUNE>(p, X, Z, c0, nc, M, P, lgP); break;
-            case 8: fold_items<8, PRUNE>(p, X, Z, c0, nc, M, P, lgP); break;
-            case 9: fold_items<9, PRUNE>(p, X, Z, c0, nc, M, P, lgP); break;
-            case 10: fold_items<10, PRUNE>(p, X, Z, c0, nc, M, P, lgP); break;
-            default: fold_items<0, PRUNE>(p, X, Z, c0, nc, M, P, lgP); break;
+            case 4: fold_items<4, PRUNE>(p, X, Z, c0, nc, M, P, lgP, lgneed); break;
+            case 5: fold_items<5, PRUNE>(p, X, Z, c0, nc, M, P, lgP, lgneed); break;
+            case 6: fold_items<6, PRUNE>(p, X, Z, c0, nc, M, P, lgP, lgneed); break;
+            case 7: fold_items<7, PRUNE>(p, X, Z, c0, nc, M, P, lgP, lgneed); break;
+            case 8: fold_items<8, PRUNE>(p, X, Z, c0, nc, M, P, lgP, lgneed); break;
+            case 9: fold_items<9, PRUNE>(p, X, Z, c0, nc, M, P, lgP, lgneed); break;
+            case 10: fold_items<10, PRUNE>(p, X, Z, c0, nc, M, P, lgP, lgneed); break;
+            default: fold_items<0, PRUNE>(p, X, Z, c0, nc, M, P, lgP, lgneed); break;
         }
         __syncthreads();
 
@@ -1145,6 +1216,10 @@ __device__ __forceinline__ void spectral_body(const SpecLaunch& p, int seg, int 
         // items of 32 consecutive frames of one row; the row is read once
         // per row or item, stores are coalesced and reads conflict-free.
         {
+            const int clip = vpos[1];
+            const int nc = min(p.nconc, min(p.n_sp, vpos[2] * p.group_size + p.group_size) - c0);
+            int64_t len, F, k0;
+            cta_pos(p, true, vpos[0], clip, &len, &F, &k0);
             const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
             const int nwarps = blockDim.x >> 5;
             const int Fs = p.seg_frames;
@@ -1161,14 +1236,17 @@ __device__ __forceinline__ void spectral_body(const SpecLaunch& p, int seg, int 
                     }
                 }
             } else {
-                const int nch = (fend + 31) >> 5;
-                for (int it = warp; it < nc * nch; it += nwarps) {
-                    const int c = it / nch;
-                    const int f = (it - c * nch) * 32 + lane;
-                    if (f < fend) {
-                        const float2 w = Z[c * P + p.kp0 + f];
-                        p.out[((int64_t)clip * p.S_total + p.sc[c0 + c].row) * p.frames_max + k0 +
-                              f] = fast_sqrt(fmaf(w.x, w.x, w.y * w.y));
+                // Fewer rows than warps (small hops, long rows): the whole
+                // CTA strides over one row's frames at a time, independent
+                // iterations, so loads and stores overlap.
+                for (int c = 0; c < nc; ++c) {
+                    float* o = p.out +
+                               ((int64_t)clip * p.S_total + p.sc[c0 + c].row) * p.frames_max + k0;
+                    const float2* z = Z + c * P + p.kp0;
+#pragma unroll 4
+                    for (int f = threadIdx.x; f < fend; f += blockDim.x) {
+                        const float2 w = z[f];
+                        o[f] = fast_sqrt(fmaf(w.x, w.x, w.y * w.y));
                     }
                 }
             }

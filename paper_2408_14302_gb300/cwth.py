@@ -28,7 +28,9 @@ EXPORTS = ("cwth_plan", "cwth_execute", "cwth_execute_host", "cwth_destroy",
            "cwth_selftest_wait_timeout", "cwth_measure_fp32_fma", "cwth_plan_resampled",
            "cwth_plan_segment", "cwth_noalloc_status", "cwth_batch_create",
            "cwth_batch_execute", "cwth_batch_items", "cwth_batch_destroy",
-           "cwth_plan_reserve")
+           "cwth_plan_reserve", "cwth_server_create", "cwth_server_submit", "cwth_server_poll",
+           "cwth_server_stats_query", "cwth_server_plan_bytes", "cwth_server_replay",
+           "cwth_server_destroy")
 
 
 class CwthError(RuntimeError):
@@ -43,6 +45,36 @@ class Morlet(ctypes.Structure):
     _fields_ = [("bandwidth", ctypes.c_double), ("center_freq", ctypes.c_double)]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_double), ("plan_cache_bytes", ctypes.c_double),
+                ("max_batch", ctypes.c_int32), ("slots", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("path", ctypes.c_int32),
+                ("f_lo", ctypes.c_double), ("f_hi", ctypes.c_double), ("wavelet", Morlet),
+                ("dry_run", ctypes.c_int32)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("rid", ctypes.c_int64), ("x", ctypes.c_void_p), ("n", ctypes.c_int64),
+                ("fs", ctypes.c_double), ("n_scales", ctypes.c_int32), ("hop", ctypes.c_int32),
+                ("out", ctypes.c_void_p)]
+
+
+class Completion(ctypes.Structure):
+    _fields_ = [("rid", ctypes.c_int64), ("status", ctypes.c_int32),
+                ("batch_size", ctypes.c_int32), ("t_done", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("bytes_in_use", ctypes.c_double), ("peak_bytes", ctypes.c_double),
+                ("plan_bytes", ctypes.c_double), ("plans", ctypes.c_int32),
+                ("evictions", ctypes.c_int32), ("launched_batches", ctypes.c_int64),
+                ("completed", ctypes.c_int64), ("rejected", ctypes.c_int64),
+                ("pending", ctypes.c_int32), ("in_flight", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class PlanInfo(ctypes.Structure):
     _fields_ = [("num_scales", ctypes.c_int32), ("hop", ctypes.c_int32),
                 ("max_len", ctypes.c_int64), ("frames_max", ctypes.c_int64),
@@ -53,7 +85,7 @@ class PlanInfo(ctypes.Structure):
                 ("table_bytes", ctypes.c_int64), ("sample_rate", ctypes.c_double),
                 ("resample", ctypes.c_int32), ("spectral_threads", ctypes.c_int32),
                 ("spectral_pass_scales", ctypes.c_int32), ("spectral_pruned", ctypes.c_int32),
-                ("num_fused", ctypes.c_int32)]
+                ("num_fused", ctypes.c_int32), ("workspace_bytes", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -114,6 +146,24 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.cwth_batch_items.restype = i64
     lib.cwth_batch_destroy.argtypes = [vp]
     lib.cwth_batch_destroy.restype = ctypes.c_int
+    lib.cwth_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]
+    lib.cwth_server_create.restype = ctypes.c_int
+    lib.cwth_server_submit.argtypes = [vp, ctypes.POINTER(Request), i32]
+    lib.cwth_server_submit.restype = ctypes.c_int
+    lib.cwth_server_poll.argtypes = [vp, ctypes.POINTER(Completion), i32]
+    lib.cwth_server_poll.restype = ctypes.c_int32
+    lib.cwth_server_stats_query.argtypes = [vp, ctypes.POINTER(ServerStats)]
+    lib.cwth_server_stats_query.restype = ctypes.c_int
+    lib.cwth_server_plan_bytes.argtypes = [vp, dp, i32, i32, i64]
+    lib.cwth_server_plan_bytes.restype = ctypes.c_double
+    lib.cwth_server_replay.argtypes = [vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_double),
+                                       i32, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_int32),
+                                       ctypes.POINTER(ctypes.c_int32),
+                                       ctypes.POINTER(ctypes.c_double)]
+    lib.cwth_server_replay.restype = ctypes.c_int
+    lib.cwth_server_destroy.argtypes = [vp]
+    lib.cwth_server_destroy.restype = ctypes.c_int
     return lib
 
 
@@ -380,3 +430,71 @@ class Batch:
         except Exception:
             pass
 
+
+
+class Server:
+    """The library's continuous-batching server (cwth_server_*): admission
+    under a device-memory budget that includes cached plans, LRU plan cache,
+    batches of one (rate, scales, hop, length bucket) key, per-slot streams,
+    uploads from and downloads into the callers' buffers.  Requests are
+    ``Request`` structs whose ``x`` / ``out`` point at host memory that stays
+    valid until they complete (page-locked memory makes the copies DMA)."""
+
+    def __init__(self, budget_bytes=40 << 30, plan_cache_bytes=4 << 30, max_batch=16, slots=4,
+                 precision="fp32", path="auto", f_lo=50.0, f_hi=8000.0, bandwidth=1.5,
+                 center=1.0, dry_run=False):
+        cfg = ServerConfig(float(budget_bytes), float(plan_cache_bytes), int(max_batch), int(slots),
+                           PREC[precision], PATH[path], float(f_lo), float(f_hi),
+                           Morlet(float(bandwidth), float(center)), 1 if dry_run else 0)
+        self._h = ctypes.c_void_p()
+        _check(_lib.cwth_server_create(ctypes.byref(cfg), ctypes.byref(self._h)),
+               "cwth_server_create")
+        self._done = (Completion * 4096)()
+
+    def submit(self, reqs):
+        arr = reqs if isinstance(reqs, ctypes.Array) else (Request * len(reqs))(*reqs)
+        _check(_lib.cwth_server_submit(self._h, arr, len(arr)), "cwth_server_submit")
+
+    def poll(self):
+        """[(rid, status, batch_size, t_done)] of the requests completed now."""
+        k = _lib.cwth_server_poll(self._h, self._done, len(self._done))
+        if k < 0:
+            _check(-k, "cwth_server_poll")
+        return [(c.rid, c.status, c.batch_size, c.t_done) for c in self._done[:k]]
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(_lib.cwth_server_stats_query(self._h, ctypes.byref(st)), "cwth_server_stats_query")
+        return st.as_dict()
+
+    def plan_bytes(self, fs, n_scales, hop, bucket) -> float:
+        return _lib.cwth_server_plan_bytes(self._h, float(fs), int(n_scales), int(hop), int(bucket))
+
+    def replay(self, reqs, arrival_s):
+        """Open-loop replay (cwth_server_replay): returns (latency_s, batch
+        sizes, statuses, wall seconds)."""
+        import numpy as np
+        arr = reqs if isinstance(reqs, ctypes.Array) else (Request * len(reqs))(*reqs)
+        t = np.ascontiguousarray(arrival_s, dtype=np.float64)
+        lat = np.zeros(len(arr), np.float64)
+        bs = np.zeros(len(arr), np.int32)
+        stat = np.zeros(len(arr), np.int32)
+        wall = ctypes.c_double()
+        dptr = ctypes.POINTER(ctypes.c_double)
+        _check(_lib.cwth_server_replay(self._h, arr, t.ctypes.data_as(dptr), len(arr),
+                                       lat.ctypes.data_as(dptr),
+                                       bs.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                       stat.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                       ctypes.byref(wall)), "cwth_server_replay")
+        return lat, bs, stat, wall.value
+
+    def close(self):
+        if self._h:
+            _check(_lib.cwth_server_destroy(self._h), "cwth_server_destroy")
+            self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -37,6 +37,8 @@ class Request:
     hop: int
     fs: float = 16000.0
     arrival: float = 0.0   # seconds after the start of the run
+    src: int = -1          # pool signal the clip was cut from (-1: none)
+    start: int = 0         # first sample of the clip in that signal
 
     @property
     def key(self):
@@ -304,10 +306,12 @@ def poisson_requests(n: int, rate: float, seed: int = 5000, pool=None, pool_seco
         t += rng.exponential(1.0 / rate)
         secs = math.exp(rng.uniform(math.log(min_s), math.log(max_s)))
         L = max(1, int(round(secs * fs)))
-        src = pool[int(rng.integers(len(pool)))]
+        k = int(rng.integers(len(pool)))
+        src = pool[k]
         start = int(rng.integers(0, max(1, len(src) - L)))
         x = np.ascontiguousarray(src[start:start + L], np.float32)
-        out.append(Request(i, x, int(rng.choice(scale_counts)), int(rng.choice(hops)), fs, t))
+        out.append(Request(i, x, int(rng.choice(scale_counts)), int(rng.choice(hops)), fs, t,
+                           k, start))
     return out
 
 
@@ -318,8 +322,50 @@ def summarize(results, wall):
             "completed": len(results), "wall_s": wall}
 
 
+def library_replay(reqs, pinned_pool, out_ring, budget_bytes=40 * GiB, plan_cache_bytes=4 * GiB,
+                   max_batch=16, slots=4, precision="fp32", path="auto", dry_run=False):
+    """Replays `reqs` through the library's server (cwth_server_replay: the
+    admission loop, batching, copies and launches all in C).  Each request's
+    samples are read in place from `pinned_pool` (a page-locked torch tensor
+    [signals, samples] holding the pool the clips were cut from) and its
+    scalogram written into `out_ring` (a page-locked float32 tensor used as
+    a ring: outputs of long-finished requests are overwritten).  Returns
+    (summary dict, latencies in s, batch sizes).  dry_run: the server's
+    dry-run mode (no device work; any CPU tensors will do)."""
+    from . import cwth
+    n = len(reqs)
+    arr = (cwth.Request * n)()
+    base = pinned_pool.data_ptr()
+    row = pinned_pool.shape[1]
+    ring = out_ring.data_ptr()
+    cap = out_ring.numel()
+    off = 0
+    for i, q in enumerate(reqs):
+        if q.src < 0:
+            raise ValueError("library_replay needs requests cut from the pool (src >= 0)")
+        m = q.n_scales * q.frames
+        if off + m > cap:
+            off = 0
+        arr[i] = cwth.Request(q.rid, base + 4 * (q.src * row + q.start), len(q.x), q.fs,
+                              q.n_scales, q.hop, ring + 4 * off)
+        off += m
+    with cwth.Server(budget_bytes=budget_bytes, plan_cache_bytes=plan_cache_bytes,
+                     max_batch=max_batch, slots=slots, precision=precision, path=path,
+                     dry_run=dry_run) as srv:
+        lat, bs, stat, wall = srv.replay(arr, np.array([q.arrival for q in reqs]))
+        st = srv.stats()
+    if np.any(stat != 0):
+        raise RuntimeError(f"{int(np.sum(stat != 0))} requests failed: {sorted(set(stat.tolist()))}")
+    lat_ms = lat * 1e3
+    return ({"p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
+             "mean_batch": float(np.mean(bs)), "completed": int(st["completed"]), "wall_s": wall,
+             "peak_gb": st["peak_bytes"] / GiB, "plans": st["plans"],
+             "evictions": st["evictions"], "rejected": int(st["rejected"])}, lat, bs)
+
+
 def main(argv=None):
-    """Sweep arrival rates for the batched and the per-clip float32 forms:
+    """Sweep arrival rates through the library's server (default) or the
+    Python scheduler:
     python -m paper_2408_14302_gb300.serving --rates 50,200,1000,2000 --requests 400"""
     import argparse
     import json
@@ -327,18 +373,42 @@ def main(argv=None):
     ap.add_argument("--rates", default="50,100,200,500,1000,2000")
     ap.add_argument("--requests", type=int, default=400)
     ap.add_argument("--budget-gb", type=float, default=40.0)
+    ap.add_argument("--plan-cache-gb", type=float, default=4.0)
     ap.add_argument("--max-batch", type=int, default=16)
     ap.add_argument("--slots", type=int, default=4)
-    ap.add_argument("--forms", default="batched_spectral_fp32,batched_auto_bf16x3,"
+    ap.add_argument("--engine", default="library", choices=["library", "python"])
+    ap.add_argument("--forms", default="batched_auto_fp32,batched_auto_bf16x3,"
                     "per_clip_fp32_spectral")
     a = ap.parse_args(argv)
     import torch
     pool = [signals.machine_clip(5000 + i, 60 * 16000, 16000.0) for i in range(8)]
-    forms = {"batched_spectral_fp32": dict(precision="fp32", path="spectral", batched=True),
+    forms = {"batched_auto_fp32": dict(precision="fp32", path="auto", batched=True),
+             "batched_spectral_fp32": dict(precision="fp32", path="spectral", batched=True),
              "batched_auto_bf16x3": dict(precision="bf16x3", path="auto", batched=True),
              "per_clip_fp32_spectral": dict(precision="fp32", path="spectral", batched=False)}
     forms = {k: forms[k] for k in a.forms.split(",")}
+    if a.engine == "library":
+        pinned = torch.from_numpy(np.stack(pool).astype(np.float32)).pin_memory()
+        ring = torch.empty(1 << 29, dtype=torch.float32).pin_memory()   # 2 GiB of outputs
     for name, f in forms.items():
+        mb = a.max_batch if f["batched"] else 1
+        if a.engine == "library":
+            # warm: plans of the mix and the kernels, one pass of back-to-back requests
+            warm = poisson_requests(min(400, a.requests), 1e6, seed=4000, pool=pool)
+            library_replay(warm, pinned, ring, int(a.budget_gb * GiB),
+                           int(a.plan_cache_gb * GiB), mb, a.slots, f["precision"], f["path"])
+            for rate in [float(r) for r in a.rates.split(",")]:
+                reqs = poisson_requests(a.requests, rate, seed=5000 + int(rate), pool=pool)
+                torch.cuda.synchronize()
+                s, _, _ = library_replay(reqs, pinned, ring, int(a.budget_gb * GiB),
+                                         int(a.plan_cache_gb * GiB), mb, a.slots,
+                                         f["precision"], f["path"])
+                audio = sum(r.audio_seconds for r in reqs)
+                s.update({"engine": "library", "form": name, "rate_req_s": rate,
+                          "audio_sec_per_s": audio / s["wall_s"],
+                          "offered_audio_sec_per_s": audio / reqs[-1].arrival})
+                print(json.dumps(s), flush=True)
+            continue
         ex = GpuExecutor(slots=a.slots, precision=f["precision"], path=f["path"])
         ex.warm([16000.0], (32, 64, 128, 256), (32, 64, 128, 256, 512),
                 [0.5 * 16000, 60 * 16000] + [2 ** k for k in range(14, 21)])
@@ -354,7 +424,8 @@ def main(argv=None):
             res, wall = srv.run(reqs)
             s = summarize(res, wall)
             audio = sum(r.audio_seconds for r in reqs)
-            s.update({"form": name, "rate_req_s": rate, "audio_sec_per_s": audio / wall,
+            s.update({"engine": "python", "form": name, "rate_req_s": rate,
+                      "audio_sec_per_s": audio / wall,
                       "offered_audio_sec_per_s": audio / reqs[-1].arrival,
                       "peak_gb": srv.peak_bytes / GiB, "rejected": len(srv.rejected)})
             print(json.dumps(s), flush=True)

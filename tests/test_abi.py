@@ -134,3 +134,31 @@ def test_noalloc_wrapper_checks_arguments_before_the_library(cw):
         cw.execute_direct_noalloc([2.0, 4.0, 8.0], 64, x, out)          # host memory
     with pytest.raises(ValueError):
         cw.execute_direct_noalloc([2.0, 4.0, 8.0], 64, x.double(), out)  # float64
+
+
+def test_plan_wrappers_marshal_their_arguments(cw, monkeypatch):
+    """The binding's plan methods that need no tensor pass their arguments
+    through unchanged (checked against a stand-in library, no device)."""
+    calls = []
+
+    class Fake:
+        def __getattr__(self, name):
+            def f(*a):
+                calls.append((name, a))
+                return 0
+            return f
+
+    monkeypatch.setattr(cw, "_lib", Fake())
+    p = object.__new__(cw.Plan)
+    p._h = ctypes.c_void_p(12345)
+    try:
+        p.reserve(8, ld_x=100, host=True)
+        p.reserve(3)
+        p.set_host_chunks(2)
+        p.close()
+    finally:
+        p._h = ctypes.c_void_p()
+    assert [c[0] for c in calls] == ["cwth_plan_reserve", "cwth_plan_reserve",
+                                     "cwth_plan_set_host_chunks", "cwth_destroy"]
+    assert calls[0][1][1:] == (8, 100, 1) and calls[1][1][1:] == (3, 0, 0)
+    assert calls[2][1][1:] == (2,)

@@ -64,3 +64,21 @@ def test_per_clip_form_runs_one_request_per_batch():
     ex = serving.MockExecutor()
     serving.Server(ex, 1 << 40, max_batch=16, max_inflight=2, batched=False).run(reqs)
     assert all(len(h["reqs"]) == 1 for h in ex.launched)
+
+
+def test_library_replay_marshals_pool_and_ring():
+    """serving.library_replay points each request into the sample pool and
+    the output ring and replays them through the library's server (its
+    dry-run mode: no device work)."""
+    torch = __import__("pytest").importorskip("torch")
+    pool = [np.arange(30000, dtype=np.float32) + 1e5 * k for k in range(3)]
+    reqs = serving.poisson_requests(50, 1e5, seed=9, pool=pool, min_s=0.01, max_s=1.0,
+                                    scale_counts=(4, 8), hops=(64, 128))
+    pooled = torch.from_numpy(np.stack(pool))
+    ring = torch.zeros(1 << 16)
+    s, lat, bs = serving.library_replay(reqs, pooled, ring, max_batch=4, slots=2, dry_run=True)
+    assert s["completed"] == 50 and s["rejected"] == 0 and s["mean_batch"] >= 1
+    assert np.all(lat >= 0)
+    # requests carry where they were cut from
+    for q in reqs:
+        assert np.array_equal(pool[q.src][q.start:q.start + len(q.x)], q.x)
