@@ -31,8 +31,9 @@ constexpr double kEpsBand = 1e-7;
 // the whole budget is available.
 constexpr size_t kSmemCap = 227 * 1024 - 1024;
 // Dynamic shared memory per spectral CTA that still lets two CTAs share an
-// SM (228 KB per SM, 1 KB reserved per CTA).
-constexpr size_t kSmemPair = 113 * 1024;
+// SM (228 KB per SM, 1 KB reserved per CTA), less 256 bytes for the
+// kernel's static shared variables.
+constexpr size_t kSmemPair = 113 * 1024 - 256;
 // Cost of one pass over a group of scales (fold + inverse FFT + stores, each
 // ending at a CTA barrier) in the model's lane-operation units (~3k cycles
 // measured on GB300).
@@ -265,7 +266,8 @@ bool choose_segment(const cwth_plan_s& p, const std::vector<double>& sp_scales,
     const int hop = p.hop;
     int fd_taps = 0, fd_hw = 0;
     double fd_rows = 0;
-    if (!fd_h.empty()) fd_make_groups(fd_h, &fd_taps, &fd_hw, &fd_rows);
+    int fd_ngroups = 0;
+    if (!fd_h.empty()) fd_ngroups = (int)fd_make_groups(fd_h, &fd_taps, &fd_hw, &fd_rows).size();
     const int64_t h = std::max<int64_t>(
         sp_scales.empty() ? 0 : (int64_t)ceil(a_max * sqrt(p.B * log(1.0 / kEpsWrap))), fd_hw);
     const int64_t halo = ((h + hop - 1) / hop) * hop;
@@ -285,7 +287,7 @@ bool choose_segment(const cwth_plan_s& p, const std::vector<double>& sp_scales,
         const int64_t Fseg = last - kp0 + 1;
         if (Fseg < 1) continue;
         const int fst = (int)(Fseg | 1);
-        const size_t fdb = cwth::spectral_fd_bytes(fd_taps, fd_hw, fst);
+        const size_t fdb = cwth::spectral_fd_bytes(fd_taps, fd_hw, fst, fd_ngroups);
         if (cwth::spectral_smem_bytes((int)M, (int)P, 1, fdb) > kSmemCap) continue;
         const int threads = spectral_threads((int)M, (int)P, fdb);
         if (M / 2 > cwth::kMaxFftPoints || P > cwth::kMaxFftPoints) continue;
@@ -512,7 +514,9 @@ bool encode_bf16_2d(CUtensorMap* map, const void* base, uint64_t inner, uint64_t
 
 // Shared-memory bytes of a plan's fused time-domain phase (0 without one).
 size_t fd_bytes(const cwth_plan_s* p) {
-    return p->n_fd > 0 ? cwth::spectral_fd_bytes(p->fd_taps_n, p->fd_hw, p->fd_fst) : 0;
+    return p->n_fd > 0 ? cwth::spectral_fd_bytes(p->fd_taps_n, p->fd_hw, p->fd_fst,
+                                                  (int)p->fd_groups.size())
+                       : 0;
 }
 
 cwth_status build_direct(cwth_plan_s* p) {

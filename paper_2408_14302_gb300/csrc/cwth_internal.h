@@ -168,9 +168,10 @@ cwth_status noalloc_status_word(int** word);
 
 size_t spectral_smem_bytes(int M, int P, int nconc, size_t fd_bytes = 0);
 // Shared-memory bytes of the fused time-domain scales, held in the fold's
-// buffer before the fold: their tap tables (taps_n complex) and frame
-// windows ((2 hw + 1) rows of fst floats, plus slack).
-size_t spectral_fd_bytes(int taps_n, int hw, int fst);
+// buffer before the fold: their tap tables (taps_n complex), the n_groups
+// group records and the frame windows ((2 hw + 1) rows of fst floats, plus
+// slack).
+size_t spectral_fd_bytes(int taps_n, int hw, int fst, int n_groups);
 cudaError_t spectral_make_fd_taps(const double* d_scales, const int32_t* d_h, const int32_t* d_gidx,
                                   const FdGroup* d_grp, int n_groups, int taps_n, double B,
                                   double C, float2* d_taps, cudaStream_t st);

@@ -59,7 +59,47 @@ struct CachedPlan {
 struct Pending {
     cwth_request r;
     int64_t bucket;
+    // device addresses of r.x and r.out when both are page-locked (mapped
+    // into the device's address space), else null
+    const float* dx;
+    float* dout;
 };
+
+// One request of a batch as its gather / scatter kernels see it.
+struct IoEntry {
+    const float* x;  // device address of the request's samples (host memory)
+    float* out;      // device address of its [S][F] output (host memory)
+    int64_t n;
+    int64_t F;
+};
+
+// Copies request i's samples from page-locked host memory into row i of
+// the batch (and its length), reading them over the host link in place.
+__global__ void serve_gather(const IoEntry* __restrict__ tab, float* __restrict__ d_x, int64_t L,
+                             int64_t* __restrict__ d_len) {
+    const int i = blockIdx.y;
+    const IoEntry e = tab[i];
+    if (blockIdx.x == 0 && threadIdx.x == 0) d_len[i] = e.n;
+    float* row = d_x + (int64_t)i * L;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < e.n;
+         t += (int64_t)gridDim.x * blockDim.x)
+        row[t] = e.x[t];
+}
+
+// Writes request i's valid frames, [S][F_i] of the batch's [S][F] rows,
+// straight into its page-locked host buffer.
+__global__ void serve_scatter(const IoEntry* __restrict__ tab, const float* __restrict__ d_out,
+                              int S, int64_t F) {
+    const int i = blockIdx.y;
+    const IoEntry e = tab[i];
+    const int64_t total = (int64_t)S * e.F;
+    const float* src = d_out + (int64_t)i * S * F;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = t / e.F;
+        e.out[t] = src[s * F + (t - s * e.F)];
+    }
+}
 
 struct Slot {
     cudaStream_t st = nullptr;
@@ -72,9 +112,13 @@ struct Slot {
     size_t out_cap = 0;
     int64_t* h_len = nullptr;  // page-locked
     size_t hlen_cap = 0;
+    IoEntry* h_tab = nullptr;  // page-locked, read by the gather / scatter kernels
+    IoEntry* d_tab = nullptr;  // its device address
+    size_t tab_cap = 0;
     bool busy = false;
     int32_t status = CWTH_OK;
     std::vector<cwth_request> reqs;
+    std::vector<Pending> io;
     Key plan_key{};
     double bytes = 0;
 };
@@ -223,12 +267,14 @@ struct cwth_server_s {
         }
     }
 
-    cwth_status launch(Slot& sl, CachedPlan* cp, const Key& key, std::vector<cwth_request>& reqs,
+    cwth_status launch(Slot& sl, CachedPlan* cp, const Key& key, std::vector<Pending>& sel,
                        double bytes) {
-        const int32_t b = (int32_t)reqs.size();
+        const int32_t b = (int32_t)sel.size();
         const int64_t L = key.bucket;
         const int64_t F = (L + key.hop - 1) / key.hop;
-        sl.reqs.swap(reqs);
+        sl.io.swap(sel);
+        sl.reqs.clear();
+        for (const Pending& q : sl.io) sl.reqs.push_back(q.r);
         sl.plan_key = key;
         sl.bytes = bytes;
         sl.status = CWTH_OK;
@@ -247,6 +293,45 @@ struct cwth_server_s {
             sl.hlen_cap = 0;
             e = cudaMallocHost(&sl.h_len, sizeof(int64_t) * (size_t)cfg.max_batch);
             if (e == cudaSuccess) sl.hlen_cap = (size_t)cfg.max_batch;
+        }
+        if (e == cudaSuccess && sl.tab_cap < (size_t)b) {
+            cudaFreeHost(sl.h_tab);
+            sl.h_tab = nullptr;
+            sl.d_tab = nullptr;
+            sl.tab_cap = 0;
+            e = cudaMallocHost(&sl.h_tab, sizeof(IoEntry) * (size_t)cfg.max_batch);
+            if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&sl.d_tab, sl.h_tab, 0);
+            if (e == cudaSuccess) sl.tab_cap = (size_t)cfg.max_batch;
+        }
+        // Page-locked requests: one gather and one scatter kernel move the
+        // whole batch (no per-request copy call); others take one copy each
+        // way per request.
+        bool mapped = true;
+        for (const Pending& q : sl.io) mapped = mapped && q.dx && q.dout;
+        if (mapped && e == cudaSuccess) {
+            int64_t nmax = 0, omax = 0;
+            for (int32_t i = 0; i < b; ++i) {
+                const Pending& q = sl.io[i];
+                const int64_t Fi = (q.r.n + key.hop - 1) / key.hop;
+                sl.h_tab[i] = IoEntry{q.dx, q.dout, q.r.n, Fi};
+                nmax = std::max(nmax, q.r.n);
+                omax = std::max(omax, (int64_t)key.S * Fi);
+            }
+            const int gx = (int)std::min<int64_t>(64, (nmax + 4095) / 4096);
+            serve_gather<<<dim3(gx, b), 256, 0, sl.st>>>(sl.d_tab, sl.d_x, L, sl.d_len);
+            e = cudaGetLastError();
+            cwth_status st = e == cudaSuccess ? CWTH_OK : CWTH_ERR_CUDA;
+            if (st == CWTH_OK)
+                st = cwth_execute(cp->plan, sl.d_x, L, sl.d_len, b, sl.d_out, sl.st);
+            if (st == CWTH_OK) {
+                const int ox = (int)std::min<int64_t>(128, (omax + 4095) / 4096);
+                serve_scatter<<<dim3(ox, b), 256, 0, sl.st>>>(sl.d_tab, sl.d_out, key.S, F);
+                if (cudaGetLastError() != cudaSuccess) st = CWTH_ERR_CUDA;
+            }
+            e = cudaEventRecord(sl.ev, sl.st);
+            if (st == CWTH_OK && e != cudaSuccess) st = CWTH_ERR_CUDA;
+            sl.status = st;
+            return st;
         }
         for (int32_t i = 0; i < b && e == cudaSuccess; ++i) {
             const cwth_request& r = sl.reqs[i];
@@ -325,13 +410,13 @@ struct cwth_server_s {
                 }
                 continue;
             }
-            std::vector<cwth_request> reqs;
-            reqs.reserve(b);
+            std::vector<Pending> sel;
+            sel.reserve(b);
             for (int32_t i = 0; i < b; ++i) {
-                reqs.push_back(pick[i]->r);
+                sel.push_back(*pick[i]);
                 pending.erase(pick[i]);
             }
-            launch(slots[slot], cp, key, reqs, bytes);
+            launch(slots[slot], cp, key, sel, bytes);
         }
     }
 };
@@ -377,7 +462,23 @@ cwth_status cwth_server_submit(cwth_server_t s, const cwth_request* reqs, int32_
         if (!r.x || !r.out || r.n < 1 || !(r.fs > 0) || r.n_scales < 1 || r.hop < 1)
             return CWTH_ERR_INVALID_ARG;
     }
-    for (int32_t i = 0; i < n; ++i) s->pending.push_back(Pending{reqs[i], length_bucket(reqs[i].n)});
+    for (int32_t i = 0; i < n; ++i) {
+        Pending q{reqs[i], length_bucket(reqs[i].n), nullptr, nullptr};
+        if (!s->cfg.dry_run) {
+            // Page-locked buffers are read and written in place by the
+            // batch's gather / scatter kernels (their device addresses).
+            cudaPointerAttributes ax, ao;
+            if (cudaPointerGetAttributes(&ax, reqs[i].x) == cudaSuccess &&
+                ax.type == cudaMemoryTypeHost && ax.devicePointer &&
+                cudaPointerGetAttributes(&ao, reqs[i].out) == cudaSuccess &&
+                ao.type == cudaMemoryTypeHost && ao.devicePointer) {
+                q.dx = static_cast<const float*>(ax.devicePointer);
+                q.dout = static_cast<float*>(ao.devicePointer);
+            }
+            cudaGetLastError();  // a pageable pointer may leave an error behind
+        }
+        s->pending.push_back(q);
+    }
     return CWTH_OK;
 }
 
@@ -498,6 +599,7 @@ cwth_status cwth_server_destroy(cwth_server_t s) {
         cudaFree(sl.d_len);
         cudaFree(sl.d_out);
         if (sl.h_len) cudaFreeHost(sl.h_len);
+        if (sl.h_tab) cudaFreeHost(sl.h_tab);
         if (sl.ev) cudaEventDestroy(sl.ev);
         if (sl.st) cudaStreamDestroy(sl.st);
     }

@@ -55,9 +55,9 @@ size_t spectral_smem_bytes(int M, int P, int nconc, size_t fd_bytes) {
     return (size_t)(spectral_twiddle_entries(M) + M / 2 + 2) * sizeof(float2) + z;
 }
 
-size_t spectral_fd_bytes(int taps_n, int hw, int fst) {
+size_t spectral_fd_bytes(int taps_n, int hw, int fst, int n_groups) {
     if (taps_n <= 0) return 0;
-    return (size_t)taps_n * sizeof(float2) +
+    return (size_t)taps_n * sizeof(float2) + (size_t)n_groups * sizeof(FdGroup) +
            (((size_t)(2 * hw + 1) * fst + 4) * sizeof(float) + 15) / 16 * 16;
 }
 

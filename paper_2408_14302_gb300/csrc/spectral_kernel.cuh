@@ -744,7 +744,8 @@ __device__ __forceinline__ void fold_residue(const float2* __restrict__ X, const
 // xs[halo + f H - hw + tau] (tau = 0 .. 2 hw, f < seg_frames, rows fst
 // floats apart, fst odd) is copied from the staged samples before the
 // forward FFT overwrites them: each warp reads consecutive samples and
-// writes a column with an odd stride, both free of bank conflicts.
+// writes a column with an odd stride, both free of bank conflicts.  (The
+// taps and group records were copied during staging.)
 __device__ __forceinline__ void fd_copy_windows(const SpecLaunch& p, const float* __restrict__ xs,
                                                 float* __restrict__ Xw, float2* __restrict__ T) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
@@ -762,7 +763,6 @@ __device__ __forceinline__ void fd_copy_windows(const SpecLaunch& p, const float
                 if (t0 + 32 * u < wlen) Xw[(t0 + 32 * u) * fst + f] = v[u];
         }
     }
-    for (int i = threadIdx.x; i < p.fd_taps_n; i += blockDim.x) T[i] = __ldg(p.fd_taps + i);
 }
 
 // One fused item: the n scales of tap group g over the 32 frames
@@ -815,10 +815,10 @@ __device__ __forceinline__ void fd_sum(const float* __restrict__ xc, int fst,
 }
 
 __device__ __forceinline__ void fd_item(const SpecLaunch& p, const float* __restrict__ Xw,
-                                        const float2* __restrict__ T, int clip, int64_t k0,
-                                        int64_t F, int g, int fb) {
+                                        const float2* __restrict__ T, const FdGroup* G, int clip,
+                                        int64_t k0, int64_t F, int g, int fb) {
     const int lane = threadIdx.x & 31;
-    const FdGroup gr = p.fd_grp[g];
+    const FdGroup gr = G[g];
     const int Fs = p.seg_frames, fst = p.fd_fst;
     const int f = fb * 32 + lane;
     const int fc = f < Fs ? f : Fs - 1;  // idle lanes re-read a valid column
@@ -847,15 +847,18 @@ __device__ __forceinline__ void fd_item(const SpecLaunch& p, const float* __rest
 struct FdWork {
     const float* Xw;
     const float2* T;
+    const FdGroup* G;
     int clip, grp, ngrp, nfb, nitems;
     int64_t k0, F;
 };
 
 __device__ __forceinline__ FdWork fd_work(const SpecLaunch& p, const float* Xw, const float2* T,
-                                          int clip, int64_t k0, int64_t F, int grp, int ngrp) {
+                                          const FdGroup* G, int clip, int64_t k0, int64_t F,
+                                          int grp, int ngrp) {
     FdWork w;
     w.Xw = Xw;
     w.T = T;
+    w.G = G;
     w.clip = clip;
     w.grp = grp;
     w.ngrp = ngrp;
@@ -868,7 +871,7 @@ __device__ __forceinline__ FdWork fd_work(const SpecLaunch& p, const float* Xw, 
 
 __device__ __forceinline__ void fd_run(const SpecLaunch& p, const FdWork& w, int i) {
     const int q = i / w.nfb;
-    fd_item(p, w.Xw, w.T, w.clip, w.k0, w.F, w.grp + q * w.ngrp, i - q * w.nfb);
+    fd_item(p, w.Xw, w.T, w.G, w.clip, w.k0, w.F, w.grp + q * w.ngrp, i - q * w.nfb);
 }
 
 // a3 for one chunk of scales: band multiply + hop fold.  Scales are taken
@@ -1073,6 +1076,16 @@ __device__ __forceinline__ void spectral_item(const SpecLaunch& p, int seg, int 
             X[at] = make_float2(a, b);
         }
     }
+    if (has_fd) {
+        // The fused scales' taps and group records, into the fold's buffer
+        // (unused until the fold) while the sample loads are in flight.
+        float2* Tfd = Z;
+        for (int i = threadIdx.x; i < p.fd_taps_n; i += blockDim.x) Tfd[i] = __ldg(p.fd_taps + i);
+        int* Gw = reinterpret_cast<int*>(Tfd + p.fd_taps_n);
+        const int* Gr = reinterpret_cast<const int*>(p.fd_grp);
+        const int nw = p.fd_groups * (int)(sizeof(FdGroup) / sizeof(int));
+        for (int i = threadIdx.x; i < nw; i += blockDim.x) Gw[i] = __ldg(Gr + i);
+    }
     __syncthreads();
 
     // Short-support scales: summed here, before the forward FFT overwrites
@@ -1082,12 +1095,13 @@ __device__ __forceinline__ void spectral_item(const SpecLaunch& p, int seg, int 
         // buffer (unused until the fold), items dealt to whichever warp is
         // free (a shared counter, largest groups first).
         float2* Tfd = Z;
-        float* Xw = reinterpret_cast<float*>(Tfd + p.fd_taps_n);
+        const FdGroup* Gfd = reinterpret_cast<const FdGroup*>(Tfd + p.fd_taps_n);
+        float* Xw = reinterpret_cast<float*>(const_cast<FdGroup*>(Gfd) + p.fd_groups);
         __shared__ int s_ctr;
         if (threadIdx.x == 0) s_ctr = 0;
         fd_copy_windows(p, reinterpret_cast<const float*>(X), Xw, Tfd);
         __syncthreads();
-        const FdWork fw = fd_work(p, Xw, Tfd, clip, k0, F, grp, ngrp);
+        const FdWork fw = fd_work(p, Xw, Tfd, Gfd, clip, k0, F, grp, ngrp);
         const int lane = threadIdx.x & 31;
         for (;;) {
             int it = 0;

@@ -38,26 +38,36 @@ def test_mix_equals_alone_and_oracle(precision, path):
         assert np.max(np.abs(got - ref)) <= 1e-5 * np.max(ref), q.rid
 
 
-@pytest.mark.parametrize("precision,path", [("bf16x3", "auto"), ("fp32", "auto")])
-def test_library_server_mix_equals_alone_and_oracle(precision, path):
+@pytest.mark.parametrize("precision,path,pinned", [("bf16x3", "auto", False),
+                                                  ("fp32", "auto", False),
+                                                  ("fp32", "auto", True)])
+def test_library_server_mix_equals_alone_and_oracle(precision, path, pinned):
     """The library's server (cwth_server_*): requests replayed at their
     arrival times in batches of one key give each request's scalogram as a
     plan of its own would (1e-5 of max|W|; the server derives the scales in
-    C) and match the float64 oracle."""
+    C) and match the float64 oracle.  Pageable buffers take one copy per
+    request; page-locked ones the batch's gather and scatter kernels."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     import oracle
     from paper_2408_14302_gb300 import cwth, serving, signals
     pool = [signals.machine_clip(950 + i, 40000, 16000.0) for i in range(3)]
-    reqs = serving.poisson_requests(40, 5000.0, seed=37, pool=pool, min_s=0.05, max_s=2.0,
+    # arrivals microseconds apart: requests wait together and share batches
+    reqs = serving.poisson_requests(40, 1e6, seed=37, pool=pool, min_s=0.05, max_s=2.0,
                                     scale_counts=(8, 12), hops=(64, 96, 128))
     arr = (cwth.Request * len(reqs))()
-    outs = []
+    outs, keep = [], []
     for i, q in enumerate(reqs):
-        out = np.full((q.n_scales, q.frames), -1.0, np.float32)
+        if pinned:
+            xt = torch.from_numpy(q.x).pin_memory()
+            ot = torch.full((q.n_scales, q.frames), -1.0).pin_memory()
+            keep += [xt, ot]
+            xp, out, op = xt.data_ptr(), ot.numpy(), ot.data_ptr()
+        else:
+            out = np.full((q.n_scales, q.frames), -1.0, np.float32)
+            xp, op = q.x.ctypes.data, out.ctypes.data
         outs.append(out)
-        arr[i] = cwth.Request(q.rid, q.x.ctypes.data, len(q.x), q.fs, q.n_scales, q.hop,
-                              out.ctypes.data)
+        arr[i] = cwth.Request(q.rid, xp, len(q.x), q.fs, q.n_scales, q.hop, op)
     with cwth.Server(budget_bytes=1 << 34, plan_cache_bytes=1 << 30, max_batch=6, slots=3,
                      precision=precision, path=path) as srv:
         lat, bs, stat, wall = srv.replay(arr, [q.arrival for q in reqs])
