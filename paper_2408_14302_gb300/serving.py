@@ -373,7 +373,7 @@ def main(argv=None):
     ap.add_argument("--rates", default="50,100,200,500,1000,2000")
     ap.add_argument("--requests", type=int, default=400)
     ap.add_argument("--budget-gb", type=float, default=40.0)
-    ap.add_argument("--plan-cache-gb", type=float, default=4.0)
+    ap.add_argument("--plan-cache-gb", type=float, default=16.0)
     ap.add_argument("--max-batch", type=int, default=16)
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--engine", default="library", choices=["library", "python"])

@@ -73,12 +73,16 @@ def test_replay_is_repeatable_and_cache_is_written(batch):
 def test_worklist_batch_matches_per_group_executes():
     """The work-list launch gives each group's cwth_execute result (byte for
     byte: the same kernel arithmetic per item), including clips of length 0
-    and 1, and leaves frames past each clip untouched."""
+    and 1 and hops with an odd factor, and leaves frames past each clip
+    untouched."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_2408_14302_gb300 import cwth, signals
+    # hops 96 and 100: segments with an odd factor (column FFTs plus
+    # radix-3/5 passes) in the same launch as power-of-two ones
     specs = [(16000.0, 12, 128, [9000, 1, 0, 4000]), (48000.0, 8, 256, [20000, 12345]),
-             (16000.0, 20, 512, [30000])]
+             (16000.0, 20, 512, [30000]), (16000.0, 10, 96, [25000, 7777]),
+             (16000.0, 6, 100, [18000])]
     groups, plans, refs = [], [], []
     for fs, S, hop, lens in specs:
         n = max(lens)
@@ -103,3 +107,31 @@ def test_worklist_batch_matches_per_group_executes():
     b.close()
     for p in plans:
         p.close()
+
+
+def test_worklist_mode_runs_pruned_groups_beside_the_launch():
+    """Small hops give plans with pruned inverse FFTs, which the work list
+    does not take: in the work-list mode those groups run as their own
+    executes beside its launch (in the same graph), and every clip still
+    matches the oracle."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import oracle
+    from paper_2408_14302_gb300 import batching, signals
+    clips, fs, ns, hs = batching.uneven_workload(n_clips=8, seed=91, min_s=0.05, max_s=0.8,
+                                                 p48k=0.0, scale_counts=(6,), hops=(4, 128))
+    runner = batching.BatchRunner(clips, fs, ns, hs, tune=False, mode="worklist")
+    try:
+        assert runner.solo and runner.batch is not None
+        assert all(g["plan"].info()["spectral_pruned"] for g in runner.solo)
+        runner.capture()
+        runner.replay()
+        torch.cuda.synchronize()
+        for i in range(len(clips)):
+            got = runner.result(i).astype(np.float64)
+            sc = signals.scales_for_band(50.0, 8000.0, ns[i], fs[i])
+            ref = oracle.cwth_magnitude(np.asarray(clips[i], np.float32).astype(np.float64), sc,
+                                        hs[i])
+            assert np.max(np.abs(got - ref)) <= TOL * np.max(ref), i
+    finally:
+        runner.close()
