@@ -388,7 +388,7 @@ cwth_status cwth_batch_destroy(cwth_batch_t batch);
  *
  * The first call on a device sets that device up (looks up the array's
  * device address, sets the kernels' shared-memory limit, fetches the
- * tensor-map encoder); make that first call before any stream capture.
+ * tensor-map encoder).
  * Every call on a device reuses the same array and leaves the previous call's
  * contents in it (each call rewrites what it reads), so calls whose work
  * overlaps on the GPU - on different streams, or from different threads -
