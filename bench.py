@@ -463,6 +463,7 @@ def run_ours(args, rank, world, local_rank):
         hop1 = {"ms_per_step": ms1, "audio_sec_per_s": world * audio_s / (ms1 * 1e-3),
                 "scalogram_gbs": world * o1.numel() * 4 / (ms1 * 1e-3) / 1e9,
                 "seg_len": p1.info()["seg_len"], "num_segments": p1.info()["num_segments"],
+                "spectral_parts": p1.info()["spectral_parts"],
                 "bytes_per_launch": int(algorithmic_bytes_per_clip(scales, 1) * N_CLIPS),
                 "flops_per_launch": algorithmic_flops_per_clip(scales, 1)[0] * N_CLIPS}
         del o1
@@ -545,7 +546,8 @@ def run_ours(args, rank, world, local_rank):
                    "morlet": [B_MORLET, C_MORLET], "path": "auto", "precision": "fp32",
                    "l2": "flushed: 256 MiB write before every timed step",
                    "seg_len": info["seg_len"], "num_segments": info["num_segments"],
-                   "num_spectral": info["num_spectral"], "num_direct": info["num_direct"]},
+                   "num_spectral": info["num_spectral"], "num_direct": info["num_direct"],
+                   "spectral_parts": info["spectral_parts"]},
         "scalogram_gbs": world * out_bytes / (ms * 1e-3) / 1e9,
         "roofline": {"bound": "hbm" if t_hbm_peak >= t_alu_peak else "alu",
                      "kernel": "spectral_segment_kernel",
@@ -571,7 +573,9 @@ def run_ours(args, rank, world, local_rank):
                 "h2d_bytes_per_step": int(hx.numel() * 4),
                 "d2h_bytes_per_step": int(hout.numel() * 4),
                 "ms_per_step": e2e_s * 1e3, "api": "cwth_execute_host (pinned host buffers)"},
-        "gpu_launches": args.steps * 1,
+        # the automatic float32 plan launches its spectral kernel once per
+        # spectral part (no direct-path scales at float32 power-of-two hops)
+        "gpu_launches": args.steps * max(1, info["spectral_parts"]),
         "clocks": clocks,
         "hop1": hop1,
         "auto_bf16x3": auto,

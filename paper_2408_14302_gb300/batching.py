@@ -90,11 +90,12 @@ def group_key(fs: float, n_scales: int, hop: int):
 
 def _worklist_ok(plan) -> bool:
     """Whether cwth_batch_create takes the plan: spectral-path scales only
-    (folded or fused), two CTAs per SM, no pruned inverse FFTs, no
-    re-sampling."""
+    (folded or fused) in one part, two CTAs per SM, no pruned inverse FFTs,
+    no re-sampling."""
     i = plan.info()
     return (i["num_direct"] == i["num_fused"] and not i["spectral_pruned"]
-            and i["spectral_threads"] in (0, 512) and i["resample"] == 1)
+            and i["spectral_threads"] in (0, 512) and i["resample"] == 1
+            and i["spectral_parts"] <= 1)
 
 
 class BatchRunner:

@@ -70,6 +70,10 @@ int spectral_nconc(int M, int P, int limit, int threads, size_t fd_bytes) {
 // Internal path marker: a short-support scale summed in the time domain
 // inside the spectral kernel (reported as CWTH_PATH_DIRECT).
 constexpr int32_t kPathFused = 3;
+// Internal path marker: a spectral scale of the plan's second part (its
+// child plan with a shorter-halo segmentation; reported as
+// CWTH_PATH_SPECTRAL).
+constexpr int32_t kPathSpectralChild = 4;
 // Largest half support a fused scale may have (window rows 2h + 1).
 constexpr int kFdMaxHalf = 256;
 // Cost model, in the segment model's lane-operation units (a fold bin is
@@ -362,6 +366,11 @@ int choose_fused_count(const cwth_plan_s& p, const std::vector<int32_t>& asc) {
 }
 
 void free_plan_memory(cwth_plan_s* p) {
+    if (p->child) {
+        free_plan_memory(p->child);
+        delete p->child;
+        p->child = nullptr;
+    }
     cudaFree(p->d_tw);
     cudaFree(p->d_sp);
     cudaFree(p->d_fd_taps);
@@ -776,6 +785,78 @@ cwth_status build_spectral(cwth_plan_s* p) {
     return cuda_status(e);
 }
 
+// Two spectral parts when the cost model prefers them: the smallest
+// spectral scales (shortest supports) in a child plan whose segments need
+// only their own, short halo, so more of each segment's frames are valid;
+// the rest (and the fused scales) stay in this plan.  Every split point of
+// the ascending scale list is costed with each part's best segment length;
+// a split is kept only if it saves at least a tenth of the one-part cost
+// (the second part repeats the forward FFTs).  Not for forced segment
+// lengths.
+constexpr double kSplitGain = 0.9;
+
+cwth_status split_spectral(cwth_plan_s* p) {
+    if (p->no_split || p->seg_force > 0 || !spectral_hop_ok(p->hop)) return CWTH_OK;
+    std::vector<int32_t> order;
+    for (int s = 0; s < p->S; ++s)
+        if (p->scale_path[s] == CWTH_PATH_SPECTRAL) order.push_back(s);
+    if (order.size() < 2) return CWTH_OK;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int32_t i, int32_t j) { return p->scales[i] < p->scales[j]; });
+    std::vector<double> sp;
+    for (int32_t s : order) sp.push_back(p->scales[s]);
+    std::vector<int32_t> fd_idx;
+    for (int s = 0; s < p->S; ++s)
+        if (p->scale_path[s] == kPathFused) fd_idx.push_back(s);
+    std::stable_sort(fd_idx.begin(), fd_idx.end(),
+                     [&](int32_t i, int32_t j) { return p->scales[i] > p->scales[j]; });
+    std::vector<int32_t> fd_h;
+    for (int32_t s : fd_idx) fd_h.push_back(fd_half_support(p->scales[s], p->B));
+    SegChoice one;
+    if (!choose_segment(*p, sp, fd_h, &one)) return CWTH_OK;
+    double best = one.cost;
+    size_t best_j = 0;
+    const std::vector<int32_t> none;
+    for (size_t j = 1; j < sp.size(); ++j) {
+        const std::vector<double> a(sp.begin(), sp.begin() + j), b(sp.begin() + j, sp.end());
+        SegChoice ca, cb;
+        if (!choose_segment(*p, a, none, &ca) || !choose_segment(*p, b, fd_h, &cb)) continue;
+        if (ca.cost + cb.cost < best) {
+            best = ca.cost + cb.cost;
+            best_j = j;
+        }
+    }
+    if (best_j == 0 || best > kSplitGain * one.cost) return CWTH_OK;
+    cwth_plan_s* q = new (std::nothrow) cwth_plan_s();
+    if (!q) return CWTH_ERR_OOM;
+    q->device = p->device;
+    q->B = p->B;
+    q->C = p->C;
+    q->fs = p->fs;
+    q->S = p->S;
+    q->hop = p->hop;
+    q->precision = p->precision;
+    q->path = p->path;
+    q->max_len = p->max_len;
+    q->frames_max = p->frames_max;
+    q->scales = p->scales;
+    q->scale_path.assign(p->S, CWTH_PATH_DIRECT);
+    for (size_t j = 0; j < best_j; ++j) q->scale_path[order[j]] = CWTH_PATH_SPECTRAL;
+    q->no_split = true;
+    q->setup = p->setup;
+    cwth_status st = build_spectral(q);
+    q->setup = nullptr;
+    if (st != CWTH_OK) {
+        free_plan_memory(q);
+        delete q;
+        return st;
+    }
+    p->child = q;
+    for (size_t j = 0; j < best_j; ++j) p->scale_path[order[j]] = kPathSpectralChild;
+    p->table_bytes += q->table_bytes;
+    return CWTH_OK;
+}
+
 // The spectral kernel's launch record of a plan for one batch: scale
 // groups (enough CTAs for two waves, each group at least 8 scales, since
 // every group repeats its segment's forward FFT; one group when fill_gpu is
@@ -990,8 +1071,10 @@ cwth_status launch_direct(cwth_plan_s* p, const float* d_x, int64_t ld_x, const 
 cwth_status launch_all(cwth_plan_s* p, const float* d_x, int64_t ld_x, const int64_t* d_len,
                        int32_t batch, float* d_out, cudaStream_t st, bool fill_gpu = true) {
     cwth_status s = launch_direct(p, d_x, ld_x, d_len, batch, d_out, st);
-    if (s != CWTH_OK) return s;
-    return launch_spectral(p, d_x, ld_x, d_len, batch, d_out, st, fill_gpu);
+    if (s == CWTH_OK) s = launch_spectral(p, d_x, ld_x, d_len, batch, d_out, st, fill_gpu);
+    if (s == CWTH_OK && p->child)
+        s = launch_spectral(p->child, d_x, ld_x, d_len, batch, d_out, st, fill_gpu);
+    return s;
 }
 
 // Samples each input row must hold: the longest clip, or for a
@@ -1170,6 +1253,7 @@ cwth_status plan_create(const cwth_morlet* w, const double* scales, int32_t S, i
         if (st == CWTH_OK && cudaStreamCreateWithFlags(&p->setup, cudaStreamNonBlocking) != cudaSuccess)
             st = CWTH_ERR_CUDA;
         if (st == CWTH_OK) st = build_direct(p);
+        if (st == CWTH_OK) st = split_spectral(p);
         if (st == CWTH_OK) st = build_spectral(p);
         if (p->setup) {
             cudaStreamSynchronize(p->setup);
@@ -1367,7 +1451,8 @@ cwth_status cwth_plan_query(cwth_plan_t p, cwth_plan_info* info) {
     info->hop = p->hop;
     info->max_len = p->max_len;
     info->frames_max = p->frames_max;
-    info->num_spectral = p->n_sp;
+    info->num_spectral = p->n_sp + (p->child ? p->child->n_sp : 0);
+    info->spectral_parts = p->child ? 2 : (p->n_sp + p->n_fd > 0 ? 1 : 0);
     info->num_direct = p->n_dir + p->n_fd;
     info->num_fused = p->n_fd;
     info->seg_len = p->M;
@@ -1442,7 +1527,10 @@ cwth_status cwth_plan_scale_paths(cwth_plan_t p, int32_t* paths) {
     if (!valid_plan(p)) return CWTH_ERR_BAD_PLAN;
     if (!paths) return CWTH_ERR_INVALID_ARG;
     for (int s = 0; s < p->S; ++s)
-        paths[s] = p->scale_path[s] == kPathFused ? CWTH_PATH_DIRECT : p->scale_path[s];
+        paths[s] = p->scale_path[s] == kPathFused
+                       ? CWTH_PATH_DIRECT
+                       : (p->scale_path[s] == kPathSpectralChild ? CWTH_PATH_SPECTRAL
+                                                                 : p->scale_path[s]);
     return CWTH_OK;
 }
 
@@ -1465,9 +1553,9 @@ cwth_status cwth_batch_create(int32_t n, const cwth_plan_t* plans, const float* 
         // One launch of the paired spectral kernel serves plans whose every
         // scale is spectral or fused, without pruned inverse FFTs or
         // re-sampling.
-        if (p->n_dir > 0 || p->resample > 1 || p->spec_prune) {
-            note_error("batched plans must be float32 spectral/fused plans without pruning or "
-                       "re-sampling");
+        if (p->n_dir > 0 || p->resample > 1 || p->spec_prune || p->child) {
+            note_error("batched plans must be one-part float32 spectral/fused plans without "
+                       "pruning or re-sampling");
             return CWTH_ERR_UNSUPPORTED;
         }
         if ((p->n_sp > 0 || p->n_fd > 0) &&

@@ -85,7 +85,8 @@ class PlanInfo(ctypes.Structure):
                 ("table_bytes", ctypes.c_int64), ("sample_rate", ctypes.c_double),
                 ("resample", ctypes.c_int32), ("spectral_threads", ctypes.c_int32),
                 ("spectral_pass_scales", ctypes.c_int32), ("spectral_pruned", ctypes.c_int32),
-                ("num_fused", ctypes.c_int32), ("workspace_bytes", ctypes.c_int64)]
+                ("num_fused", ctypes.c_int32), ("workspace_bytes", ctypes.c_int64),
+                ("spectral_parts", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -333,6 +333,27 @@ def test_1024_thread_shape_hop2_long_segments(cw, sig):
         assert np.all(got[i, :, F:] == -3.0)
 
 
+def test_two_part_plan_hop1(cw, sig):
+    """Hop 1 over 50-8000 Hz: the cost model runs the smallest scales as a
+    second spectral part with its own short-halo segments.  Rows of both
+    parts against the oracle, and the whole scalogram against a one-part
+    plan (a forced segment length never splits)."""
+    n, hop = 60000, 1
+    xs = sig.machine_batch(2, n)
+    sc = sig.scales_for_band(50, 8000, 48, 16000.0)
+    got, info = run_gpu(cw, xs, sc, hop)
+    assert info["spectral_parts"] == 2 and info["num_spectral"] == 48, info
+    with cw.Plan(sc, hop=hop, max_len=n, seg_len=info["seg_len"]) as one:
+        assert one.info()["spectral_parts"] == 1
+        ref1 = one.execute(torch.from_numpy(xs.astype(np.float32)).cuda()).cpu().numpy()
+    rows = np.array([0, 8, 16, 24, 32, 40, 47])
+    for i in range(2):
+        assert rel_err(got[i], ref1[i]) <= TOL_FP32
+        ref = oracle_mag(xs[i], sc[rows], hop)
+        err = float(np.max(np.abs(got[i, rows] - ref))) / float(ref.max())
+        assert err <= TOL_FP32, (i, err)
+
+
 @pytest.mark.parametrize("hop", [3, 5, 7, 12, 54, 96, 100, 336, 1600])
 def test_non_power_of_two_hops(cw, sig, hop):
     """Hops with an odd factor d (3, 5, 7, 3 * 2^2, 27 * 2, 3 * 2^5, 25 * 2^2,
