@@ -276,11 +276,12 @@ typedef struct {
                                   the time domain inside the spectral kernel   */
     int64_t workspace_bytes;   /* device bytes the plan's growable workspaces
                                   hold now (see cwth_execute, cwth_plan_reserve) */
-    int32_t spectral_parts;    /* spectral launches per execute: 2 when the
-                                  smallest spectral scales run with their own,
-                                  shorter-halo segments (the other fields
-                                  describe the part with the larger scales),
-                                  1, or 0 without spectral scales            */
+    int32_t spectral_parts;    /* spectral launches per execute: more than 1
+                                  when the smallest spectral scales run in
+                                  parts with their own, shorter-halo segments
+                                  (the other fields describe the part with
+                                  the largest scales), 1, or 0 without
+                                  spectral scales                            */
 } cwth_plan_info;
 
 /* Fill *info.  Errors: CWTH_ERR_BAD_PLAN, CWTH_ERR_INVALID_ARG (NULL info). */

@@ -785,26 +785,20 @@ cwth_status build_spectral(cwth_plan_s* p) {
     return cuda_status(e);
 }
 
-// Two spectral parts when the cost model prefers them: the smallest
+// Several spectral parts when the cost model prefers them: the smallest
 // spectral scales (shortest supports) in a child plan whose segments need
 // only their own, short halo, so more of each segment's frames are valid;
 // the rest (and the fused scales) stay in this plan.  Every split point of
 // the ascending scale list is costed with each part's best segment length;
-// a split is kept only if it saves at least a tenth of the one-part cost
-// (the second part repeats the forward FFTs).  Not for forced segment
-// lengths.
+// a split is kept only if it saves at least a tenth of the cost before it
+// (each part repeats the forward FFTs).  The remaining scales are then
+// offered the same split again, up to kMaxSpectralParts parts (children
+// chained in split order).  Not for forced segment lengths.
 constexpr double kSplitGain = 0.9;
+constexpr int kMaxSpectralParts = 4;
 
 cwth_status split_spectral(cwth_plan_s* p) {
     if (p->no_split || p->seg_force > 0 || !spectral_hop_ok(p->hop)) return CWTH_OK;
-    std::vector<int32_t> order;
-    for (int s = 0; s < p->S; ++s)
-        if (p->scale_path[s] == CWTH_PATH_SPECTRAL) order.push_back(s);
-    if (order.size() < 2) return CWTH_OK;
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int32_t i, int32_t j) { return p->scales[i] < p->scales[j]; });
-    std::vector<double> sp;
-    for (int32_t s : order) sp.push_back(p->scales[s]);
     std::vector<int32_t> fd_idx;
     for (int s = 0; s < p->S; ++s)
         if (p->scale_path[s] == kPathFused) fd_idx.push_back(s);
@@ -812,48 +806,60 @@ cwth_status split_spectral(cwth_plan_s* p) {
                      [&](int32_t i, int32_t j) { return p->scales[i] > p->scales[j]; });
     std::vector<int32_t> fd_h;
     for (int32_t s : fd_idx) fd_h.push_back(fd_half_support(p->scales[s], p->B));
-    SegChoice one;
-    if (!choose_segment(*p, sp, fd_h, &one)) return CWTH_OK;
-    double best = one.cost;
-    size_t best_j = 0;
     const std::vector<int32_t> none;
-    for (size_t j = 1; j < sp.size(); ++j) {
-        const std::vector<double> a(sp.begin(), sp.begin() + j), b(sp.begin() + j, sp.end());
-        SegChoice ca, cb;
-        if (!choose_segment(*p, a, none, &ca) || !choose_segment(*p, b, fd_h, &cb)) continue;
-        if (ca.cost + cb.cost < best) {
-            best = ca.cost + cb.cost;
-            best_j = j;
+    cwth_plan_s** tail = &p->child;
+    for (int part = 1; part < kMaxSpectralParts; ++part) {
+        std::vector<int32_t> order;
+        for (int s = 0; s < p->S; ++s)
+            if (p->scale_path[s] == CWTH_PATH_SPECTRAL) order.push_back(s);
+        if (order.size() < 2) break;
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int32_t i, int32_t j) { return p->scales[i] < p->scales[j]; });
+        std::vector<double> sp;
+        for (int32_t s : order) sp.push_back(p->scales[s]);
+        SegChoice one;
+        if (!choose_segment(*p, sp, fd_h, &one)) break;
+        double best = one.cost;
+        size_t best_j = 0;
+        for (size_t j = 1; j < sp.size(); ++j) {
+            const std::vector<double> a(sp.begin(), sp.begin() + j), b(sp.begin() + j, sp.end());
+            SegChoice ca, cb;
+            if (!choose_segment(*p, a, none, &ca) || !choose_segment(*p, b, fd_h, &cb)) continue;
+            if (ca.cost + cb.cost < best) {
+                best = ca.cost + cb.cost;
+                best_j = j;
+            }
         }
+        if (best_j == 0 || best > kSplitGain * one.cost) break;
+        cwth_plan_s* q = new (std::nothrow) cwth_plan_s();
+        if (!q) return CWTH_ERR_OOM;
+        q->device = p->device;
+        q->B = p->B;
+        q->C = p->C;
+        q->fs = p->fs;
+        q->S = p->S;
+        q->hop = p->hop;
+        q->precision = p->precision;
+        q->path = p->path;
+        q->max_len = p->max_len;
+        q->frames_max = p->frames_max;
+        q->scales = p->scales;
+        q->scale_path.assign(p->S, CWTH_PATH_DIRECT);
+        for (size_t j = 0; j < best_j; ++j) q->scale_path[order[j]] = CWTH_PATH_SPECTRAL;
+        q->no_split = true;
+        q->setup = p->setup;
+        cwth_status st = build_spectral(q);
+        q->setup = nullptr;
+        if (st != CWTH_OK) {
+            free_plan_memory(q);
+            delete q;
+            return st;
+        }
+        *tail = q;
+        tail = &q->child;
+        for (size_t j = 0; j < best_j; ++j) p->scale_path[order[j]] = kPathSpectralChild;
+        p->table_bytes += q->table_bytes;
     }
-    if (best_j == 0 || best > kSplitGain * one.cost) return CWTH_OK;
-    cwth_plan_s* q = new (std::nothrow) cwth_plan_s();
-    if (!q) return CWTH_ERR_OOM;
-    q->device = p->device;
-    q->B = p->B;
-    q->C = p->C;
-    q->fs = p->fs;
-    q->S = p->S;
-    q->hop = p->hop;
-    q->precision = p->precision;
-    q->path = p->path;
-    q->max_len = p->max_len;
-    q->frames_max = p->frames_max;
-    q->scales = p->scales;
-    q->scale_path.assign(p->S, CWTH_PATH_DIRECT);
-    for (size_t j = 0; j < best_j; ++j) q->scale_path[order[j]] = CWTH_PATH_SPECTRAL;
-    q->no_split = true;
-    q->setup = p->setup;
-    cwth_status st = build_spectral(q);
-    q->setup = nullptr;
-    if (st != CWTH_OK) {
-        free_plan_memory(q);
-        delete q;
-        return st;
-    }
-    p->child = q;
-    for (size_t j = 0; j < best_j; ++j) p->scale_path[order[j]] = kPathSpectralChild;
-    p->table_bytes += q->table_bytes;
     return CWTH_OK;
 }
 
@@ -1072,8 +1078,8 @@ cwth_status launch_all(cwth_plan_s* p, const float* d_x, int64_t ld_x, const int
                        int32_t batch, float* d_out, cudaStream_t st, bool fill_gpu = true) {
     cwth_status s = launch_direct(p, d_x, ld_x, d_len, batch, d_out, st);
     if (s == CWTH_OK) s = launch_spectral(p, d_x, ld_x, d_len, batch, d_out, st, fill_gpu);
-    if (s == CWTH_OK && p->child)
-        s = launch_spectral(p->child, d_x, ld_x, d_len, batch, d_out, st, fill_gpu);
+    for (cwth_plan_s* q = p->child; q && s == CWTH_OK; q = q->child)
+        s = launch_spectral(q, d_x, ld_x, d_len, batch, d_out, st, fill_gpu);
     return s;
 }
 
@@ -1451,8 +1457,12 @@ cwth_status cwth_plan_query(cwth_plan_t p, cwth_plan_info* info) {
     info->hop = p->hop;
     info->max_len = p->max_len;
     info->frames_max = p->frames_max;
-    info->num_spectral = p->n_sp + (p->child ? p->child->n_sp : 0);
-    info->spectral_parts = p->child ? 2 : (p->n_sp + p->n_fd > 0 ? 1 : 0);
+    info->num_spectral = p->n_sp;
+    info->spectral_parts = p->n_sp + p->n_fd > 0 ? 1 : 0;
+    for (const cwth_plan_s* q = p->child; q; q = q->child) {
+        info->num_spectral += q->n_sp;
+        info->spectral_parts += 1;
+    }
     info->num_direct = p->n_dir + p->n_fd;
     info->num_fused = p->n_fd;
     info->seg_len = p->M;

@@ -263,9 +263,10 @@ struct cwth_plan_s {
     int32_t fft_d = 1, fft_n2 = 0;  // forward FFT: fft_d column FFTs of fft_n2 points
     double seg_cost = 0;      // cost model's lane operations per segment
     int32_t seg_force = 0;    // segment length fixed by cwth_plan_segment (0: cost model)
-    // The smallest spectral scales may run as a second part with its own
-    // (shorter-halo) segmentation: a child plan holding the same scale list
-    // and output rows, launched after this one (null: one part).
+    // The smallest spectral scales may run as further parts with their own
+    // (shorter-halo) segmentations: child plans holding the same scale list
+    // and output rows, chained through `child` and launched after this one
+    // (null: one part).
     cwth_plan_s* child = nullptr;
     bool no_split = false;    // a child never splits again
     float2* d_tw = nullptr;

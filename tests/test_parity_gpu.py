@@ -334,15 +334,15 @@ def test_1024_thread_shape_hop2_long_segments(cw, sig):
 
 
 def test_two_part_plan_hop1(cw, sig):
-    """Hop 1 over 50-8000 Hz: the cost model runs the smallest scales as a
-    second spectral part with its own short-halo segments.  Rows of both
+    """Hop 1 over 50-8000 Hz: the cost model runs the smallest scales as
+    further spectral parts with their own short-halo segments.  Rows of both
     parts against the oracle, and the whole scalogram against a one-part
     plan (a forced segment length never splits)."""
     n, hop = 60000, 1
     xs = sig.machine_batch(2, n)
     sc = sig.scales_for_band(50, 8000, 48, 16000.0)
     got, info = run_gpu(cw, xs, sc, hop)
-    assert info["spectral_parts"] == 2 and info["num_spectral"] == 48, info
+    assert info["spectral_parts"] >= 2 and info["num_spectral"] == 48, info
     with cw.Plan(sc, hop=hop, max_len=n, seg_len=info["seg_len"]) as one:
         assert one.info()["spectral_parts"] == 1
         ref1 = one.execute(torch.from_numpy(xs.astype(np.float32)).cuda()).cpu().numpy()
