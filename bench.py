@@ -392,6 +392,40 @@ def run_direct_leg(torch, cwth, dev, flush, stream, steps, peak_bf16):
             "peak_bf16_tflops": peak_bf16, "roofline": roof, "runs": res}
 
 
+def run_serving_leg(torch, cwth):
+    """Continuous-batching server (the library's cwth_server_*) on the
+    serving mix: log-uniform 0.5-60 s machine-sound clips at 16 kHz, 32-256
+    scales (50-8000 Hz), hops 32-512, cut from a page-locked pool of seeded
+    signals, scalograms into a page-locked ring.  One warm-up pass builds
+    the server's plans; then 2000 Poisson requests at 1000 req/s (p50/p99
+    latency) and 2000 arriving at once (saturation throughput)."""
+    from paper_2408_14302_gb300 import serving
+    pool = [signals.machine_clip(5000 + i, 60 * 16000, 16000.0) for i in range(8)]
+    pinned = torch.from_numpy(np.stack(pool).astype(np.float32)).pin_memory()
+    ring = torch.empty(1 << 28, dtype=torch.float32).pin_memory()
+    srv = cwth.Server(budget_bytes=40 << 30, plan_cache_bytes=16 << 30, max_batch=16, slots=8,
+                      precision="fp32", path="auto")
+    try:
+        serving.library_replay(serving.poisson_requests(1000, 1e6, seed=4000, pool=pool),
+                               pinned, ring, server=srv)
+        res = {}
+        for name, rate in (("poisson_1000_per_s", 1000.0), ("saturation", 1e6)):
+            reqs = serving.poisson_requests(2000, rate, seed=6000 + int(rate), pool=pool)
+            s, _, _ = serving.library_replay(reqs, pinned, ring, server=srv)
+            audio = sum(r.audio_seconds for r in reqs)
+            res[name] = {"p50_ms": s["p50_ms"], "p99_ms": s["p99_ms"],
+                         "audio_sec_per_s": audio / s["wall_s"],
+                         "offered_audio_sec_per_s": audio / max(reqs[-1].arrival, 1e-9),
+                         "mean_batch": s["mean_batch"], "requests": len(reqs)}
+    finally:
+        srv.close()
+    res["config"] = {"engine": "cwth_server (library)", "precision": "fp32", "path": "auto",
+                     "slots": 8, "max_batch": 16, "budget_gb": 40, "plan_cache_gb": 16,
+                     "clips": "log-uniform 0.5-60 s at 16 kHz", "scales": [32, 64, 128, 256],
+                     "hops": [32, 64, 128, 256, 512]}
+    return res
+
+
 # ------------------------------------------------------------------ our arm
 def time_steps(torch, fn, steps, flush, stream):
     """Per-step CUDA-event time on `stream` with an L2 flush before each step."""
@@ -468,6 +502,10 @@ def run_ours(args, rank, world, local_rank):
                 "flops_per_launch": algorithmic_flops_per_clip(scales, 1)[0] * N_CLIPS}
         del o1
         p1.close()
+
+    serving_leg = None
+    if not args.no_serving and rank == 0:
+        serving_leg = run_serving_leg(torch, cwth)
 
     pk, pk_kind = peaks()
     direct = None
@@ -580,6 +618,7 @@ def run_ours(args, rank, world, local_rank):
         "hop1": hop1,
         "auto_bf16x3": auto,
         "direct": direct,
+        "serving": serving_leg,
     }
     plan.close()
     return line
@@ -650,6 +689,7 @@ def main():
     ap.add_argument("--no-hop1", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-direct", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -440,10 +440,11 @@ cwth_status cwth_noalloc_status(void *stream);
  * their device tables; their bytes count against the budget and the cache
  * evicts the least recently used idle plan when it would exceed
  * plan_cache_bytes.  Each request's samples are read straight from the
- * caller's memory and its scalogram written straight into the caller's
- * buffer: when both are page-locked, one gather and one scatter kernel per
- * batch access them in place over the host link; otherwise one copy each
- * way per request.  Not thread-safe: one thread drives a server.
+ * caller's memory (when page-locked, by one gather kernel per batch that
+ * reads them in place over the host link; otherwise one upload per
+ * request) and its scalogram is downloaded straight into the caller's
+ * buffer (one copy per request; page-locked buffers make it asynchronous).
+ * Not thread-safe: one thread drives a server.
  */
 typedef struct cwth_server_s *cwth_server_t;
 

@@ -8,9 +8,9 @@
 // The admission budget charges the staging of every batch in flight plus
 // the device bytes of every cached plan; the plan cache evicts the least
 // recently used idle plan when a new one would exceed its own bound.  Each
-// request's samples are uploaded from the caller's memory and its scalogram
-// downloaded into the caller's buffer by the slot's stream, so the host
-// never copies samples.
+// request's samples are read from the caller's memory (in place by a
+// gather kernel when page-locked) and its scalogram downloaded into the
+// caller's buffer by the slot's stream, so the host never copies samples.
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -59,46 +59,43 @@ struct CachedPlan {
 struct Pending {
     cwth_request r;
     int64_t bucket;
-    // device addresses of r.x and r.out when both are page-locked (mapped
-    // into the device's address space), else null
+    // device address of r.x when it is page-locked (mapped into the
+    // device's address space), else null
     const float* dx;
-    float* dout;
 };
 
-// One request of a batch as its gather / scatter kernels see it.
+// One request of a batch as its gather kernel sees it.
 struct IoEntry {
     const float* x;  // device address of the request's samples (host memory)
-    float* out;      // device address of its [S][F] output (host memory)
     int64_t n;
-    int64_t F;
 };
 
 // Copies request i's samples from page-locked host memory into row i of
-// the batch (and its length), reading them over the host link in place.
+// the batch (and its length), reading them over the host link in place
+// with 16-byte aligned float4 loads (a scalar head up to the source's
+// alignment, a scalar tail).
 __global__ void serve_gather(const IoEntry* __restrict__ tab, float* __restrict__ d_x, int64_t L,
                              int64_t* __restrict__ d_len) {
     const int i = blockIdx.y;
     const IoEntry e = tab[i];
     if (blockIdx.x == 0 && threadIdx.x == 0) d_len[i] = e.n;
     float* row = d_x + (int64_t)i * L;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < e.n;
-         t += (int64_t)gridDim.x * blockDim.x)
-        row[t] = e.x[t];
-}
-
-// Writes request i's valid frames, [S][F_i] of the batch's [S][F] rows,
-// straight into its page-locked host buffer.
-__global__ void serve_scatter(const IoEntry* __restrict__ tab, const float* __restrict__ d_out,
-                              int S, int64_t F) {
-    const int i = blockIdx.y;
-    const IoEntry e = tab[i];
-    const int64_t total = (int64_t)S * e.F;
-    const float* src = d_out + (int64_t)i * S * F;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t s = t / e.F;
-        e.out[t] = src[s * F + (t - s * e.F)];
+    const int64_t head = (int64_t)((16 - ((uintptr_t)e.x & 15)) & 15) / 4;
+    const int64_t h = head < e.n ? head : e.n;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t step = (int64_t)gridDim.x * blockDim.x;
+    if (t0 < h) row[t0] = e.x[t0];
+    const int64_t n4 = (e.n - h) / 4;
+    const float4* x4 = reinterpret_cast<const float4*>(e.x + h);
+    for (int64_t q = t0; q < n4; q += step) {
+        const float4 v = x4[q];
+        float* r = row + h + 4 * q;
+        r[0] = v.x;
+        r[1] = v.y;
+        r[2] = v.z;
+        r[3] = v.w;
     }
+    for (int64_t t = h + 4 * n4 + t0; t < e.n; t += step) row[t] = e.x[t];
 }
 
 struct Slot {
@@ -112,7 +109,7 @@ struct Slot {
     size_t out_cap = 0;
     int64_t* h_len = nullptr;  // page-locked
     size_t hlen_cap = 0;
-    IoEntry* h_tab = nullptr;  // page-locked, read by the gather / scatter kernels
+    IoEntry* h_tab = nullptr;  // page-locked, read by the gather kernel
     IoEntry* d_tab = nullptr;  // its device address
     size_t tab_cap = 0;
     bool busy = false;
@@ -303,19 +300,18 @@ struct cwth_server_s {
             if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&sl.d_tab, sl.h_tab, 0);
             if (e == cudaSuccess) sl.tab_cap = (size_t)cfg.max_batch;
         }
-        // Page-locked requests: one gather and one scatter kernel move the
-        // whole batch (no per-request copy call); others take one copy each
-        // way per request.
+        // Page-locked inputs: one gather kernel reads the whole batch's
+        // samples in place (no per-request upload call); others take one
+        // upload each.  Scalograms go back by one copy-engine transfer per
+        // request (measured faster than device stores into host memory).
         bool mapped = true;
-        for (const Pending& q : sl.io) mapped = mapped && q.dx && q.dout;
+        for (const Pending& q : sl.io) mapped = mapped && q.dx;
         if (mapped && e == cudaSuccess) {
-            int64_t nmax = 0, omax = 0;
+            int64_t nmax = 0;
             for (int32_t i = 0; i < b; ++i) {
                 const Pending& q = sl.io[i];
-                const int64_t Fi = (q.r.n + key.hop - 1) / key.hop;
-                sl.h_tab[i] = IoEntry{q.dx, q.dout, q.r.n, Fi};
+                sl.h_tab[i] = IoEntry{q.dx, q.r.n};
                 nmax = std::max(nmax, q.r.n);
-                omax = std::max(omax, (int64_t)key.S * Fi);
             }
             const int gx = (int)std::min<int64_t>(64, (nmax + 4095) / 4096);
             serve_gather<<<dim3(gx, b), 256, 0, sl.st>>>(sl.d_tab, sl.d_x, L, sl.d_len);
@@ -323,10 +319,14 @@ struct cwth_server_s {
             cwth_status st = e == cudaSuccess ? CWTH_OK : CWTH_ERR_CUDA;
             if (st == CWTH_OK)
                 st = cwth_execute(cp->plan, sl.d_x, L, sl.d_len, b, sl.d_out, sl.st);
-            if (st == CWTH_OK) {
-                const int ox = (int)std::min<int64_t>(128, (omax + 4095) / 4096);
-                serve_scatter<<<dim3(ox, b), 256, 0, sl.st>>>(sl.d_tab, sl.d_out, key.S, F);
-                if (cudaGetLastError() != cudaSuccess) st = CWTH_ERR_CUDA;
+            for (int32_t i = 0; i < b && st == CWTH_OK; ++i) {
+                const cwth_request& r = sl.reqs[i];
+                const int64_t Fi = (r.n + key.hop - 1) / key.hop;
+                if (cudaMemcpy2DAsync(r.out, sizeof(float) * (size_t)Fi,
+                                      sl.d_out + (size_t)i * key.S * (size_t)F,
+                                      sizeof(float) * (size_t)F, sizeof(float) * (size_t)Fi,
+                                      (size_t)key.S, cudaMemcpyDeviceToHost, sl.st) != cudaSuccess)
+                    st = CWTH_ERR_CUDA;
             }
             e = cudaEventRecord(sl.ev, sl.st);
             if (st == CWTH_OK && e != cudaSuccess) st = CWTH_ERR_CUDA;
@@ -463,18 +463,14 @@ cwth_status cwth_server_submit(cwth_server_t s, const cwth_request* reqs, int32_
             return CWTH_ERR_INVALID_ARG;
     }
     for (int32_t i = 0; i < n; ++i) {
-        Pending q{reqs[i], length_bucket(reqs[i].n), nullptr, nullptr};
+        Pending q{reqs[i], length_bucket(reqs[i].n), nullptr};
         if (!s->cfg.dry_run) {
-            // Page-locked buffers are read and written in place by the
-            // batch's gather / scatter kernels (their device addresses).
-            cudaPointerAttributes ax, ao;
+            // Page-locked samples are read in place by the batch's gather
+            // kernel (through their device address).
+            cudaPointerAttributes ax;
             if (cudaPointerGetAttributes(&ax, reqs[i].x) == cudaSuccess &&
-                ax.type == cudaMemoryTypeHost && ax.devicePointer &&
-                cudaPointerGetAttributes(&ao, reqs[i].out) == cudaSuccess &&
-                ao.type == cudaMemoryTypeHost && ao.devicePointer) {
+                ax.type == cudaMemoryTypeHost && ax.devicePointer)
                 q.dx = static_cast<const float*>(ax.devicePointer);
-                q.dout = static_cast<float*>(ao.devicePointer);
-            }
             cudaGetLastError();  // a pageable pointer may leave an error behind
         }
         s->pending.push_back(q);

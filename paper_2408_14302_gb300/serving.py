@@ -323,7 +323,8 @@ def summarize(results, wall):
 
 
 def library_replay(reqs, pinned_pool, out_ring, budget_bytes=40 * GiB, plan_cache_bytes=4 * GiB,
-                   max_batch=16, slots=4, precision="fp32", path="auto", dry_run=False):
+                   max_batch=16, slots=4, precision="fp32", path="auto", dry_run=False,
+                   server=None):
     """Replays `reqs` through the library's server (cwth_server_replay: the
     admission loop, batching, copies and launches all in C).  Each request's
     samples are read in place from `pinned_pool` (a page-locked torch tensor
@@ -331,7 +332,10 @@ def library_replay(reqs, pinned_pool, out_ring, budget_bytes=40 * GiB, plan_cach
     scalogram written into `out_ring` (a page-locked float32 tensor used as
     a ring: outputs of long-finished requests are overwritten).  Returns
     (summary dict, latencies in s, batch sizes).  dry_run: the server's
-    dry-run mode (no device work; any CPU tensors will do)."""
+    dry-run mode (no device work; any CPU tensors will do).  server: an
+    open cwth.Server to replay through (its plan cache carries over from
+    earlier replays); otherwise one is made from the other arguments and
+    closed afterwards."""
     from . import cwth
     n = len(reqs)
     arr = (cwth.Request * n)()
@@ -349,18 +353,25 @@ def library_replay(reqs, pinned_pool, out_ring, budget_bytes=40 * GiB, plan_cach
         arr[i] = cwth.Request(q.rid, base + 4 * (q.src * row + q.start), len(q.x), q.fs,
                               q.n_scales, q.hop, ring + 4 * off)
         off += m
-    with cwth.Server(budget_bytes=budget_bytes, plan_cache_bytes=plan_cache_bytes,
-                     max_batch=max_batch, slots=slots, precision=precision, path=path,
-                     dry_run=dry_run) as srv:
+    srv = server or cwth.Server(budget_bytes=budget_bytes, plan_cache_bytes=plan_cache_bytes,
+                                max_batch=max_batch, slots=slots, precision=precision, path=path,
+                                dry_run=dry_run)
+    try:
+        before = srv.stats()
         lat, bs, stat, wall = srv.replay(arr, np.array([q.arrival for q in reqs]))
         st = srv.stats()
+    finally:
+        if server is None:
+            srv.close()
     if np.any(stat != 0):
         raise RuntimeError(f"{int(np.sum(stat != 0))} requests failed: {sorted(set(stat.tolist()))}")
     lat_ms = lat * 1e3
     return ({"p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
-             "mean_batch": float(np.mean(bs)), "completed": int(st["completed"]), "wall_s": wall,
+             "mean_batch": float(np.mean(bs)),
+             "completed": int(st["completed"] - before["completed"]), "wall_s": wall,
              "peak_gb": st["peak_bytes"] / GiB, "plans": st["plans"],
-             "evictions": st["evictions"], "rejected": int(st["rejected"])}, lat, bs)
+             "evictions": int(st["evictions"] - before["evictions"]),
+             "rejected": int(st["rejected"] - before["rejected"])}, lat, bs)
 
 
 def main(argv=None):
@@ -375,7 +386,7 @@ def main(argv=None):
     ap.add_argument("--budget-gb", type=float, default=40.0)
     ap.add_argument("--plan-cache-gb", type=float, default=16.0)
     ap.add_argument("--max-batch", type=int, default=16)
-    ap.add_argument("--slots", type=int, default=4)
+    ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--engine", default="library", choices=["library", "python"])
     ap.add_argument("--forms", default="batched_auto_fp32,batched_auto_bf16x3,"
                     "per_clip_fp32_spectral")
@@ -393,21 +404,24 @@ def main(argv=None):
     for name, f in forms.items():
         mb = a.max_batch if f["batched"] else 1
         if a.engine == "library":
-            # warm: plans of the mix and the kernels, one pass of back-to-back requests
-            warm = poisson_requests(min(400, a.requests), 1e6, seed=4000, pool=pool)
-            library_replay(warm, pinned, ring, int(a.budget_gb * GiB),
-                           int(a.plan_cache_gb * GiB), mb, a.slots, f["precision"], f["path"])
+            from . import cwth
+            srv = cwth.Server(budget_bytes=int(a.budget_gb * GiB),
+                              plan_cache_bytes=int(a.plan_cache_gb * GiB), max_batch=mb,
+                              slots=a.slots, precision=f["precision"], path=f["path"])
+            # warm: the server's plans for the mix (they stay cached) and the
+            # kernels, one pass of back-to-back requests
+            warm = poisson_requests(min(1000, a.requests), 1e6, seed=4000, pool=pool)
+            library_replay(warm, pinned, ring, server=srv)
             for rate in [float(r) for r in a.rates.split(",")]:
                 reqs = poisson_requests(a.requests, rate, seed=5000 + int(rate), pool=pool)
                 torch.cuda.synchronize()
-                s, _, _ = library_replay(reqs, pinned, ring, int(a.budget_gb * GiB),
-                                         int(a.plan_cache_gb * GiB), mb, a.slots,
-                                         f["precision"], f["path"])
+                s, _, _ = library_replay(reqs, pinned, ring, server=srv)
                 audio = sum(r.audio_seconds for r in reqs)
                 s.update({"engine": "library", "form": name, "rate_req_s": rate,
                           "audio_sec_per_s": audio / s["wall_s"],
                           "offered_audio_sec_per_s": audio / reqs[-1].arrival})
                 print(json.dumps(s), flush=True)
+            srv.close()
             continue
         ex = GpuExecutor(slots=a.slots, precision=f["precision"], path=f["path"])
         ex.warm([16000.0], (32, 64, 128, 256), (32, 64, 128, 256, 512),

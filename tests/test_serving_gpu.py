@@ -45,8 +45,8 @@ def test_library_server_mix_equals_alone_and_oracle(precision, path, pinned):
     """The library's server (cwth_server_*): requests replayed at their
     arrival times in batches of one key give each request's scalogram as a
     plan of its own would (1e-5 of max|W|; the server derives the scales in
-    C) and match the float64 oracle.  Pageable buffers take one copy per
-    request; page-locked ones the batch's gather and scatter kernels."""
+    C) and match the float64 oracle.  Pageable inputs take one upload per
+    request; page-locked ones the batch's gather kernel."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     import oracle
@@ -81,3 +81,22 @@ def test_library_server_mix_equals_alone_and_oracle(precision, path, pinned):
         assert np.max(np.abs(got - alone)) <= 1e-5 * np.max(alone), q.rid
         ref = oracle.cwth_magnitude(q.x.astype(np.float64), sc, q.hop)
         assert np.max(np.abs(got - ref)) <= 1e-5 * np.max(ref), q.rid
+
+
+def test_library_server_reports_a_plan_it_cannot_build():
+    """A request whose plan the forced path cannot build (hop 11 on the
+    spectral path) completes with that plan's status; the requests around
+    it complete normally."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2408_14302_gb300 import cwth, signals
+    x = np.ascontiguousarray(signals.machine_clip(5, 8000), np.float32)
+    specs = [(0, 64), (1, 11), (2, 128)]
+    outs = [np.zeros((8, -(-len(x) // h)), np.float32) for _, h in specs]
+    arr = (cwth.Request * 3)(*[cwth.Request(rid, x.ctypes.data, len(x), 16000.0, 8, h,
+                                            o.ctypes.data) for (rid, h), o in zip(specs, outs)])
+    with cwth.Server(budget_bytes=1 << 32, max_batch=4, slots=2, precision="fp32",
+                     path="spectral") as srv:
+        lat, bs, stat, wall = srv.replay(arr, [0.0, 0.0, 0.0])
+    assert list(stat) == [0, 4, 0]
+    assert outs[0].max() > 0 and outs[2].max() > 0 and outs[1].max() == 0
