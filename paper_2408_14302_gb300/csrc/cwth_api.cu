@@ -1192,6 +1192,7 @@ namespace {
 cwth_status plan_create(const cwth_morlet* w, const double* scales, int32_t S, int32_t hop,
                         double sample_rate, int64_t max_len, int32_t precision, int32_t path,
                         int32_t seg_len, cwth_plan_t* out) {
+    cwth::NvtxRange nvtx_range("cwth_plan");
     if (out) *out = nullptr;
     if (!w || !scales || !out) return CWTH_ERR_INVALID_ARG;
     if (S < 1 || hop < 1 || max_len < 1) return CWTH_ERR_INVALID_ARG;
@@ -1303,6 +1304,7 @@ cwth_status cwth_plan_resampled(const cwth_morlet* w, const double* scales, int3
 
 cwth_status cwth_execute(cwth_plan_t p, const float* d_x, int64_t ld_x, const int64_t* d_lengths,
                          int32_t batch, float* d_out, void* stream) {
+    cwth::NvtxRange nvtx_range("cwth_execute");
     if (!valid_plan(p)) return CWTH_ERR_BAD_PLAN;
     if (batch < 0) return CWTH_ERR_INVALID_ARG;
     if (batch == 0) return CWTH_OK;
@@ -1316,6 +1318,7 @@ cwth_status cwth_execute(cwth_plan_t p, const float* d_x, int64_t ld_x, const in
 cwth_status cwth_execute_host(cwth_plan_t p, const float* h_x, int64_t ld_x,
                               const int64_t* h_lengths, int32_t batch, float* h_out,
                               void* stream) {
+    cwth::NvtxRange nvtx_range("cwth_execute_host");
     if (!valid_plan(p)) return CWTH_ERR_BAD_PLAN;
     if (batch < 0) return CWTH_ERR_INVALID_ARG;
     if (batch == 0) return CWTH_OK;
@@ -1650,6 +1653,7 @@ cwth_status cwth_batch_create(int32_t n, const cwth_plan_t* plans, const float* 
 }
 
 cwth_status cwth_batch_execute(cwth_batch_t b, void* stream) {
+    cwth::NvtxRange nvtx_range("cwth_batch_execute");
     if (!b || b->magic != (cwth::kPlanMagic ^ 0x5A5A5A5Au)) return CWTH_ERR_BAD_PLAN;
     DeviceGuard g(b->device);
     if (!g.ok) return CWTH_ERR_CUDA;

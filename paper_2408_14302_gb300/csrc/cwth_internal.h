@@ -10,9 +10,21 @@
 
 #include <algorithm>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "cwth.h"
 
 namespace cwth {
+
+// A named NVTX range for the duration of a scope (plan, execute, batch,
+// server launch), visible in timeline profilers; header-only NVTX v3, a
+// no-op unless a tool is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 constexpr uint32_t kPlanMagic = 0xC0A7B17Eu;
 // Spectral CTA shapes (64 registers per thread either way): two 512-thread

@@ -130,6 +130,7 @@ cwth_status cwth_execute_direct_noalloc(const cwth_morlet* w, const double* scal
                                         int32_t hop, int32_t precision, const float* d_x,
                                         int64_t ld_x, int64_t max_len, const int64_t* d_lengths,
                                         int32_t batch, float* d_out, void* stream) {
+    cwth::NvtxRange nvtx_range("cwth_execute_direct_noalloc");
     if (!w || !scales) return fail(CWTH_ERR_INVALID_ARG, "NULL wavelet or scale list");
     if (S < 1 || S > kMaxScales) return fail(CWTH_ERR_INVALID_ARG, "S must be in [1, 1024]");
     if (hop < 8 || hop % 8 != 0) return fail(CWTH_ERR_INVALID_ARG, "hop must be a positive multiple of 8");

@@ -266,6 +266,7 @@ struct cwth_server_s {
 
     cwth_status launch(Slot& sl, CachedPlan* cp, const Key& key, std::vector<Pending>& sel,
                        double bytes) {
+        cwth::NvtxRange nvtx_range("cwth_server_launch_batch");
         const int32_t b = (int32_t)sel.size();
         const int64_t L = key.bucket;
         const int64_t F = (L + key.hop - 1) / key.hop;

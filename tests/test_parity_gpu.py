@@ -404,3 +404,40 @@ def test_unsupported_hop_for_spectral(cw):
         with pytest.raises(cw.CwthError) as e:
             cw.Plan([2.0, 5.0], hop=hop, max_len=1000, path="spectral")
         assert e.value.status == 4
+
+
+def test_outputs_stay_inside_their_buffers(cw, sig):
+    """Guard bands: every path writes only inside its [batch][S][F_max]
+    output (a sentinel before and after it survives, as does the sentinel
+    in the frames past each clip) — the automatic float32 plan at hop 256
+    (folded and fused scales) and at hop 4 (several spectral parts, pruned
+    inverse FFTs), a tensor-core bf16x3 plan, an odd hop, and the host entry
+    point."""
+    n, G, sent = 30000, 4096, -7.0
+    xs = sig.machine_batch(3, n)
+    lengths = [n, 17001, 1]
+    sc = sig.scales_for_band(50, 8000, 24, 16000.0)
+    xd = torch.from_numpy(np.ascontiguousarray(xs, np.float32)).cuda()
+    ld = torch.tensor(lengths, dtype=torch.int64, device="cuda")
+    for hop, precision in ((256, "fp32"), (4, "fp32"), (64, "bf16x3"), (96, "fp32")):
+        with cw.Plan(sc, hop=hop, max_len=n, precision=precision) as plan:
+            F = plan.frames_max
+            size = 3 * len(sc) * F
+            big = torch.full((size + 2 * G,), sent, device="cuda")
+            out = big[G:G + size].view(3, len(sc), F)
+            plan.execute(xd, lengths=ld, out=out)
+            plan.sync()
+            h = big.cpu().numpy()
+            assert np.all(h[:G] == sent) and np.all(h[G + size:] == sent), (hop, precision)
+            o = out.cpu().numpy()
+            for i, L in enumerate(lengths):
+                assert np.all(o[i, :, -(-L // hop):] == sent), (hop, precision, i)
+            assert np.all(np.isfinite(o)) and o[0].max() > 0
+    with cw.Plan(sc, hop=128, max_len=n) as plan:
+        F = plan.frames_max
+        size = 3 * len(sc) * F
+        hbig = np.full(size + 2 * G, sent, np.float32)
+        hout = hbig[G:G + size].reshape(3, len(sc), F)
+        plan.execute_host(np.ascontiguousarray(xs, np.float32), hout)
+        assert np.all(hbig[:G] == sent) and np.all(hbig[G + size:] == sent)
+        assert np.all(np.isfinite(hout)) and hout.max() > 0
