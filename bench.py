@@ -54,14 +54,14 @@ def peaks():
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
     """Samples SM clock, power and clock-event reasons through NVML (ctypes)
-    every few ms while running; falls back to nothing if NVML is absent."""
+    every millisecond while running; falls back to nothing if NVML is absent."""
 
     REASONS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap",
                0x8: "hw_slowdown", 0x10: "sync_boost", 0x20: "sw_thermal_slowdown",
                0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown",
                0x100: "display_clock_setting"}
 
-    def __init__(self, device_index: int = 0, period_s: float = 0.005):
+    def __init__(self, device_index: int = 0, period_s: float = 0.001):
         self.samples = []
         self.period = period_s
         self._stop = threading.Event()
