@@ -526,6 +526,18 @@ int32_t cwth_server_poll(cwth_server_t s, cwth_completion *done, int32_t max_don
 cwth_status cwth_server_stats_query(cwth_server_t s, cwth_server_stats *st);
 
 /*
+ * Builds (or finds) the cached plan that requests of (fs, n_scales, hop)
+ * with up to n_max samples will use, for every slot when plans are kept
+ * per slot, so that the first such request does not wait for a plan.
+ * Cached plans count against the budget and may be evicted like any other
+ * (least recently used first when the plan cache is full).
+ * Errors: CWTH_ERR_INVALID_ARG for a NULL server or a field out of range;
+ * the plan's own error when the path cannot serve the key.
+ */
+cwth_status cwth_server_prepare(cwth_server_t s, double fs, int32_t n_scales, int32_t hop,
+                                int64_t n_max);
+
+/*
  * Device bytes a plan of the server holds for (fs, S, hop, bucket length):
  * its tables and workspaces (as cwth_plan_query reports table_bytes), the
  * figure the budget charges for it.  In dry-run mode an estimate from the

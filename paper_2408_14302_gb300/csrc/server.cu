@@ -494,6 +494,28 @@ int32_t cwth_server_poll(cwth_server_t s, cwth_completion* done, int32_t max_don
     return k;
 }
 
+cwth_status cwth_server_prepare(cwth_server_t s, double fs, int32_t n_scales, int32_t hop,
+                                int64_t n_max) {
+    if (!s || s->magic != kServerMagic || !(fs > 0) || n_scales < 1 || hop < 1 || n_max < 1)
+        return CWTH_ERR_INVALID_ARG;
+    cwth_request r;
+    memset(&r, 0, sizeof(r));
+    r.fs = fs;
+    r.n_scales = n_scales;
+    r.hop = hop;
+    r.n = n_max;
+    const Pending q{r, length_bucket(n_max), nullptr};
+    const bool per_slot = s->cfg.precision != CWTH_PREC_FP32 && s->cfg.path != CWTH_PATH_SPECTRAL;
+    const int nslots = per_slot ? (int)s->slots.size() : 1;
+    for (int slot = 0; slot < nslots; ++slot) {
+        Key key;
+        CachedPlan* cp = nullptr;
+        const cwth_status st = s->get_plan(q, slot, &key, &cp);
+        if (st != CWTH_OK) return st;
+    }
+    return CWTH_OK;
+}
+
 cwth_status cwth_server_stats_query(cwth_server_t s, cwth_server_stats* st) {
     if (!s || s->magic != kServerMagic || !st) return CWTH_ERR_INVALID_ARG;
     memset(st, 0, sizeof(*st));

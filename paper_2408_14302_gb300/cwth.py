@@ -30,7 +30,7 @@ EXPORTS = ("cwth_plan", "cwth_execute", "cwth_execute_host", "cwth_destroy",
            "cwth_batch_execute", "cwth_batch_items", "cwth_batch_destroy",
            "cwth_plan_reserve", "cwth_server_create", "cwth_server_submit", "cwth_server_poll",
            "cwth_server_stats_query", "cwth_server_plan_bytes", "cwth_server_replay",
-           "cwth_server_destroy")
+           "cwth_server_destroy", "cwth_server_prepare")
 
 
 class CwthError(RuntimeError):
@@ -163,6 +163,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                        ctypes.POINTER(ctypes.c_int32),
                                        ctypes.POINTER(ctypes.c_double)]
     lib.cwth_server_replay.restype = ctypes.c_int
+    lib.cwth_server_prepare.argtypes = [vp, dp, i32, i32, i64]
+    lib.cwth_server_prepare.restype = ctypes.c_int
     lib.cwth_server_destroy.argtypes = [vp]
     lib.cwth_server_destroy.restype = ctypes.c_int
     return lib
@@ -467,6 +469,12 @@ class Server:
         st = ServerStats()
         _check(_lib.cwth_server_stats_query(self._h, ctypes.byref(st)), "cwth_server_stats_query")
         return st.as_dict()
+
+    def prepare(self, fs, n_scales, hop, n_max):
+        """Builds the cached plan(s) requests of (fs, n_scales, hop) with up
+        to n_max samples will use (cwth_server_prepare)."""
+        _check(_lib.cwth_server_prepare(self._h, float(fs), int(n_scales), int(hop), int(n_max)),
+               "cwth_server_prepare")
 
     def plan_bytes(self, fs, n_scales, hop, bucket) -> float:
         return _lib.cwth_server_plan_bytes(self._h, float(fs), int(n_scales), int(hop), int(bucket))

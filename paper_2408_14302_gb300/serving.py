@@ -322,6 +322,22 @@ def summarize(results, wall):
             "completed": len(results), "wall_s": wall}
 
 
+def prepare_mix(server, fs=16000.0, scale_counts=(32, 64, 128, 256), hops=(32, 64, 128, 256, 512),
+                min_s=0.5, max_s=60.0):
+    """Builds the server's plans for every (scales, hop, length bucket) key
+    that poisson_requests with these parameters can produce."""
+    lo, hi = length_bucket(int(min_s * fs)), length_bucket(int(max_s * fs))
+    buckets = []
+    b = lo
+    while b <= hi:
+        buckets.append(b)
+        b *= 2
+    for S in scale_counts:
+        for hop in hops:
+            for b in buckets:
+                server.prepare(fs, S, hop, b)
+
+
 def library_replay(reqs, pinned_pool, out_ring, budget_bytes=40 * GiB, plan_cache_bytes=4 * GiB,
                    max_batch=16, slots=4, precision="fp32", path="auto", dry_run=False,
                    server=None):
@@ -408,8 +424,11 @@ def main(argv=None):
             srv = cwth.Server(budget_bytes=int(a.budget_gb * GiB),
                               plan_cache_bytes=int(a.plan_cache_gb * GiB), max_batch=mb,
                               slots=a.slots, precision=f["precision"], path=f["path"])
-            # warm: the server's plans for the mix (they stay cached) and the
-            # kernels, one pass of back-to-back requests
+            # warm: the server's plans for every key of the mix (shared
+            # float32 plans: 4 scale counts x 5 hops x 7 length buckets; they
+            # stay cached), then one pass of back-to-back requests
+            if f["precision"] == "fp32":
+                prepare_mix(srv)
             warm = poisson_requests(min(1000, a.requests), 1e6, seed=4000, pool=pool)
             library_replay(warm, pinned, ring, server=srv)
             for rate in [float(r) for r in a.rates.split(",")]:

@@ -132,3 +132,22 @@ def test_server_rejects_bad_arguments(cw):
         bad = (cw.Request * 1)(cw.Request(0, None, 10, 16000.0, 8, 64, None))
         assert lib.cwth_server_submit(srv._h, bad, 1) == 1
         assert srv.stats()["pending"] == 0
+
+
+def test_prepare_builds_the_plan_a_request_will_use(cw):
+    keep = []
+    with cw.Server(budget_bytes=1e12, max_batch=4, slots=3, dry_run=True) as srv:
+        srv.prepare(16000.0, 16, 64, 1000)
+        st = srv.stats()
+        assert st["plans"] == 1 and st["plan_bytes"] == pytest.approx(
+            srv.plan_bytes(16000.0, 16, 64, 1 << 14))
+        srv.submit(_requests(cw, [(0, 900, 16, 64), (1, 16000, 16, 64)], keep))
+        assert len(_drain(srv, 2)) == 2
+        assert srv.stats()["plans"] == 1   # same key and bucket: no new plan
+    with cw.Server(budget_bytes=1e12, max_batch=4, slots=3, precision="bf16x3",
+                   dry_run=True) as srv:
+        srv.prepare(16000.0, 16, 64, 1000)
+        assert srv.stats()["plans"] == 3   # bf16 staging: one plan per slot
+    with cw.Server(dry_run=True) as srv:
+        with pytest.raises(cw.CwthError):
+            srv.prepare(16000.0, 0, 64, 1000)
