@@ -210,6 +210,20 @@ cwth_status cwth_execute_host(cwth_plan_t plan, const float *h_x, int64_t ld_x,
 cwth_status cwth_plan_set_host_chunks(cwth_plan_t plan, int32_t n);
 
 /*
+ * Pass plan of the spectral path's inverse FFTs (an autotuner's knob; the
+ * result agrees with any other plan within the float32 tolerance):
+ * radix 0 restores the plan's cost-model choice, 16 takes radix-16 passes
+ * (with a leading 8 / 4), 8 takes radix-8 passes (with a leading 4 / 4,4),
+ * which keeps more warps busy when a pass holds few points.  Applies to
+ * every spectral part of the plan; later executes use it.
+ * Errors: CWTH_ERR_BAD_PLAN; CWTH_ERR_INVALID_ARG for another radix;
+ * CWTH_ERR_UNSUPPORTED for 8 when a part's passes cannot take it (pruned
+ * inverse FFTs, 1024-thread segments, or more points per pass than eight
+ * per thread).
+ */
+cwth_status cwth_plan_set_inverse_radix(cwth_plan_t plan, int32_t radix);
+
+/*
  * Sizes a plan's growable device workspaces for batches of up to `batch`
  * clips, so that later cwth_execute calls with batch' <= batch allocate
  * nothing (and, with host != 0, cwth_execute_host calls with batch' <= batch
@@ -282,6 +296,9 @@ typedef struct {
                                   (the other fields describe the part with
                                   the largest scales), 1, or 0 without
                                   spectral scales                            */
+    int32_t inverse_radix;     /* main radix of the spectral inverse FFTs'
+                                  pass plan (16, or 8 for the radix-8 plan),
+                                  0 without folded scales                    */
 } cwth_plan_info;
 
 /* Fill *info.  Errors: CWTH_ERR_BAD_PLAN, CWTH_ERR_INVALID_ARG (NULL info). */

@@ -13,7 +13,7 @@ Two modes:
   the work list cannot take (small hops, whose plans prune their inverse
   FFTs, or 1024-thread segments) run as their own executes beside it.  The
   autotuner picks each group's FFT segment length (the cost model's, half
-  or twice it).
+  or twice it) and its inverse FFTs' pass plan (radix 16 or 8).
 * "graph": each group runs as its own `cwth_execute` (any path and
   precision, e.g. the tensor-core split-bf16 path) and all groups' executes
   are captured in one CUDA graph.  Its autotuner also tries the automatic
@@ -157,23 +157,29 @@ class BatchRunner:
                                          for g in wl])
 
     # ------------------------------------------------------------ planning
-    def _plan(self, g, path, precision, seg_len=0):
+    def _plan(self, g, path, precision, seg_len=0, radix=0):
         gfs, S, hop = g["key"]
-        return cwth.Plan(g["scales"], hop=hop, max_len=g["max_len"], bandwidth=self.bandwidth,
-                         center=self.center, sample_rate=gfs, precision=precision, path=path,
-                         seg_len=seg_len)
+        p = cwth.Plan(g["scales"], hop=hop, max_len=g["max_len"], bandwidth=self.bandwidth,
+                      center=self.center, sample_rate=gfs, precision=precision, path=path,
+                      seg_len=seg_len)
+        if radix:
+            p.set_inverse_radix(radix)
+        return p
 
     def _choose(self, g, gpu):
-        """(path, precision, seg_len) of the group: cached, else the fastest
-        candidate; the spectral path also tries half and twice the segment
-        length its cost model picks."""
+        """(path, precision, seg_len, inverse radix) of the group: cached,
+        else the fastest candidate; the spectral path also tries half and
+        twice the segment length its cost model picks, and each float32
+        plan the other inverse-FFT pass plan (radix 8 / 16) where it can
+        take it."""
         gfs, S, hop = g["key"]
         key = (f"{gpu}|{gfs:g}|{S}|{hop}|{length_bucket(g['max_len'])}|{self.accuracy}"
                f"|{self.mode}")
         if self.cache is not None:
             hit = self.cache.get(key)
             if hit:
-                return hit["path"], hit["precision"], int(hit.get("seg_len", 0))
+                return (hit["path"], hit["precision"], int(hit.get("seg_len", 0)),
+                        int(hit.get("radix", 0)))
         best = None
         cands = WORKLIST_CANDIDATES if self.mode == "worklist" else CANDIDATES[self.accuracy]
         for path, prec in cands:
@@ -189,16 +195,25 @@ class BatchRunner:
                         info["seg_len"] > 0:
                     segs = [m for m in (info["seg_len"] // 2, info["seg_len"] * 2)
                             if 512 <= m <= 32768]
-                ms = self._time(plan, g)
+                radices = [0]
+                if prec == "fp32" and info["inverse_radix"]:
+                    radices.append(8 if info["inverse_radix"] == 16 else 16)
+                for radix in radices:
+                    if radix:
+                        try:
+                            plan.set_inverse_radix(radix)
+                        except cwth.CwthError:
+                            continue
+                    ms = self._time(plan, g)
+                    if best is None or ms < best[4]:
+                        best = (path, prec, seg, radix, ms)
                 plan.close()
-                if best is None or ms < best[3]:
-                    best = (path, prec, seg, ms)
         if best is None:
             raise cwth.CwthError(4, f"no evaluation serves group {g['key']}")
         if self.cache is not None:
             self.cache.put(key, {"path": best[0], "precision": best[1], "seg_len": best[2],
-                                 "ms": best[3]})
-        return best[0], best[1], best[2]
+                                 "radix": best[3], "ms": best[4]})
+        return best[0], best[1], best[2], best[3]
 
     def _time(self, plan, g, reps: int = 3) -> float:
         torch = self.torch

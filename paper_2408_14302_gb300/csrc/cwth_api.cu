@@ -766,8 +766,13 @@ cwth_status build_spectral(cwth_plan_s* p) {
     // Decided once per plan, for its largest pass, so that every launch (any
     // scale grouping, any host chunk) runs the same inverse FFTs and gives
     // the same bytes.
-    p->inv_r8 = inverse_fft_radix8(
-        p->P, spectral_nconc(p->M, p->P, p->n_sp, threads, fd_bytes(p)), threads, p->spec_prune);
+    {
+        const int nc = spectral_nconc(p->M, p->P, p->n_sp, threads, fd_bytes(p));
+        p->inv_r8 = inverse_fft_radix8(p->P, nc, threads, p->spec_prune);
+        p->inv_r8_model = p->inv_r8;
+        p->inv_r8_ok = !p->spec_prune && threads == cwth::kSpecThreadsPair &&
+                       (int64_t)nc * p->P <= 8 * (int64_t)threads;
+    }
     const size_t ntw = (size_t)cwth::spectral_twiddle_entries(p->M);
     e = cudaMalloc(&p->d_tw, sizeof(float2) * ntw);
     if (e != cudaSuccess) return cuda_status(e);
@@ -1442,6 +1447,16 @@ cwth_status cwth_plan_set_host_chunks(cwth_plan_t p, int32_t chunks) {
     return CWTH_OK;
 }
 
+cwth_status cwth_plan_set_inverse_radix(cwth_plan_t p, int32_t radix) {
+    if (!valid_plan(p)) return CWTH_ERR_BAD_PLAN;
+    if (radix != 0 && radix != 8 && radix != 16) return CWTH_ERR_INVALID_ARG;
+    for (const cwth_plan_s* q = p; q; q = q->child)
+        if (radix == 8 && q->n_sp > 0 && !q->inv_r8_ok) return CWTH_ERR_UNSUPPORTED;
+    for (cwth_plan_s* q = p; q; q = q->child)
+        q->inv_r8 = q->n_sp > 0 && (radix == 0 ? q->inv_r8_model : radix == 8);
+    return CWTH_OK;
+}
+
 cwth_status cwth_destroy(cwth_plan_t p) {
     if (!p) return CWTH_OK;
     if (!valid_plan(p)) return CWTH_ERR_BAD_PLAN;
@@ -1485,6 +1500,7 @@ cwth_status cwth_plan_query(cwth_plan_t p, cwth_plan_info* info) {
         if (nc > 1) nc &= ~1;  // passes hold whole fold pairs (see spectral_record)
         info->spectral_pass_scales = nc;
         info->spectral_pruned = p->spec_prune ? 1 : 0;
+        info->inverse_radix = p->n_sp > 0 ? (p->inv_r8 ? 8 : 16) : 0;
     }
     const int64_t xparts = p->x_elems ? (p->d_xlo2 ? 3 : 2) : 0;
     info->workspace_bytes = (int64_t)(p->x_elems * xparts * sizeof(__nv_bfloat16) +

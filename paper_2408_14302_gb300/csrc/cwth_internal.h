@@ -272,6 +272,8 @@ struct cwth_plan_s {
     int32_t M = 0, P = 0, halo = 0, kp0 = 0, seg_frames = 0, n_seg = 0;
     bool spec_prune = false;  // narrow bands let inverse FFTs skip passes
     bool inv_r8 = false;      // inverse FFTs on the radix-8 plan
+    bool inv_r8_model = false;  // the cost model's choice (cwth_plan_set_inverse_radix 0)
+    bool inv_r8_ok = false;     // the radix-8 plan can serve every pass of the plan
     int32_t fft_d = 1, fft_n2 = 0;  // forward FFT: fft_d column FFTs of fft_n2 points
     double seg_cost = 0;      // cost model's lane operations per segment
     int32_t seg_force = 0;    // segment length fixed by cwth_plan_segment (0: cost model)

@@ -30,7 +30,7 @@ EXPORTS = ("cwth_plan", "cwth_execute", "cwth_execute_host", "cwth_destroy",
            "cwth_batch_execute", "cwth_batch_items", "cwth_batch_destroy",
            "cwth_plan_reserve", "cwth_server_create", "cwth_server_submit", "cwth_server_poll",
            "cwth_server_stats_query", "cwth_server_plan_bytes", "cwth_server_replay",
-           "cwth_server_destroy", "cwth_server_prepare")
+           "cwth_server_destroy", "cwth_server_prepare", "cwth_plan_set_inverse_radix")
 
 
 class CwthError(RuntimeError):
@@ -86,7 +86,7 @@ class PlanInfo(ctypes.Structure):
                 ("resample", ctypes.c_int32), ("spectral_threads", ctypes.c_int32),
                 ("spectral_pass_scales", ctypes.c_int32), ("spectral_pruned", ctypes.c_int32),
                 ("num_fused", ctypes.c_int32), ("workspace_bytes", ctypes.c_int64),
-                ("spectral_parts", ctypes.c_int32)]
+                ("spectral_parts", ctypes.c_int32), ("inverse_radix", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -111,6 +111,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.cwth_execute_host.restype = ctypes.c_int
     lib.cwth_plan_set_host_chunks.argtypes = [vp, i32]
     lib.cwth_plan_set_host_chunks.restype = ctypes.c_int
+    lib.cwth_plan_set_inverse_radix.argtypes = [vp, i32]
+    lib.cwth_plan_set_inverse_radix.restype = ctypes.c_int
     lib.cwth_plan_reserve.argtypes = [vp, i32, i64, i32]
     lib.cwth_plan_reserve.restype = ctypes.c_int
     lib.cwth_selftest_wait_timeout.argtypes = [vp, i64, vp]
@@ -336,6 +338,12 @@ class Plan:
     def set_host_chunks(self, n: int):
         """Chunks of execute_host (0 = automatic); see cwth_plan_set_host_chunks."""
         _check(_lib.cwth_plan_set_host_chunks(self._h, int(n)), "cwth_plan_set_host_chunks")
+
+    def set_inverse_radix(self, radix: int):
+        """Inverse-FFT pass plan of the spectral path: 0 (cost model), 8 or
+        16; see cwth_plan_set_inverse_radix."""
+        _check(_lib.cwth_plan_set_inverse_radix(self._h, int(radix)),
+               "cwth_plan_set_inverse_radix")
 
     def reserve(self, batch: int, ld_x: int = 0, host: bool = False):
         """Sizes the plan's growable workspaces for `batch` clips so later

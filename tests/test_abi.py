@@ -106,6 +106,7 @@ def test_null_plan_handles(cw):
     assert lib.cwth_execute_host(None, None, 0, None, 0, None, None) == 6
     assert lib.cwth_plan_set_host_chunks(None, 2) == 6
     assert lib.cwth_plan_reserve(None, 4, 0, 0) == 6
+    assert lib.cwth_plan_set_inverse_radix(None, 8) == 6
     # (a NULL plan there names the allocation-free entry point's status
     # word, which needs a device; a budget out of range is refused first)
     assert lib.cwth_selftest_wait_timeout(None, 0, None) == 1

@@ -50,10 +50,12 @@ def test_alone_equals_in_the_mix(batch):
     runner, clips, fs, ns, hs, _ = batch
     for i in (0, 5, 11):
         gi, _ = runner.where[i]
-        path, prec, seg = runner.groups[gi]["choice"]
+        path, prec, seg, radix = runner.groups[gi]["choice"]
         sc = signals.scales_for_band(50.0, 8000.0, ns[i], fs[i])
         with cwth.Plan(sc, hop=hs[i], max_len=len(clips[i]), sample_rate=fs[i], path=path,
                        precision=prec, seg_len=seg) as p:
+            if radix:
+                p.set_inverse_radix(radix)
             alone = p.execute(torch.from_numpy(np.asarray(clips[i], np.float32)).cuda())[0]
             alone = alone.cpu().numpy()
         mixed = runner.result(i)

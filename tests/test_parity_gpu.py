@@ -441,3 +441,32 @@ def test_outputs_stay_inside_their_buffers(cw, sig):
         plan.execute_host(np.ascontiguousarray(xs, np.float32), hout)
         assert np.all(hbig[:G] == sent) and np.all(hbig[G + size:] == sent)
         assert np.all(np.isfinite(hout)) and hout.max() > 0
+
+
+def test_inverse_radix_knob(cw, sig):
+    """cwth_plan_set_inverse_radix: radix-8 and radix-16 inverse-FFT pass
+    plans give the same scalogram within the float32 tolerance (and the
+    oracle's); 0 restores the model's choice; a pruned plan refuses 8."""
+    n, hop = 30000, 256
+    xs = sig.machine_batch(2, n)
+    sc = sig.scales_for_band(50, 8000, 24, 16000.0)
+    xd = torch.from_numpy(np.ascontiguousarray(xs, np.float32)).cuda()
+    with cw.Plan(sc, hop=hop, max_len=n) as p:
+        model = p.info()["inverse_radix"]
+        assert model in (8, 16)
+        outs = {}
+        for r in (8, 16):
+            p.set_inverse_radix(r)
+            assert p.info()["inverse_radix"] == r
+            outs[r] = p.execute(xd).cpu().numpy().astype(np.float64)
+        p.set_inverse_radix(0)
+        assert p.info()["inverse_radix"] == model
+    for i in range(2):
+        assert rel_err(outs[8][i], outs[16][i]) <= TOL_FP32
+        assert rel_err(outs[8][i], oracle_mag(xs[i], sc, hop)) <= TOL_FP32
+    with cw.Plan(sc, hop=1, max_len=4000) as p1:
+        assert p1.info()["spectral_pruned"] == 1
+        with pytest.raises(cw.CwthError) as e:
+            p1.set_inverse_radix(8)
+        assert e.value.status == 4
+        p1.set_inverse_radix(16)
