@@ -433,14 +433,17 @@ def test_outputs_stay_inside_their_buffers(cw, sig):
             for i, L in enumerate(lengths):
                 assert np.all(o[i, :, -(-L // hop):] == sent), (hop, precision, i)
             assert np.all(np.isfinite(o)) and o[0].max() > 0
-    with cw.Plan(sc, hop=128, max_len=n) as plan:
-        F = plan.frames_max
-        size = 3 * len(sc) * F
-        hbig = np.full(size + 2 * G, sent, np.float32)
-        hout = hbig[G:G + size].reshape(3, len(sc), F)
-        plan.execute_host(np.ascontiguousarray(xs, np.float32), hout)
-        assert np.all(hbig[:G] == sent) and np.all(hbig[G + size:] == sent)
-        assert np.all(np.isfinite(hout)) and hout.max() > 0
+    for hop in (128, 96):
+        with cw.Plan(sc, hop=hop, max_len=n) as plan:
+            F = plan.frames_max
+            size = 3 * len(sc) * F
+            hbig = np.full(size + 2 * G, sent, np.float32)
+            hout = hbig[G:G + size].reshape(3, len(sc), F)
+            plan.execute_host(np.ascontiguousarray(xs, np.float32), hout)
+            assert np.all(hbig[:G] == sent) and np.all(hbig[G + size:] == sent), hop
+            assert np.all(np.isfinite(hout)) and hout.max() > 0
+            dev = plan.execute(xd).cpu().numpy()
+            assert np.array_equal(dev, hout), hop
 
 
 def test_inverse_radix_knob(cw, sig):
