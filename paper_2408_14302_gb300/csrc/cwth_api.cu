@@ -826,7 +826,10 @@ cwth_status split_spectral(cwth_plan_s* p) {
         if (!choose_segment(*p, sp, fd_h, &one)) break;
         double best = one.cost;
         size_t best_j = 0;
-        for (size_t j = 1; j < sp.size(); ++j) {
+        // At most ~128 candidate split points (plan time grows with their
+        // number times the scale count).
+        const size_t step = std::max<size_t>(1, sp.size() / 128);
+        for (size_t j = step; j < sp.size(); j += step) {
             const std::vector<double> a(sp.begin(), sp.begin() + j), b(sp.begin() + j, sp.end());
             SegChoice ca, cb;
             if (!choose_segment(*p, a, none, &ca) || !choose_segment(*p, b, fd_h, &cb)) continue;
