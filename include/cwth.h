@@ -96,8 +96,10 @@ enum {
  * positive, or an unknown flag; CWTH_ERR_UNSUPPORTED when the forced path
  * cannot serve the request (the spectral path needs hop = 2^e d with d a
  * product of 3, 5 and 7 no larger than 27, e.g. 3, 96 or 100, and
- * hop <= 2048; the direct path needs hop % 8 == 0 for bf16 operands and at
- * most 4096 taps);
+ * hop <= 2048, and a segment of at most 16384 samples with M / hop <= 8192
+ * must hold a valid frame beside the largest scale's support: about
+ * a <= 1390 samples at hops >= 2, a <= 690 at hop 1; the direct path needs
+ * hop % 8 == 0 for bf16 operands and at most 4096 taps);
  * CWTH_ERR_OOM / CWTH_ERR_CUDA otherwise.  On error *out is set to NULL.
  */
 cwth_status cwth_plan(const cwth_morlet *w, const double *scales, int32_t S, int32_t hop,
