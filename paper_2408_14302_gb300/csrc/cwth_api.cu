@@ -157,7 +157,7 @@ void band_limits(double a, double B, double C, int M, int64_t* q_lo, int64_t* q_
     *q_hi = (int64_t)ceil((double)M * (C + delta) / a);
 }
 
-// Pass plan of the spectral kernel's FFTs (the device's fft_radix): with
+// Pass plan of the spectral kernel's FFTs (the device's ct_radix): with
 // 16 points per thread (512-thread CTAs) radix 16 and a leading 8, 4 or
 // 8,4; with 8, radix 8 and a leading 4 or 4,4.
 std::vector<int> spectral_fft_radices(int L, int threads) {

@@ -247,71 +247,14 @@ __device__ __forceinline__ void fft_pass(float2* __restrict__ buf, int L, int nb
     __syncthreads();
 }
 
-template <int R, bool INV, int PPT, bool BC = false>
-__device__ __forceinline__ void fft_pass_dispatch(float2* buf, int L, int nbatch, int Ns,
-                                                  const TwTab& tw, int tstride, bool rs, bool ws) {
-    const int nb = nbatch * (L / R);
-    const int per = (nb + blockDim.x - 1) / blockDim.x;
-    // Up to PPT complex values per thread: the caller keeps nbatch * L <=
-    // kMaxFftPoints = PPT * blockDim.x.
-    constexpr int kMaxB = PPT / R;
-    if (per <= 1 || kMaxB <= 1)
-        fft_pass<R, 1, INV, BC>(buf, L, nbatch, Ns, tw, tstride, rs, ws);
-    else if (per <= 2 || kMaxB <= 2)
-        fft_pass<R, 2, INV, BC>(buf, L, nbatch, Ns, tw, tstride, rs, ws);
-    else if (per <= 4 || kMaxB <= 4)
-        fft_pass<R, (kMaxB < 4 ? kMaxB : 4), INV, BC>(buf, L, nbatch, Ns, tw, tstride, rs, ws);
-    else
-        fft_pass<R, kMaxB, INV, BC>(buf, L, nbatch, Ns, tw, tstride, rs, ws);
-}
-
-// Radix of pass i of a transform of 2^e points.  With 16 or more points
-// per thread: 16 where possible, the remainder of e as a leading 8, 4 or
-// 8,4 (8192 points: 8,4,16,16); with fewer: 8 where possible, a leading 4
-// (or 4,4).
-template <int PPT>
-__device__ __forceinline__ int fft_radix(int e, int i) {
-    if constexpr (PPT >= 16) {
-        const int m = e & 3;
-        const int n8 = (m == 3 || m == 1) ? 1 : 0;
-        const int n4 = (m == 2 || m == 1) ? 1 : 0;
-        return i < n8 ? 8 : (i < n8 + n4 ? 4 : 16);
-    } else {
-        const int n4 = (e % 3 == 1) ? 2 : (e % 3 == 2) ? 1 : 0;
-        return i < n4 ? 4 : 8;
-    }
-}
-
-template <int PPT>
-__device__ __forceinline__ int fft_npass(int e) {
-    if constexpr (PPT >= 16) {
-        const int m = e & 3;
-        const int n8 = (m == 3 || m == 1) ? 1 : 0;
-        const int n4 = (m == 2 || m == 1) ? 1 : 0;
-        return n8 + n4 + (e - 3 * n8 - 2 * n4) / 4;
-    } else {
-        const int n4 = (e % 3 == 1) ? 2 : (e % 3 == 2) ? 1 : 0;
-        return n4 + (e - 2 * n4) / 3;
-    }
-}
-
-template <bool INV, int PPT, bool BC>
-__device__ __forceinline__ void fft_pass_radix(int R, float2* buf, int L, int nbatch, int Ns,
-                                               const TwTab& tw, int ts, bool rs, bool ws) {
-    if (R == 4) {
-        fft_pass_dispatch<4, INV, PPT, BC>(buf, L, nbatch, Ns, tw, ts * (L / (Ns * 4)), rs, ws);
-    } else if (R == 8) {
-        fft_pass_dispatch<8, INV, PPT, BC>(buf, L, nbatch, Ns, tw, ts * (L / (Ns * 8)), rs, ws);
-    } else if constexpr (PPT >= 16) {
-        fft_pass_dispatch<16, INV, PPT, BC>(buf, L, nbatch, Ns, tw, ts * (L / (Ns * 16)), rs, ws);
-    }
-}
-
 // The forward FFT's pass sequence unrolled at compile time for each
 // transform length: every pass's radix, stride, butterflies per thread and
 // layouts are constants, and no run-time pass loop holds registers across
 // passes (the run-time loop spills under the 64-register bound of the
-// paired shape; each pass alone does not).  Same plans as fft_radix.
+// paired shape; each pass alone does not).  Plans: with 16 or more points
+// per thread radix 16 where possible, the remainder of the exponent as a
+// leading 8, 4 or 8,4 (8192 points: 8,4,16,16); with fewer, radix 8 and a
+// leading 4 or 4,4.
 __host__ __device__ constexpr int ct_npass(int ppt, int e) {
     return ppt >= 16 ? ((e & 3) == 3 || (e & 3) == 1 ? 1 : 0) + ((e & 3) == 2 || (e & 3) == 1 ? 1 : 0) +
                            (e - 3 * ((e & 3) == 3 || (e & 3) == 1 ? 1 : 0) -
@@ -506,7 +449,7 @@ __device__ __forceinline__ void fft_many_pass(float2* buf, int L, int nbatch, in
                                          i + 1 < np);
 }
 
-// nbatch transforms of L points (the plan's radices, as fft_radix): the
+// nbatch transforms of L points (the plan's radices, as ct_radix): the
 // leading radix-8 / radix-4 passes in line, then a loop whose body is the
 // plan's main radix alone (a loop over every radix holds too many registers
 // for the 64-register bound of the paired shape).
@@ -537,72 +480,6 @@ __device__ __forceinline__ void fft_many(float2* buf, int L, int nbatch, const T
             fft_many_pass<4, CAP, INV, PRUNE>(buf, L, nbatch, Ns, tw, ts, i, np, i0);
         for (; i < np; ++i, Ns *= 8)
             fft_many_pass<8, CAP, INV, PRUNE>(buf, L, nbatch, Ns, tw, ts, i, np, i0);
-    }
-}
-
-// Batched power-of-two FFT in shared memory, natural order in and out.
-// ts = M / L maps the transform's twiddles onto the table of exp(-2 pi i m/M).
-// PRUNE: every input is zero from index wmax on, so the leading passes
-// whose radices multiply to at most L / wmax (all but the last, at most)
-// are skipped and the next pass reads their result directly (see BC).
-// R8: the radix-8 plan (radix 8 with a leading 4 or 4, 4) whatever the
-// points per thread (PPT bounds only the butterflies a thread holds).
-template <bool INV, int PPT, bool PRUNE = false, bool R8 = false>
-__device__ __forceinline__ void fft_block(float2* buf, int L, int nbatch, const TwTab& tw, int ts,
-                                          int wmax = 0) {
-    constexpr int PLAN = R8 ? 8 : PPT;
-    const int e = __ffs(L) - 1;  // L >= 8: the plan keeps P = M/H >= 8 and M/2 >= 256
-    int Ns = 1;
-    if constexpr (PRUNE) {
-        const int npass = fft_npass<PLAN>(e);
-        int i = 0;
-        while (i + 1 < npass && (int64_t)wmax * Ns * fft_radix<PLAN>(e, i) <= L)
-            Ns *= fft_radix<PLAN>(e, i++);
-        if (i > 0) {
-            const int R = fft_radix<PLAN>(e, i);
-            fft_pass_radix<INV, PPT, true>(R, buf, L, nbatch, Ns, tw, ts, false, i + 1 < npass);
-            Ns *= R;
-            ++i;
-        }
-        for (; i < npass; ++i) {
-            const int R = fft_radix<PLAN>(e, i);
-            fft_pass_radix<INV, PPT, false>(R, buf, L, nbatch, Ns, tw, ts, i > 0, i + 1 < npass);
-            Ns *= R;
-        }
-    } else if constexpr (PLAN >= 16) {
-        // The same plan as fft_radix, with the passes unrolled by kind
-        // (measured faster than dispatching on the radix at run time).
-        const int m = e & 3;
-        const int n8 = (m == 3 || m == 1) ? 1 : 0;
-        const int n4 = (m == 2 || m == 1) ? 1 : 0;
-        const int npass = n8 + n4 + (e - 3 * n8 - 2 * n4) / 4;
-        for (int i = 0; i < npass; ++i) {
-            const bool rs = i > 0, ws = i + 1 < npass;
-            if (i < n8) {
-                fft_pass_dispatch<8, INV, PPT>(buf, L, nbatch, Ns, tw, ts * (L / (Ns * 8)), rs, ws);
-                Ns *= 8;
-            } else if (i < n8 + n4) {
-                fft_pass_dispatch<4, INV, PPT>(buf, L, nbatch, Ns, tw, ts * (L / (Ns * 4)), rs, ws);
-                Ns *= 4;
-            } else {
-                fft_pass_dispatch<16, INV, PPT>(buf, L, nbatch, Ns, tw, ts * (L / (Ns * 16)), rs,
-                                                ws);
-                Ns *= 16;
-            }
-        }
-    } else {
-        const int n4 = (e % 3 == 1) ? 2 : (e % 3 == 2) ? 1 : 0;
-        const int npass = n4 + (e - 2 * n4) / 3;
-        for (int i = 0; i < npass; ++i) {
-            const bool rs = i > 0, ws = i + 1 < npass;
-            if (i < n4) {
-                fft_pass_dispatch<4, INV, PPT>(buf, L, nbatch, Ns, tw, ts * (L / (Ns * 4)), rs, ws);
-                Ns *= 4;
-            } else {
-                fft_pass_dispatch<8, INV, PPT>(buf, L, nbatch, Ns, tw, ts * (L / (Ns * 8)), rs, ws);
-                Ns *= 8;
-            }
-        }
     }
 }
 
