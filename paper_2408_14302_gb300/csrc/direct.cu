@@ -65,12 +65,14 @@ __device__ __forceinline__ float sqrt_approx(float v) {
 // part 1) (the differences are exact in float32).  Row b = batch is the
 // zero tail after the last clip.  Each thread writes 8 consecutive bf16
 // (one 16-byte store per buffer); rows and the tail are multiples of 8
-// elements long.  Null part buffers are not written.
+// elements long.  Null part buffers are not written.  vec: x, ld_x and
+// h_front keep every 8-element source run of a row 16-byte aligned, so runs
+// wholly inside the clip are read as two float4 loads.
 __global__ void stage_bf16_kernel(const float* __restrict__ x, int64_t ld_x,
                                   const int64_t* __restrict__ lengths, int64_t max_len, int batch,
                                   __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo,
                                   __nv_bfloat16* __restrict__ lo2, int64_t lpad, int64_t h_front,
-                                  int64_t total) {
+                                  int64_t total, bool vec) {
     const int b = blockIdx.y;
     const int64_t row_len = b < batch ? lpad : total - (int64_t)batch * lpad;
     int64_t len = 0;
@@ -83,14 +85,23 @@ __global__ void stage_bf16_kernel(const float* __restrict__ x, int64_t ld_x,
     for (int64_t j0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 8; j0 < row_len;
          j0 += (int64_t)gridDim.x * blockDim.x * 8) {
         uint32_t wh[4], wl[4], w2[4];
+        float xv[8];
+        const int64_t n0 = j0 - h_front;
+        if (vec && n0 >= 0 && n0 + 8 <= len) {
+            const float4 a = __ldg(reinterpret_cast<const float4*>(xr + n0));
+            const float4 c = __ldg(reinterpret_cast<const float4*>(xr + n0 + 4));
+            xv[0] = a.x, xv[1] = a.y, xv[2] = a.z, xv[3] = a.w;
+            xv[4] = c.x, xv[5] = c.y, xv[6] = c.z, xv[7] = c.w;
+        } else {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int64_t n = n0 + e;
+                xv[e] = (n >= 0 && n < len) ? __ldg(xr + n) : 0.f;
+            }
+        }
 #pragma unroll
         for (int e = 0; e < 8; e += 2) {
-            float v[2];
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                const int64_t n = j0 + e + q - h_front;
-                v[q] = (n >= 0 && n < len) ? __ldg(xr + n) : 0.f;
-            }
+            const float v[2] = {xv[e], xv[e + 1]};
             const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[0], v[1]);
             const float2 hf = __bfloat1622float2(h2);
             const float r0 = v[0] - hf.x, r1 = v[1] - hf.y;
@@ -709,8 +720,9 @@ cudaError_t direct_stage(const float* x, int64_t ld_x, const int64_t* lengths, i
     const int64_t longest = std::max<int64_t>(lpad, total - (int64_t)batch * lpad);
     const unsigned bx = (unsigned)std::min<int64_t>((longest / 8 + 255) / 256, 1024);
     dim3 grid(bx > 0 ? bx : 1, (unsigned)batch + 1);
+    const bool vec = ((uintptr_t)x & 15) == 0 && (ld_x & 3) == 0 && (h_front & 3) == 0;
     stage_bf16_kernel<<<grid, 256, 0, st>>>(x, ld_x, lengths, max_len, batch, hi, lo, lo2, lpad,
-                                            h_front, total);
+                                            h_front, total, vec);
     return cudaGetLastError();
 }
 
