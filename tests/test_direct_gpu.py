@@ -215,3 +215,38 @@ def test_reserve_moves_workspace_growth_out_of_execute(cw, sig):
     # 32000 samples staged as two bf16 parts are about 6 MB).
     assert grew_plain > 0
     assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("precision", ["bf16", "bf16x3"])
+def test_staging_alignment_does_not_change_results(cw, sig, precision):
+    """The bf16 staging reads 16-byte-aligned interior runs as float4 and
+    everything else element by element; a batch whose rows are offset by
+    one float (no float4 reads) and one with an odd row stride give the
+    aligned batch's scalograms byte for byte."""
+    hop, n = 64, 9001
+    lengths = [9001, 8999, 4097, 1]
+    xs = np.stack([sig.machine_clip(300 + i, n) for i in range(len(lengths))]).astype(np.float32)
+    sc = sig.scales_for_band(100, 8000, 24, 16000.0)
+    ld = torch.tensor(lengths, dtype=torch.int64, device="cuda")
+    with cw.Plan(sc, hop=hop, max_len=n, precision=precision, path="direct") as plan:
+        outs = []
+        wide = torch.zeros((len(lengths), n + 3), device="cuda")
+        wide[:, 1:n + 1] = torch.from_numpy(xs).cuda()
+        for x in (torch.from_numpy(xs).cuda(),   # ld_x = 9001 (odd)
+                  wide[:, 1:n + 1]):             # base one float past 16-byte alignment
+            out = torch.full((len(lengths), len(sc), plan.frames_max), -1.0, device="cuda")
+            plan.execute(x, lengths=ld, out=out)
+            outs.append(out)
+        plan.sync()
+        # the aligned reference: rows of 9004 floats, base aligned (the
+        # staged signal's front padding is a multiple of 8 samples)
+        al = torch.zeros((len(lengths), n + 3), device="cuda")
+        al[:, :n] = torch.from_numpy(xs).cuda()
+        ref = torch.full_like(outs[0], -1.0)
+        plan.execute(al[:, :n], lengths=ld, out=ref)
+        plan.sync()
+    for out in outs:
+        assert torch.equal(out, ref)
+    F = -(-lengths[0] // hop)
+    assert np.max(np.abs(ref[0, :, :F].cpu().numpy() - oracle_mag(xs[0], sc, hop))) / \
+        float(ref[0].max()) <= TOL[precision]
