@@ -136,14 +136,19 @@ double batch_bytes(int32_t b, int64_t L, int32_t S, int32_t hop) {
     return 4.0 * b * (double)L + 8.0 * b + 4.0 * b * (double)S * (double)F;
 }
 
+// Grows a slot buffer in stream order on the slot's own stream, whose
+// previous batch has completed: unlike cudaFree, which waits for the whole
+// device, this never stalls the other slots' batches.  Capacity grows by
+// at least half, so a slot meets few growths as its batches get larger.
 template <class T>
-cudaError_t grow_dev(T** p, size_t* cap, size_t need) {
+cudaError_t grow_dev(T** p, size_t* cap, size_t need, cudaStream_t st) {
     if (*cap >= need) return cudaSuccess;
-    cudaFree(*p);
+    const size_t n = std::max(need, *cap + *cap / 2);
+    if (*p) cudaFreeAsync(*p, st);
     *p = nullptr;
     *cap = 0;
-    cudaError_t e = cudaMalloc((void**)p, need * sizeof(T));
-    if (e == cudaSuccess) *cap = need;
+    cudaError_t e = cudaMallocAsync((void**)p, n * sizeof(T), st);
+    if (e == cudaSuccess) *cap = n;
     return e;
 }
 
@@ -282,9 +287,9 @@ struct cwth_server_s {
         note_peak();
         ++launched;
         if (cfg.dry_run) return CWTH_OK;
-        cudaError_t e = grow_dev(&sl.d_x, &sl.x_cap, (size_t)b * (size_t)L);
-        if (e == cudaSuccess) e = grow_dev(&sl.d_len, &sl.len_cap, (size_t)b);
-        if (e == cudaSuccess) e = grow_dev(&sl.d_out, &sl.out_cap, (size_t)b * key.S * (size_t)F);
+        cudaError_t e = grow_dev(&sl.d_x, &sl.x_cap, (size_t)b * (size_t)L, sl.st);
+        if (e == cudaSuccess) e = grow_dev(&sl.d_len, &sl.len_cap, (size_t)b, sl.st);
+        if (e == cudaSuccess) e = grow_dev(&sl.d_out, &sl.out_cap, (size_t)b * key.S * (size_t)F, sl.st);
         if (e == cudaSuccess && sl.hlen_cap < (size_t)b) {
             cudaFreeHost(sl.h_len);
             sl.h_len = nullptr;
@@ -613,10 +618,13 @@ cwth_status cwth_server_destroy(cwth_server_t s) {
     if (s->magic != kServerMagic) return CWTH_ERR_INVALID_ARG;
     for (Slot& sl : s->slots) {
         if (s->cfg.dry_run) break;
-        if (sl.st) cudaStreamSynchronize(sl.st);
-        cudaFree(sl.d_x);
-        cudaFree(sl.d_len);
-        cudaFree(sl.d_out);
+        if (sl.st) {
+            // The slot buffers came from the stream-ordered allocator.
+            if (sl.d_x) cudaFreeAsync(sl.d_x, sl.st);
+            if (sl.d_len) cudaFreeAsync(sl.d_len, sl.st);
+            if (sl.d_out) cudaFreeAsync(sl.d_out, sl.st);
+            cudaStreamSynchronize(sl.st);
+        }
         if (sl.h_len) cudaFreeHost(sl.h_len);
         if (sl.h_tab) cudaFreeHost(sl.h_tab);
         if (sl.ev) cudaEventDestroy(sl.ev);
