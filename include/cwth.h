@@ -463,6 +463,11 @@ cwth_status cwth_noalloc_status(void *stream);
  * reads them in place over the host link; otherwise one upload per
  * request) and its scalogram is downloaded straight into the caller's
  * buffer (one copy per request; page-locked buffers make it asynchronous).
+ * Each slot keeps device buffers for its batches' samples and scalograms,
+ * grown on demand (at least by half) from a memory pool the server owns,
+ * which keeps the blocks a slot outgrew for reuse until
+ * cwth_server_destroy; these are not charged to the budget, which limits
+ * the bytes of the batches in flight.
  * Not thread-safe: one thread drives a server.
  */
 typedef struct cwth_server_s *cwth_server_t;

@@ -138,16 +138,18 @@ double batch_bytes(int32_t b, int64_t L, int32_t S, int32_t hop) {
 
 // Grows a slot buffer in stream order on the slot's own stream, whose
 // previous batch has completed: unlike cudaFree, which waits for the whole
-// device, this never stalls the other slots' batches.  Capacity grows by
-// at least half, so a slot meets few growths as its batches get larger.
+// device, this never stalls the other slots' batches.  The blocks come
+// from the server's own memory pool, which keeps freed blocks mapped for
+// reuse (no release at synchronisation points).  Capacity grows by at least
+// half, so a slot meets few growths as its batches get larger.
 template <class T>
-cudaError_t grow_dev(T** p, size_t* cap, size_t need, cudaStream_t st) {
+cudaError_t grow_dev(T** p, size_t* cap, size_t need, cudaMemPool_t pool, cudaStream_t st) {
     if (*cap >= need) return cudaSuccess;
     const size_t n = std::max(need, *cap + *cap / 2);
     if (*p) cudaFreeAsync(*p, st);
     *p = nullptr;
     *cap = 0;
-    cudaError_t e = cudaMallocAsync((void**)p, n * sizeof(T), st);
+    cudaError_t e = cudaMallocFromPoolAsync((void**)p, n * sizeof(T), pool, st);
     if (e == cudaSuccess) *cap = n;
     return e;
 }
@@ -157,6 +159,7 @@ cudaError_t grow_dev(T** p, size_t* cap, size_t need, cudaStream_t st) {
 struct cwth_server_s {
     uint32_t magic = kServerMagic;
     int device = 0;
+    cudaMemPool_t pool = nullptr;  // slot buffers
     cwth_server_config cfg{};
     std::chrono::steady_clock::time_point t0;
     std::list<Pending> pending;
@@ -287,9 +290,10 @@ struct cwth_server_s {
         note_peak();
         ++launched;
         if (cfg.dry_run) return CWTH_OK;
-        cudaError_t e = grow_dev(&sl.d_x, &sl.x_cap, (size_t)b * (size_t)L, sl.st);
-        if (e == cudaSuccess) e = grow_dev(&sl.d_len, &sl.len_cap, (size_t)b, sl.st);
-        if (e == cudaSuccess) e = grow_dev(&sl.d_out, &sl.out_cap, (size_t)b * key.S * (size_t)F, sl.st);
+        cudaError_t e = grow_dev(&sl.d_x, &sl.x_cap, (size_t)b * (size_t)L, pool, sl.st);
+        if (e == cudaSuccess) e = grow_dev(&sl.d_len, &sl.len_cap, (size_t)b, pool, sl.st);
+        if (e == cudaSuccess)
+            e = grow_dev(&sl.d_out, &sl.out_cap, (size_t)b * key.S * (size_t)F, pool, sl.st);
         if (e == cudaSuccess && sl.hlen_cap < (size_t)b) {
             cudaFreeHost(sl.h_len);
             sl.h_len = nullptr;
@@ -447,6 +451,18 @@ cwth_status cwth_server_create(const cwth_server_config* cfg, cwth_server_t* out
     if (!cfg->dry_run) {
         if (cudaGetDevice(&s->device) != cudaSuccess) {
             delete s;
+            return CWTH_ERR_CUDA;
+        }
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = s->device;
+        uint64_t keep = ~uint64_t(0);
+        if (cudaMemPoolCreate(&s->pool, &props) != cudaSuccess ||
+            cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) {
+            cwth_server_destroy(s);
             return CWTH_ERR_CUDA;
         }
         for (Slot& sl : s->slots) {
@@ -630,6 +646,7 @@ cwth_status cwth_server_destroy(cwth_server_t s) {
         if (sl.ev) cudaEventDestroy(sl.ev);
         if (sl.st) cudaStreamDestroy(sl.st);
     }
+    if (s->pool) cudaMemPoolDestroy(s->pool);
     for (auto& kv : s->plans)
         if (kv.second.plan) cwth_destroy(kv.second.plan);
     s->magic = 0;
