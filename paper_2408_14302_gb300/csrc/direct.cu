@@ -73,6 +73,9 @@ __global__ void stage_bf16_kernel(const float* __restrict__ x, int64_t ld_x,
                                   __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo,
                                   __nv_bfloat16* __restrict__ lo2, int64_t lpad, int64_t h_front,
                                   int64_t total, bool vec) {
+    // The tensor-core kernel that follows may start its prologue now; it
+    // waits for this grid's completion before reading the staged signal.
+    asm volatile("griddepcontrol.launch_dependents;");
     const int b = blockIdx.y;
     const int64_t row_len = b < batch ? lpad : total - (int64_t)batch * lpad;
     int64_t len = 0;
@@ -287,7 +290,13 @@ __global__ void __launch_bounds__(kDirThreads, 1)
     // serial (each tcgen05.mma waits for the one before it to be accepted),
     // so any latency between two issues adds to the tensor-core time.
     if (warp == 0) {
-        // Producer.
+        // Producer.  The kernel is launched as a programmatic dependent of
+        // the staging kernel (its prologue above overlaps that kernel's
+        // tail); the staged signal is read only after the preceding grid
+        // has completed and its writes are visible.  Nothing else in the
+        // kernel reads memory the preceding grid writes, and the epilogue's
+        // stores follow the producer's copies.
+        asm volatile("griddepcontrol.wait;" ::: "memory");
         uint32_t g = 0;            // steps issued over all units
         int s = 0;                 // stage of step g
         uint32_t sph = 0;          // parity of stage s's current fill
@@ -737,17 +746,28 @@ cudaError_t direct_launch_mma(const CUtensorMap* maps, const DirLaunch& L, int n
     const int64_t tiles = std::min<int64_t>(units, sms);
     const size_t smem = direct_smem_bytes(L.ncols, L.stages, nparts, L.a_shift ? L.win_rows : 0,
                                           L.unit, L.win_sets, L.a_phases);
-    const dim3 grid((unsigned)tiles);
+    // Programmatic stream serialisation: the kernel may begin while the
+    // preceding kernel (the bf16 staging) finishes; its producer waits for
+    // that grid (griddepcontrol.wait) before the first copy of the signal.
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3((unsigned)tiles);
+    cfg.blockDim = dim3(kDirThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
     if (nparts == 3)
-        direct_mma_kernel<3><<<grid, kDirThreads, smem, st>>>(maps[0], maps[1], maps[2], maps[3],
-                                                             maps[4], maps[5], L);
-    else if (nparts == 2)
-        direct_mma_kernel<2><<<grid, kDirThreads, smem, st>>>(maps[0], maps[1], maps[1], maps[3],
-                                                             maps[4], maps[4], L);
-    else
-        direct_mma_kernel<1><<<grid, kDirThreads, smem, st>>>(maps[0], maps[0], maps[0], maps[3],
-                                                             maps[3], maps[3], L);
-    return cudaGetLastError();
+        return cudaLaunchKernelEx(&cfg, direct_mma_kernel<3>, maps[0], maps[1], maps[2], maps[3],
+                                  maps[4], maps[5], L);
+    if (nparts == 2)
+        return cudaLaunchKernelEx(&cfg, direct_mma_kernel<2>, maps[0], maps[1], maps[1], maps[3],
+                                  maps[4], maps[4], L);
+    return cudaLaunchKernelEx(&cfg, direct_mma_kernel<1>, maps[0], maps[0], maps[0], maps[3],
+                              maps[3], maps[3], L);
 }
 
 cudaError_t direct_launch_f32(const float* x, int64_t ld_x, const float2* bank, const int32_t* d_h,
