@@ -944,7 +944,7 @@ void spectral_record(const cwth_plan_s* p, const float* d_x, int64_t ld_x, const
 
 cwth_status launch_spectral(cwth_plan_s* p, const float* d_x, int64_t ld_x,
                             const int64_t* d_len, int32_t batch, float* d_out, cudaStream_t st,
-                            bool fill_gpu) {
+                            bool fill_gpu, bool dependent = false) {
     if ((p->n_sp == 0 && p->n_fd == 0) || batch == 0) return CWTH_OK;
     if (batch > 65535 || p->n_seg > 0x7fffffff) return CWTH_ERR_UNSUPPORTED;
     SpecLaunch L;
@@ -952,7 +952,8 @@ cwth_status launch_spectral(cwth_plan_s* p, const float* d_x, int64_t ld_x,
     size_t smem = 0;
     spectral_record(p, d_x, ld_x, d_len, batch, d_out, fill_gpu, &L, &threads, &n_groups, &smem);
     return cuda_status(
-        cwth::spectral_launch(L, threads, p->spec_prune, p->n_seg, batch, n_groups, smem, st));
+        cwth::spectral_launch(L, threads, p->spec_prune, p->n_seg, batch, n_groups, smem, st,
+                              dependent));
 }
 
 // Rows of one clip in the direct path's staged signal (the clip with its
@@ -1086,8 +1087,10 @@ cwth_status launch_all(cwth_plan_s* p, const float* d_x, int64_t ld_x, const int
                        int32_t batch, float* d_out, cudaStream_t st, bool fill_gpu = true) {
     cwth_status s = launch_direct(p, d_x, ld_x, d_len, batch, d_out, st);
     if (s == CWTH_OK) s = launch_spectral(p, d_x, ld_x, d_len, batch, d_out, st, fill_gpu);
+    // Later parts read the same input and write other rows: each may start
+    // on the SMs the part before it leaves idle in its last wave.
     for (cwth_plan_s* q = p->child; q && s == CWTH_OK; q = q->child)
-        s = launch_spectral(q, d_x, ld_x, d_len, batch, d_out, st, fill_gpu);
+        s = launch_spectral(q, d_x, ld_x, d_len, batch, d_out, st, fill_gpu, true);
     return s;
 }
 

@@ -190,12 +190,15 @@ cudaError_t spectral_make_fd_taps(const double* d_scales, const int32_t* d_h, co
 int spectral_twiddle_entries(int M);
 cudaError_t spectral_prepare_device();
 cudaError_t spectral_make_twiddles(float2* d_tw, int M, cudaStream_t st);
+// dependent: launch as a programmatic dependent of the kernel before it on
+// st (a plan's second and later spectral parts; the kernel makes the
+// grid complete after its predecessor).
 cudaError_t spectral_launch(const SpecLaunch& L, int threads, bool prune, int n_seg, int batch,
-                            int n_groups, size_t smem, cudaStream_t st);
+                            int n_groups, size_t smem, cudaStream_t st, bool dependent);
 // The 1024-thread instantiations (compiled in their own translation unit).
 cudaError_t spectral_prepare_solo();
 cudaError_t spectral_launch_solo(const SpecLaunch& L, bool prune, dim3 grid, size_t smem,
-                                 cudaStream_t st);
+                                 cudaStream_t st, bool dependent);
 // One launch of the paired shape over a work list: block i runs item i,
 // {group, segment, clip, scale group | scale groups << 16}, of the plan
 // records g[] (passed by value).

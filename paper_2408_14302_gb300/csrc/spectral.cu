@@ -96,9 +96,15 @@ cudaError_t spectral_make_twiddles(float2* d_tw, int M, cudaStream_t st) {
 }
 
 cudaError_t spectral_launch(const SpecLaunch& L, int threads, bool prune, int n_seg, int batch,
-                            int n_groups, size_t smem, cudaStream_t st) {
+                            int n_groups, size_t smem, cudaStream_t st, bool dependent) {
     dim3 grid(n_seg, batch, n_groups);
-    if (threads == kSpecThreadsSolo) return spectral_launch_solo(L, prune, grid, smem, st);
+    if (threads == kSpecThreadsSolo)
+        return spectral_launch_solo(L, prune, grid, smem, st, dependent);
+    if (dependent)
+        return spectral_launch_dependent(
+            prune ? spectral_segment_kernel<kSpecThreadsPair, true>
+                  : spectral_segment_kernel<kSpecThreadsPair, false>,
+            L, grid, kSpecThreadsPair, smem, st);
     if (prune)
         spectral_segment_kernel<kSpecThreadsPair, true><<<grid, kSpecThreadsPair, smem, st>>>(L);
     else

@@ -997,7 +997,34 @@ __device__ __forceinline__ void spectral_item(const SpecLaunch& p, int seg, int 
 template <int THREADS, bool PRUNE>
 __global__ void __launch_bounds__(THREADS, THREADS >= 1024 ? 1 : 2)
     spectral_segment_kernel(const SpecLaunch p) {
+    // The plan's next spectral part, launched as a programmatic dependent,
+    // may start on the SMs this grid's last CTAs leave idle.
+    asm volatile("griddepcontrol.launch_dependents;");
     spectral_item<THREADS, PRUNE>(p, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.z);
+    // As such a dependent (the parts read the same input and write disjoint
+    // rows, so nothing waits at the start), the grid completes only after
+    // the part before it, and whatever follows on the stream still follows
+    // every part; in any other launch this returns at once.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+// Launches kern with programmatic stream serialisation: it may begin once
+// every CTA of the kernel before it on st has started.
+inline cudaError_t spectral_launch_dependent(void (*kern)(SpecLaunch), const SpecLaunch& L,
+                                             dim3 grid, int threads, size_t smem,
+                                             cudaStream_t st) {
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, L);
 }
 
 // One launch over a device work list spanning several plans (the groups

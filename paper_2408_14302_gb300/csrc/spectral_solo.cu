@@ -16,7 +16,12 @@ cudaError_t spectral_prepare_solo() {
 }
 
 cudaError_t spectral_launch_solo(const SpecLaunch& L, bool prune, dim3 grid, size_t smem,
-                                 cudaStream_t st) {
+                                 cudaStream_t st, bool dependent) {
+    if (dependent)
+        return spectral_launch_dependent(
+            prune ? spectral_segment_kernel<kSpecThreadsSolo, true>
+                  : spectral_segment_kernel<kSpecThreadsSolo, false>,
+            L, grid, kSpecThreadsSolo, smem, st);
     if (prune)
         spectral_segment_kernel<kSpecThreadsSolo, true><<<grid, kSpecThreadsSolo, smem, st>>>(L);
     else
