@@ -1086,7 +1086,11 @@ cwth_status launch_direct(cwth_plan_s* p, const float* d_x, int64_t ld_x, const 
 cwth_status launch_all(cwth_plan_s* p, const float* d_x, int64_t ld_x, const int64_t* d_len,
                        int32_t batch, float* d_out, cudaStream_t st, bool fill_gpu = true) {
     cwth_status s = launch_direct(p, d_x, ld_x, d_len, batch, d_out, st);
-    if (s == CWTH_OK) s = launch_spectral(p, d_x, ld_x, d_len, batch, d_out, st, fill_gpu);
+    // After the direct path's kernels (other rows, the same input), the
+    // spectral part may start on the SMs they leave as they finish.
+    if (s == CWTH_OK)
+        s = launch_spectral(p, d_x, ld_x, d_len, batch, d_out, st, fill_gpu,
+                            p->n_dir > 0 && batch > 0);
     // Later parts read the same input and write other rows: each may start
     // on the SMs the part before it leaves idle in its last wave.
     for (cwth_plan_s* q = p->child; q && s == CWTH_OK; q = q->child)

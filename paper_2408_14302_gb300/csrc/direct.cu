@@ -234,6 +234,9 @@ __global__ void __launch_bounds__(kDirThreads, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nsteps = p.nsteps;
     const int ntiles = (int)((p.total_rows + kBM - 1) / kBM);
+    // A spectral part of the same plan, launched next as a programmatic
+    // dependent, takes each SM this persistent grid's CTAs leave.
+    asm volatile("griddepcontrol.launch_dependents;");
     const int nunits = (ntiles + T - 1) / T;
     const uint32_t acc_cols = p.tmem_cols / (uint32_t)(asets * T);  // columns per tile accumulator
 
