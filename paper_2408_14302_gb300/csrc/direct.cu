@@ -562,6 +562,10 @@ __global__ void __launch_bounds__(kDirThreads, 1)
         tmem_dealloc(tmem, p.tmem_cols);
     }
     if (threadIdx.x == 0 && abort_sh) atomicExch(p.status, (int)CWTH_ERR_TIMEOUT);
+    // Every CTA, also one that gave up before its producer waited, ends
+    // after the grid it depends on, so work after this kernel on the
+    // stream also follows that grid.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
 // ------------------------------------------------------------ float32 SIMT
