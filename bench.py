@@ -399,7 +399,8 @@ def run_serving_leg(torch, cwth):
     signals, scalograms into a page-locked ring.  The server's plans for
     every key of the mix are built first (cwth_server_prepare) and one
     warm-up pass runs; then 2000 Poisson requests at 1000 req/s (p50/p99
-    latency) and 5000 arriving at once (saturation throughput)."""
+    latency) and 5000 arriving at once, replayed three times (saturation
+    throughput: the median pass, with all three listed)."""
     from paper_2408_14302_gb300 import serving
     pool = [signals.machine_clip(5000 + i, 60 * 16000, 16000.0) for i in range(8)]
     pinned = torch.from_numpy(np.stack(pool).astype(np.float32)).pin_memory()
@@ -411,14 +412,25 @@ def run_serving_leg(torch, cwth):
         serving.library_replay(serving.poisson_requests(1000, 1e6, seed=4000, pool=pool),
                                pinned, ring, server=srv)
         res = {}
-        for name, rate, count in (("poisson_1000_per_s", 1000.0, 2000), ("saturation", 1e6, 5000)):
+        for name, rate, count, passes in (("poisson_1000_per_s", 1000.0, 2000, 1),
+                                          ("saturation", 1e6, 5000, 3)):
             reqs = serving.poisson_requests(count, rate, seed=6000 + int(rate), pool=pool)
-            s, _, _ = serving.library_replay(reqs, pinned, ring, server=srv)
             audio = sum(r.audio_seconds for r in reqs)
+            # Saturation: the same requests replayed `passes` times, the
+            # median pass reported (a pass lasts well under a second and
+            # moves ~10 GB over the shared host link).
+            runs = []
+            for _ in range(passes):
+                s, _, _ = serving.library_replay(reqs, pinned, ring, server=srv)
+                runs.append((audio / s["wall_s"], s))
+            runs.sort(key=lambda t: t[0])
+            thr, s = runs[len(runs) // 2]
             res[name] = {"p50_ms": s["p50_ms"], "p99_ms": s["p99_ms"],
-                         "audio_sec_per_s": audio / s["wall_s"],
+                         "audio_sec_per_s": thr,
                          "offered_audio_sec_per_s": audio / max(reqs[-1].arrival, 1e-9),
                          "mean_batch": s["mean_batch"], "requests": len(reqs)}
+            if passes > 1:
+                res[name]["passes_audio_sec_per_s"] = [t[0] for t in runs]
     finally:
         srv.close()
     res["config"] = {"engine": "cwth_server (library)", "precision": "fp32", "path": "auto",
