@@ -246,6 +246,27 @@ cwth_status cwth_plan_set_inverse_radix(cwth_plan_t plan, int32_t radix);
  */
 cwth_status cwth_plan_reserve(cwth_plan_t plan, int32_t batch, int64_t ld_x, int32_t host);
 
+/* Bytes of device memory the direct path's staged bf16 signal needs for
+ * `batch` clips (0 for plans without tensor-core scales), written to
+ * *bytes: the size a buffer bound by cwth_plan_bind_stage must have for an
+ * execute of that batch.  No paper counterpart.
+ * Errors: CWTH_ERR_BAD_PLAN, CWTH_ERR_INVALID_ARG (bytes NULL, batch < 0).
+ */
+cwth_status cwth_plan_stage_bytes(cwth_plan_t plan, int32_t batch, size_t *bytes);
+
+/* Bind a caller-owned device buffer (16-byte aligned, `bytes` long) in
+ * which later executes of this plan stage the direct path's bf16 signal,
+ * instead of the plan's own growable workspace; NULL unbinds.  The buffer
+ * stays the caller's: it must outlive the work enqueued with it bound, and
+ * two executes that may run at once must use different buffers (one plan
+ * can then serve several streams, each with its own buffer).  An execute
+ * whose batch needs more than `bytes` (cwth_plan_stage_bytes) fails with
+ * CWTH_ERR_INVALID_ARG before enqueuing anything.  No paper counterpart.
+ * Errors: CWTH_ERR_BAD_PLAN, CWTH_ERR_INVALID_ARG (unaligned buffer, or a
+ * buffer with bytes == 0).
+ */
+cwth_status cwth_plan_bind_stage(cwth_plan_t plan, void *buf, size_t bytes);
+
 /* Release a plan's device tables and staging.  NULL is accepted.  The caller
  * must not destroy a plan while work it enqueued may still be running. */
 cwth_status cwth_destroy(cwth_plan_t plan);
@@ -463,8 +484,10 @@ cwth_status cwth_noalloc_status(void *stream);
  * reads them in place over the host link; otherwise one upload per
  * request) and its scalogram is downloaded straight into the caller's
  * buffer (one copy per request; page-locked buffers make it asynchronous).
- * Each slot keeps device buffers for its batches' samples and scalograms,
- * grown on demand (at least by half) from a memory pool the server owns,
+ * Each slot keeps device buffers for its batches' samples and scalograms
+ * (and, for plans with tensor-core scales, the bf16 staged signal, bound
+ * to the shared plan for each execute: cwth_plan_bind_stage), grown on
+ * demand (at least by half) from a memory pool the server owns,
  * which keeps the blocks a slot outgrew for reuse until
  * cwth_server_destroy; these are not charged to the budget, which limits
  * the bytes of the batches in flight.
@@ -551,8 +574,8 @@ cwth_status cwth_server_stats_query(cwth_server_t s, cwth_server_stats *st);
 
 /*
  * Builds (or finds) the cached plan that requests of (fs, n_scales, hop)
- * with up to n_max samples will use, for every slot when plans are kept
- * per slot, so that the first such request does not wait for a plan.
+ * with up to n_max samples will use (one plan per key, shared by the
+ * slots), so that the first such request does not wait for a plan.
  * Cached plans count against the budget and may be evicted like any other
  * (least recently used first when the plan cache is full).
  * Errors: CWTH_ERR_INVALID_ARG for a NULL server or a field out of range;

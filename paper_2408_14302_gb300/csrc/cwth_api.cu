@@ -975,6 +975,19 @@ DirStageShape dir_stage_shape(const cwth_plan_s* p, int32_t batch) {
 // Grows the staged bf16 signal to `total` elements per part.  Growing frees
 // the old buffers first (cudaFree waits for the device to finish the work
 // that may still read them).
+// Elements of one staged part in a caller-bound buffer: rounded up to 128
+// (256 bytes), so each part starts aligned for the tensor maps.
+int64_t dir_stage_part(int64_t total) { return (total + 127) / 128 * 128; }
+
+// Bytes a caller-bound staging buffer needs for `batch` clips (0: the plan
+// stages nothing).
+size_t dir_stage_bytes(const cwth_plan_s* p, int32_t batch) {
+    if (p->n_dir == 0 || p->precision == CWTH_PREC_FP32 || batch <= 0) return 0;
+    const DirStageShape sh = dir_stage_shape(p, batch);
+    return (size_t)direct_parts(p->precision) * (size_t)dir_stage_part(sh.total) *
+           sizeof(__nv_bfloat16);
+}
+
 cwth_status dir_stage_grow(cwth_plan_s* p, int64_t total) {
     const int nparts = direct_parts(p->precision);
     if ((size_t)total > p->x_elems) {
@@ -1030,31 +1043,50 @@ cwth_status launch_direct(cwth_plan_s* p, const float* d_x, int64_t ld_x, const 
     const int64_t total = sh.total;
     if (total_rows > (int64_t(1) << 31) - 256) return CWTH_ERR_UNSUPPORTED;
     {
-        cwth_status gs = dir_stage_grow(p, total);
-        if (gs != CWTH_OK) return gs;
+        if (!p->ext_stage) {
+            cwth_status gs = dir_stage_grow(p, total);
+            if (gs != CWTH_OK) return gs;
+        }
     }
-    if (p->x_maps_ptr != p->d_xhi || p->x_maps_rows != total_rows) {
+    // The staged parts: the plan's own buffers, or consecutive parts of a
+    // caller-bound buffer.
+    __nv_bfloat16* xhi = p->d_xhi;
+    __nv_bfloat16* xlo = p->d_xlo;
+    __nv_bfloat16* xlo2 = p->d_xlo2;
+    if (p->ext_stage) {
+        if (p->ext_stage_bytes < dir_stage_bytes(p, batch)) {
+            char msg[160];
+            snprintf(msg, sizeof(msg), "the bound staging buffer holds %zu bytes; this batch needs %zu",
+                     p->ext_stage_bytes, dir_stage_bytes(p, batch));
+            note_error(msg);
+            return CWTH_ERR_INVALID_ARG;
+        }
+        const int64_t part = dir_stage_part(total);
+        xhi = static_cast<__nv_bfloat16*>(p->ext_stage);
+        xlo = nparts > 1 ? xhi + part : xhi;
+        xlo2 = nparts > 2 ? xhi + 2 * part : xlo;
+    }
+    if (p->x_maps_ptr != xhi || p->x_maps_rows != total_rows) {
         p->maps_a_hi.assign(p->groups.size(), CUtensorMap());
         p->maps_a_lo.assign(p->groups.size(), CUtensorMap());
         p->maps_a_lo2.assign(p->groups.size(), CUtensorMap());
         for (size_t gi = 0; gi < p->groups.size(); ++gi) {
             const cwth::DirGroup& g = p->groups[gi];
             const int64_t off = p->dir_front - g.h;
-            if (!encode_bf16_2d(&p->maps_a_hi[gi], p->d_xhi + off, g.k_pad, total_rows, hop * 2, 32) ||
-                !encode_bf16_2d(&p->maps_a_lo[gi], p->d_xlo + off, g.k_pad, total_rows, hop * 2, 32) ||
-                (nparts > 2 && !encode_bf16_2d(&p->maps_a_lo2[gi], p->d_xlo2 + off, g.k_pad,
+            if (!encode_bf16_2d(&p->maps_a_hi[gi], xhi + off, g.k_pad, total_rows, hop * 2, 32) ||
+                !encode_bf16_2d(&p->maps_a_lo[gi], xlo + off, g.k_pad, total_rows, hop * 2, 32) ||
+                (nparts > 2 && !encode_bf16_2d(&p->maps_a_lo2[gi], xlo2 + off, g.k_pad,
                                                total_rows, hop * 2, 32))) {
                 note_error("cuTensorMapEncodeTiled rejected the frame-matrix tensor map");
                 return CWTH_ERR_UNSUPPORTED;
             }
         }
-        p->x_maps_ptr = p->d_xhi;
+        p->x_maps_ptr = xhi;
         p->x_maps_rows = total_rows;
     }
-    cudaError_t e = cwth::direct_stage(d_x, ld_x, d_len, p->max_len, batch, p->d_xhi,
-                                       nparts > 1 ? p->d_xlo : nullptr,
-                                       nparts > 2 ? p->d_xlo2 : nullptr, lpad, p->dir_front, total,
-                                       st);
+    cudaError_t e = cwth::direct_stage(d_x, ld_x, d_len, p->max_len, batch, xhi,
+                                       nparts > 1 ? xlo : nullptr, nparts > 2 ? xlo2 : nullptr,
+                                       lpad, p->dir_front, total, st);
     if (e != cudaSuccess) return cuda_status(e);
     L.rows_per_clip = rows_per_clip;
     L.total_rows = total_rows;
@@ -1448,6 +1480,21 @@ cwth_status cwth_plan_reserve(cwth_plan_t p, int32_t batch, int64_t ld_x, int32_
         if (s == CWTH_OK) s = cuda_status(host_pipeline_init(p));
     }
     return s;
+}
+
+cwth_status cwth_plan_stage_bytes(cwth_plan_t p, int32_t batch, size_t* bytes) {
+    if (!valid_plan(p)) return CWTH_ERR_BAD_PLAN;
+    if (!bytes || batch < 0) return CWTH_ERR_INVALID_ARG;
+    *bytes = dir_stage_bytes(p, batch);
+    return CWTH_OK;
+}
+
+cwth_status cwth_plan_bind_stage(cwth_plan_t p, void* buf, size_t bytes) {
+    if (!valid_plan(p)) return CWTH_ERR_BAD_PLAN;
+    if (buf && (bytes == 0 || ((uintptr_t)buf & 15) != 0)) return CWTH_ERR_INVALID_ARG;
+    p->ext_stage = buf;
+    p->ext_stage_bytes = buf ? bytes : 0;
+    return CWTH_OK;
 }
 
 cwth_status cwth_plan_set_host_chunks(cwth_plan_t p, int32_t chunks) {

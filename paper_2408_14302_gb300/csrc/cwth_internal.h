@@ -311,6 +311,10 @@ struct cwth_plan_s {
     __nv_bfloat16* d_xlo = nullptr;
     __nv_bfloat16* d_xlo2 = nullptr;
     size_t x_elems = 0;
+    // caller-bound staging (cwth_plan_bind_stage): used instead of the
+    // plan's own while set
+    void* ext_stage = nullptr;
+    size_t ext_stage_bytes = 0;
     // A-operand tensor maps per group, valid for (x_maps_ptr, x_maps_rows)
     std::vector<CUtensorMap> maps_a_hi, maps_a_lo, maps_a_lo2;
     const void* x_maps_ptr = nullptr;

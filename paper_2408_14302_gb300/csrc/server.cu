@@ -107,6 +107,8 @@ struct Slot {
     size_t len_cap = 0;
     float* d_out = nullptr;
     size_t out_cap = 0;
+    uint8_t* d_stage = nullptr;  // bf16 staging of a direct-path batch (bound to the plan)
+    size_t stage_cap = 0;
     int64_t* h_len = nullptr;  // page-locked
     size_t hlen_cap = 0;
     IoEntry* h_tab = nullptr;  // page-locked, read by the gather kernel
@@ -196,6 +198,20 @@ struct cwth_server_s {
         return a;
     }
 
+    // Bytes of a batch's bf16 staging for the direct path (in its slot's
+    // buffer); an estimate in dry-run mode, where no plan exists.
+    double stage_bytes(const CachedPlan* cp, const Key& k, int32_t b) const {
+        if (cfg.precision == CWTH_PREC_FP32 || cfg.path == CWTH_PATH_SPECTRAL) return 0.0;
+        if (cfg.dry_run || !cp->plan) {
+            const double parts = cfg.precision == CWTH_PREC_BF16 ? 1.0
+                                 : (cfg.precision == CWTH_PREC_BF16X2 ? 2.0 : 3.0);
+            return 2.0 * parts * b * (double)(k.bucket + 8192);
+        }
+        size_t n = 0;
+        if (cwth_plan_stage_bytes(cp->plan, b, &n) != CWTH_OK) return 0.0;
+        return (double)n;
+    }
+
     // Evicts least recently used idle plans until `need` more bytes fit the
     // cache bound (or no idle plan is left).
     void make_room(double need) {
@@ -213,12 +229,11 @@ struct cwth_server_s {
         }
     }
 
-    // The cached plan for (key, slot), made if needed.  Plans whose execute
-    // stages the batch in a plan-owned workspace (direct-path scales at a
-    // bf16 precision) are made per slot, others are shared.
-    cwth_status get_plan(const Pending& q, int32_t slot, Key* key_out, CachedPlan** out) {
-        const bool per_slot = cfg.precision != CWTH_PREC_FP32 && cfg.path != CWTH_PATH_SPECTRAL;
-        Key k{q.r.fs, q.r.n_scales, q.r.hop, q.bucket, per_slot ? slot : -1};
+    // The cached plan for a key, made if needed, shared by all slots: a
+    // batch with direct-path scales stages its bf16 signal in its slot's
+    // own buffer, bound to the plan for that execute.
+    cwth_status get_plan(const Pending& q, Key* key_out, CachedPlan** out) {
+        Key k{q.r.fs, q.r.n_scales, q.r.hop, q.bucket, -1};
         *key_out = k;
         auto it = plans.find(k);
         if (it != plans.end()) {
@@ -234,11 +249,8 @@ struct cwth_server_s {
             cwth_status st = cwth_plan(&cfg.wavelet, a.data(), k.S, k.hop, k.fs, k.bucket,
                                        cfg.precision, cfg.path, &cp.plan);
             if (st != CWTH_OK) return st;
-            // A plan's staging grows with the batch: size it for max_batch
-            // now, so that the bytes charged are the bytes it will hold.
-            st = cwth_plan_reserve(cp.plan, cfg.max_batch, 0, 0);
             cwth_plan_info info;
-            if (st == CWTH_OK) st = cwth_plan_query(cp.plan, &info);
+            st = cwth_plan_query(cp.plan, &info);
             if (st != CWTH_OK) {
                 cwth_destroy(cp.plan);
                 return st;
@@ -294,6 +306,16 @@ struct cwth_server_s {
         if (e == cudaSuccess) e = grow_dev(&sl.d_len, &sl.len_cap, (size_t)b, pool, sl.st);
         if (e == cudaSuccess)
             e = grow_dev(&sl.d_out, &sl.out_cap, (size_t)b * key.S * (size_t)F, pool, sl.st);
+        // A batch with direct-path scales stages its bf16 signal in the
+        // slot's buffer, bound to the (shared) plan for this execute.
+        size_t need_stage = 0;
+        if (e == cudaSuccess && cwth_plan_stage_bytes(cp->plan, b, &need_stage) == CWTH_OK &&
+            need_stage > 0) {
+            e = grow_dev(&sl.d_stage, &sl.stage_cap, need_stage, pool, sl.st);
+            if (e == cudaSuccess &&
+                cwth_plan_bind_stage(cp->plan, sl.d_stage, sl.stage_cap) != CWTH_OK)
+                e = cudaErrorInvalidValue;
+        }
         if (e == cudaSuccess && sl.hlen_cap < (size_t)b) {
             cudaFreeHost(sl.h_len);
             sl.h_len = nullptr;
@@ -390,7 +412,7 @@ struct cwth_server_s {
                     pick.push_back(it);
             Key key;
             CachedPlan* cp = nullptr;
-            const cwth_status ps = get_plan(first, slot, &key, &cp);
+            const cwth_status ps = get_plan(first, &key, &cp);
             if (ps != CWTH_OK) {
                 for (auto it : pick) {
                     complete(it->r, ps, (int32_t)pick.size(), t);
@@ -399,10 +421,10 @@ struct cwth_server_s {
                 continue;
             }
             int32_t b = (int32_t)pick.size();
-            double bytes = batch_bytes(b, key.bucket, key.S, key.hop);
+            double bytes = batch_bytes(b, key.bucket, key.S, key.hop) + stage_bytes(cp, key, b);
             while (b > 1 && used() + bytes > cfg.budget_bytes) {
                 --b;
-                bytes = batch_bytes(b, key.bucket, key.S, key.hop);
+                bytes = batch_bytes(b, key.bucket, key.S, key.hop) + stage_bytes(cp, key, b);
             }
             if (used() + bytes > cfg.budget_bytes) {
                 bool busy = false;
@@ -526,15 +548,9 @@ cwth_status cwth_server_prepare(cwth_server_t s, double fs, int32_t n_scales, in
     r.hop = hop;
     r.n = n_max;
     const Pending q{r, length_bucket(n_max), nullptr};
-    const bool per_slot = s->cfg.precision != CWTH_PREC_FP32 && s->cfg.path != CWTH_PATH_SPECTRAL;
-    const int nslots = per_slot ? (int)s->slots.size() : 1;
-    for (int slot = 0; slot < nslots; ++slot) {
-        Key key;
-        CachedPlan* cp = nullptr;
-        const cwth_status st = s->get_plan(q, slot, &key, &cp);
-        if (st != CWTH_OK) return st;
-    }
-    return CWTH_OK;
+    Key key;
+    CachedPlan* cp = nullptr;
+    return s->get_plan(q, &key, &cp);
 }
 
 cwth_status cwth_server_stats_query(cwth_server_t s, cwth_server_stats* st) {
@@ -562,10 +578,9 @@ double cwth_server_plan_bytes(cwth_server_t s, double fs, int32_t n_scales, int3
     if (s->cfg.dry_run) {
         // Estimate: per-scale records and band tables, the twiddle table of
         // a 16384-sample segment, and for bf16 precisions a tap bank of up
-        // to 4096 taps per scale part plus bf16 staging of max_batch clips.
+        // to 4096 taps per scale part (batches stage in their slot's buffer).
         double b = 64.0 * n_scales + 8.0 * (16384 / 128 + 128) + 4096.0;
-        if (s->cfg.precision != CWTH_PREC_FP32)
-            b += 2.0 * 4096.0 * 2.0 * n_scales * 3.0 + 6.0 * (double)s->cfg.max_batch * bucket;
+        if (s->cfg.precision != CWTH_PREC_FP32) b += 2.0 * 4096.0 * 2.0 * n_scales * 3.0;
         return b;
     }
     const std::vector<double> a = s->scales(fs, n_scales);
@@ -575,8 +590,7 @@ double cwth_server_plan_bytes(cwth_server_t s, double fs, int32_t n_scales, int3
         return -1.0;
     cwth_plan_info info;
     double b = -1.0;
-    if (cwth_plan_reserve(p, s->cfg.max_batch, 0, 0) == CWTH_OK &&
-        cwth_plan_query(p, &info) == CWTH_OK)
+    if (cwth_plan_query(p, &info) == CWTH_OK)
         b = (double)info.table_bytes + (double)info.workspace_bytes;
     cwth_destroy(p);
     return b;
@@ -639,6 +653,7 @@ cwth_status cwth_server_destroy(cwth_server_t s) {
             if (sl.d_x) cudaFreeAsync(sl.d_x, sl.st);
             if (sl.d_len) cudaFreeAsync(sl.d_len, sl.st);
             if (sl.d_out) cudaFreeAsync(sl.d_out, sl.st);
+            if (sl.d_stage) cudaFreeAsync(sl.d_stage, sl.st);
             cudaStreamSynchronize(sl.st);
         }
         if (sl.h_len) cudaFreeHost(sl.h_len);

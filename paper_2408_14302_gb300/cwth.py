@@ -30,7 +30,8 @@ EXPORTS = ("cwth_plan", "cwth_execute", "cwth_execute_host", "cwth_destroy",
            "cwth_batch_execute", "cwth_batch_items", "cwth_batch_destroy",
            "cwth_plan_reserve", "cwth_server_create", "cwth_server_submit", "cwth_server_poll",
            "cwth_server_stats_query", "cwth_server_plan_bytes", "cwth_server_replay",
-           "cwth_server_destroy", "cwth_server_prepare", "cwth_plan_set_inverse_radix")
+           "cwth_server_destroy", "cwth_server_prepare", "cwth_plan_set_inverse_radix",
+           "cwth_plan_stage_bytes", "cwth_plan_bind_stage")
 
 
 class CwthError(RuntimeError):
@@ -115,6 +116,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.cwth_plan_set_inverse_radix.restype = ctypes.c_int
     lib.cwth_plan_reserve.argtypes = [vp, i32, i64, i32]
     lib.cwth_plan_reserve.restype = ctypes.c_int
+    lib.cwth_plan_stage_bytes.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_size_t)]
+    lib.cwth_plan_stage_bytes.restype = ctypes.c_int
+    lib.cwth_plan_bind_stage.argtypes = [vp, vp, ctypes.c_size_t]
+    lib.cwth_plan_bind_stage.restype = ctypes.c_int
     lib.cwth_selftest_wait_timeout.argtypes = [vp, i64, vp]
     lib.cwth_selftest_wait_timeout.restype = ctypes.c_int
     lib.cwth_measure_fp32_fma.argtypes = [ctypes.POINTER(ctypes.c_double), vp]
@@ -351,6 +356,27 @@ class Plan:
         cwth_plan_reserve."""
         _check(_lib.cwth_plan_reserve(self._h, int(batch), int(ld_x), 1 if host else 0),
                "cwth_plan_reserve")
+
+    def stage_bytes(self, batch: int) -> int:
+        """Bytes the direct path's staged bf16 signal needs for `batch`
+        clips (0 without tensor-core scales); see cwth_plan_stage_bytes."""
+        n = ctypes.c_size_t(0)
+        _check(_lib.cwth_plan_stage_bytes(self._h, int(batch), ctypes.byref(n)),
+               "cwth_plan_stage_bytes")
+        return int(n.value)
+
+    def bind_stage(self, buf=None):
+        """Stage the direct path's signal in `buf` (a CUDA tensor the caller
+        keeps alive, at least stage_bytes(batch) bytes) in later executes;
+        None unbinds.  See cwth_plan_bind_stage."""
+        if buf is None:
+            _check(_lib.cwth_plan_bind_stage(self._h, None, 0), "cwth_plan_bind_stage")
+            return
+        if not buf.is_cuda or not buf.is_contiguous():
+            raise ValueError("the staging buffer must be a contiguous CUDA tensor")
+        _check(_lib.cwth_plan_bind_stage(self._h, ctypes.c_void_p(buf.data_ptr()),
+                                         buf.numel() * buf.element_size()),
+               "cwth_plan_bind_stage")
 
     def sync(self, stream=None):
         """Wait for this plan's work on ``stream`` and raise on device-side

@@ -250,3 +250,41 @@ def test_staging_alignment_does_not_change_results(cw, sig, precision):
     F = -(-lengths[0] // hop)
     assert np.max(np.abs(ref[0, :, :F].cpu().numpy() - oracle_mag(xs[0], sc, hop))) / \
         float(ref[0].max()) <= TOL[precision]
+
+
+@pytest.mark.parametrize("precision", ["bf16", "bf16x3"])
+def test_bound_staging_buffer_gives_identical_results(cw, sig, precision):
+    """A plan staging its bf16 signal in caller-bound buffers (one per
+    stream, as the server's slots do) gives the plan-owned staging's
+    scalograms byte for byte, across two buffers used in turn, with two GEMM
+    groups (200 scales); a buffer too small for the batch is refused before
+    anything is enqueued."""
+    hop, n = 64, 12000
+    lengths = [12000, 7001, 1]
+    xs = np.stack([sig.machine_clip(400 + i, n) for i in range(len(lengths))]).astype(np.float32)
+    sc = sig.scales_for_band(100, 8000, 200, 16000.0)
+    x = torch.from_numpy(xs).cuda()
+    ld = torch.tensor(lengths, dtype=torch.int64, device="cuda")
+    with cw.Plan(sc, hop=hop, max_len=n, precision=precision, path="direct") as plan:
+        ref = torch.full((len(lengths), len(sc), plan.frames_max), -4.0, device="cuda")
+        plan.execute(x, lengths=ld, out=ref)
+        need = plan.stage_bytes(len(lengths))
+        assert need > 0
+        bufs = [torch.empty(need + 512 * k, dtype=torch.uint8, device="cuda") for k in range(2)]
+        for buf in bufs + bufs:
+            plan.bind_stage(buf)
+            out = torch.full_like(ref, -4.0)
+            plan.execute(x, lengths=ld, out=out)
+            plan.sync()
+            assert torch.equal(out, ref)
+        small = torch.empty(need - 4096, dtype=torch.uint8, device="cuda")
+        plan.bind_stage(small)
+        out = torch.full_like(ref, -4.0)
+        with pytest.raises(cw.CwthError):
+            plan.execute(x, lengths=ld, out=out)
+        plan.sync()
+        assert bool((out == -4.0).all())
+        plan.bind_stage(None)
+        plan.execute(x, lengths=ld, out=out)
+        plan.sync()
+        assert torch.equal(out, ref)

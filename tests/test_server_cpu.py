@@ -147,7 +147,8 @@ def test_prepare_builds_the_plan_a_request_will_use(cw):
     with cw.Server(budget_bytes=1e12, max_batch=4, slots=3, precision="bf16x3",
                    dry_run=True) as srv:
         srv.prepare(16000.0, 16, 64, 1000)
-        assert srv.stats()["plans"] == 3   # bf16 staging: one plan per slot
+        # bf16 staging lives in each slot's buffer: one plan per key
+        assert srv.stats()["plans"] == 1
     with cw.Server(dry_run=True) as srv:
         with pytest.raises(cw.CwthError):
             srv.prepare(16000.0, 0, 64, 1000)
