@@ -473,3 +473,40 @@ def test_inverse_radix_knob(cw, sig):
             p1.set_inverse_radix(8)
         assert e.value.status == 4
         p1.set_inverse_radix(16)
+
+
+@pytest.mark.parametrize("precision,hop,n", [("fp32", 1, 60000), ("fp32", 8, 60000),
+                                             ("bf16x3", 256, 60000)])
+def test_dependent_launches_keep_stream_order(cw, sig, precision, hop, n):
+    """A plan's later spectral parts (and, with tensor-core scales, its
+    spectral part after the tensor-core kernel, which itself follows the
+    bf16 staging) start before the kernel before them ends.  Executes queued
+    back to back on one stream with no synchronisation, alternating inputs
+    and outputs, and stream work that reads each output right after its
+    execute, must see every row of every part: each result equals the same
+    input transformed alone."""
+    xs = [sig.machine_batch(2, n, seed0=s).astype(np.float32) for s in (3000, 3100)]
+    sc = sig.scales_for_band(50, 8000, 48, 16000.0)
+    with cw.Plan(sc, hop=hop, max_len=n, precision=precision) as plan:
+        info = plan.info()
+        if hop == 1:
+            assert info["spectral_parts"] >= 2, info
+        if precision != "fp32":
+            assert info["num_direct"] > 0 and info["num_spectral"] > 0, info
+        xd = [torch.from_numpy(x).cuda() for x in xs]
+        refs = []
+        for x in xd:
+            r = plan.execute(x)
+            plan.sync()
+            refs.append(r.clone())
+        outs = [torch.full_like(refs[0], -7.0) for _ in range(2)]
+        sums = []
+        for k in range(12):
+            i = k % 2
+            plan.execute(xd[i], out=outs[i])
+            sums.append(outs[i].sum(dim=(1, 2)))   # stream work right after the execute
+        torch.cuda.synchronize()
+        for k, s in enumerate(sums):
+            assert torch.equal(s, refs[k % 2].sum(dim=(1, 2))), k
+        for i in range(2):
+            assert torch.equal(outs[i], refs[i]), i
