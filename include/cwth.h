@@ -150,6 +150,13 @@ cwth_status cwth_plan_segment(const cwth_morlet *w, const double *scales, int32_
  * cudaMalloc, which wait for the device to go idle); calls with smaller or
  * equal batches allocate nothing.  cwth_plan_reserve sizes them up front.
  * Float32 plans whose scales all take the spectral path never allocate here.
+ * Within one call, the tensor-core kernel, a spectral part after it and
+ * every later spectral part are launched with programmatic stream
+ * serialisation (each may start while the kernel before it ends; none
+ * reads what that kernel writes, except the tensor-core kernel, which
+ * waits for its staging kernel first); every one of them completes after
+ * the kernel before it, so work enqueued on `stream` after the call still
+ * follows the whole transform.
  *
  * Errors: CWTH_ERR_BAD_PLAN, CWTH_ERR_INVALID_ARG (NULL buffer with
  * batch > 0, ld_x < max_len, batch < 0), CWTH_ERR_OOM (a workspace could
