@@ -427,8 +427,9 @@ void free_plan_memory(cwth_plan_s* p) {
 
 // Clip chunks of one cwth_execute_host call, never more than clips.  Spectral
 // chunks run on two alternating streams and stay efficient down to about
-// 7 MiB of input (the nearest count of 7 MiB chunks, at most 8; measured on
-// GB300 with 64 x 10 s clips, 41 MB: 6 chunks 0.299 ms, 5 chunks 0.308 ms;
+// 5 MiB of input (the nearest count of 5 MiB chunks, at most 8; measured on
+// GB300 with 64 x 10 s clips, 41 MB, medians of four: 3 / 4 / 5 / 6 / 8 /
+// 10 / 12 chunks 0.282 / 0.292 / 0.288 / 0.279 / 0.274 / 0.282 / 0.285 ms;
 // a smaller last chunk, or one split into scale groups, did not help).  Direct-path launches share one workspace and one stream,
 // and a small launch is bound by the latency of its few tiles, so plans with
 // direct-path scales use two chunks once the input reaches 16 MiB.
@@ -439,7 +440,7 @@ int32_t host_chunk_count(const cwth_plan_s* p, int32_t batch, int64_t ld_x) {
         if (p->n_dir > 0)
             n = bytes >= (16ll << 20) ? 2 : 1;
         else
-            n = std::min<int64_t>(8, (bytes + (7ll << 19)) / (7ll << 20));
+            n = std::min<int64_t>(8, (bytes + (5ll << 19)) / (5ll << 20));
     }
     n = std::max<int64_t>(1, n);
     return (int32_t)std::min<int64_t>(n, batch);
