@@ -26,6 +26,7 @@
 #ifndef CWTH_H
 #define CWTH_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus

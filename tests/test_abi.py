@@ -26,6 +26,22 @@ def cw():
     return cwth
 
 
+def test_header_compiles_as_plain_c(tmp_path):
+    """The boundary is a C ABI: include/cwth.h must stand alone in C99
+    (every type it names comes from a standard header it includes)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use_header.c"
+    src.write_text('#include "cwth.h"\nint main(void) { return (int)sizeof(cwth_plan_info) == 0; }\n')
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                        "-c", str(src), "-o", str(tmp_path / "use_header.o")],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+
+
 def test_header_declares_the_expected_entry_points():
     decl = _declared_functions()
     for name in ("cwth_plan", "cwth_execute", "cwth_destroy", "cwth_num_frames",
