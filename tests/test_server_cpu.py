@@ -88,6 +88,33 @@ def test_plan_cache_evicts_least_recently_used(cw):
     assert st["plan_bytes"] <= max(pa, pb) * 1.5
 
 
+def test_budget_charges_the_bf16_staging_of_a_batch(cw):
+    """With tensor-core scales a batch also stages its bf16 signal (in its
+    slot's buffer): the admission budget charges it, so a budget with room
+    for the plan and one clip's samples, lengths, scalograms and bf16x3
+    staging launches one clip at a time, where the same budget without the
+    staging charge would hold two clips."""
+    keep = []
+    L, S, hop = 1 << 14, 16, 64
+    with cw.Server(budget_bytes=1e12, max_batch=8, slots=4, precision="bf16x3",
+                   dry_run=True) as probe:
+        pb = probe.plan_bytes(16000.0, S, hop, L)
+    bb = _batch_bytes(1, L, S, hop)
+    sb = 2.0 * 3 * (L + 8192)          # the dry-run estimate: three bf16 parts
+    budget = pb + bb + sb + 1.0
+    assert budget >= pb + 2 * bb        # two clips fit without the staging charge
+    with cw.Server(budget_bytes=budget, plan_cache_bytes=1e12, max_batch=4, slots=2,
+                   precision="bf16x3", dry_run=True) as srv:
+        srv.submit(_requests(cw, [(i, 1000, S, hop) for i in range(6)], keep))
+        done = _drain(srv, 6)
+        st = srv.stats()
+    assert sorted(d[0] for d in done) == list(range(6))
+    assert all(d[1] == 0 for d in done)
+    assert max(d[2] for d in done) == 1
+    assert st["plans"] == 1
+    assert st["peak_bytes"] <= budget
+
+
 def test_request_that_never_fits_is_refused(cw):
     keep = []
     L, S, hop = 1 << 15, 64, 32
